@@ -1,0 +1,603 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for MC-moments micro-macro Parareal
+ * (arXiv 2310.11365).  TEST INFRASTRUCTURE ONLY: see oracle.h.
+ *
+ * Each function names the part of the paper it restates.  Readings of
+ * places where the paper is silent or garbled are marked "reading:".
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------
+ * Philox-4x32-10, from its published definition (Salmon et al., SC'11,
+ * "Parallel random numbers: as easy as 1, 2, 3"): ten rounds of the
+ * 4x32 S-box with multipliers M0, M1 and the key bumped by the Weyl
+ * constants W0, W1 between rounds.
+ * ---------------------------------------------------------------------- */
+static const uint32_t PHILOX_M0 = 0xD2511F53u;
+static const uint32_t PHILOX_M1 = 0xCD9E8D57u;
+static const uint32_t PHILOX_W0 = 0x9E3779B9u;
+static const uint32_t PHILOX_W1 = 0xBB67AE85u;
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += PHILOX_W0;
+      k1 += PHILOX_W1;
+    }
+    uint64_t prod0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+    uint64_t prod1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+    uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* u = ((o >> 9) + 1/2) 2^-23, strictly inside (0, 1). */
+double orc_uniform(uint32_t word) {
+  return ((double)(word >> 9) + 0.5) * ldexp(1.0, -23);
+}
+
+/* Box-Muller on two uniforms. */
+static void box_muller(double ua, double ub, double* z0, double* z1) {
+  const double two_pi = 6.283185307179586476925286766559;
+  double r = sqrt(-2.0 * log(ua));
+  *z0 = r * cos(two_pi * ub);
+  *z1 = r * sin(two_pi * ub);
+}
+
+/* The four normals of one Philox call, for particles 4q .. 4q+3. */
+static void normals4(const orc_problem* pr, int tag, uint32_t j, uint32_t n, uint32_t q, double z[4]) {
+  uint32_t key[2] = {(uint32_t)(pr->seed & 0xffffffffu), (uint32_t)(pr->seed >> 32)};
+  uint32_t ctr[4] = {q, j, n | ((uint32_t)tag << 24), pr->problem_tag};
+  uint32_t o[4];
+  orc_philox4x32_10(ctr, key, o);
+  box_muller(orc_uniform(o[0]), orc_uniform(o[1]), &z[0], &z[1]);
+  box_muller(orc_uniform(o[2]), orc_uniform(o[3]), &z[2], &z[3]);
+}
+
+double orc_normal(const orc_problem* pr, int tag, uint32_t j, uint32_t n, long long p) {
+  double z[4];
+  normals4(pr, tag, j, n, (uint32_t)(p / 4), z);
+  return z[p % 4];
+}
+
+void orc_initial(const orc_problem* pr, double* u0) {
+  for (long long p = 0; p < pr->P; ++p) u0[p] = pr->m0 + pr->s0 * orc_normal(pr, 1, 0, 0, p);
+}
+
+/* ------------------------------------------------------------------------
+ * Fine propagator F_n: Euler-Maruyama for the particle system, Sec. 1.2
+ * Eq. (Euler_Maruyama), Ito (Sec. 1.1).
+ * reading: the printed scheme drops the "X_n +" term; the update is
+ *   X_{j+1} = X_j + a(X_j, m_j) h + b(X_j, m_j) sqrt(h) xi_j
+ * with m_j the mean of the ensemble before the step.
+ * reading: the slice length T/N need not be a multiple of dt; the slice is
+ * cut into n_f = ceil(T/(N dt) - 1e-9) equal steps h = T/(N n_f).
+ * ---------------------------------------------------------------------- */
+int orc_fine_steps(const orc_problem* pr) {
+  double dT = pr->T / pr->N;
+  int nf = (int)ceil(dT / pr->dt - 1e-9);
+  return nf < 1 ? 1 : nf;
+}
+
+double orc_fine_h(const orc_problem* pr) {
+  return (pr->T / pr->N) / orc_fine_steps(pr);
+}
+
+static double drift(const orc_problem* pr, double x, double m) {
+  return -pr->c3 * x * x * x + pr->c1 * x + pr->kappa * m + pr->c0;
+}
+
+static double diffusion(const orc_problem* pr, double x, double m) {
+  return pr->B * x + pr->BE * m + pr->B0;
+}
+
+static double ensemble_mean(const double* u, long long P) {
+  double s = 0.0;
+  for (long long p = 0; p < P; ++p) s += u[p];
+  return s / (double)P;
+}
+
+void orc_fine(const orc_problem* pr, int n, const double* u_in, double* u_out, double* means) {
+  const long long P = pr->P;
+  const int nf = orc_fine_steps(pr);
+  const double h = orc_fine_h(pr);
+  const double sqrt_h = sqrt(h);
+  double* x = (double*)malloc(sizeof(double) * (size_t)P);
+  double* y = (double*)malloc(sizeof(double) * (size_t)P);
+  memcpy(x, u_in, sizeof(double) * (size_t)P);
+  for (int j = 0; j < nf; ++j) {
+    double m = ensemble_mean(x, P);
+    if (means) means[j] = m;
+    for (long long q = 0; 4 * q < P; ++q) {
+      double z[4];
+      normals4(pr, 0, (uint32_t)j, (uint32_t)n, (uint32_t)q, z);
+      for (int w = 0; w < 4 && 4 * q + w < P; ++w) {
+        long long p = 4 * q + w;
+        y[p] = x[p] + drift(pr, x[p], m) * h + diffusion(pr, x[p], m) * sqrt_h * z[w];
+      }
+    }
+    double* t = x; x = y; y = t;
+  }
+  if (means) means[nf] = ensemble_mean(x, P);
+  memcpy(u_out, x, sizeof(double) * (size_t)P);
+  free(x);
+  free(y);
+}
+
+/* ------------------------------------------------------------------------
+ * Restriction.  Unimodal: S(u) = [E u, V u] (Sec. 3.4).  Multimodal:
+ * Eq. (multimodal_R), per region D_i the fraction, mean and variance.
+ * reading: variances are population variances (1/n_i), which makes the
+ * mixture identity exact and keeps Lemma 3.1.
+ * reading: with I = 2, D_0 = {x < thr} and D_1 = {x >= thr}.
+ * ---------------------------------------------------------------------- */
+int orc_region(const orc_problem* pr, double x) {
+  if (pr->n_regions < 2) return 0;
+  return x < pr->threshold ? 0 : 1;
+}
+
+void orc_restrict(const orc_problem* pr, const double* u, orc_stats* st) {
+  const long long P = pr->P;
+  memset(st, 0, sizeof(*st));
+  double sum[ORC_MAX_REGIONS] = {0, 0};
+  for (int i = 0; i < ORC_MAX_REGIONS; ++i) {
+    st->min[i] = INFINITY;
+    st->max[i] = -INFINITY;
+  }
+  for (long long p = 0; p < P; ++p) {
+    int i = orc_region(pr, u[p]);
+    st->count[i] += 1;
+    sum[i] += u[p];
+    if (u[p] < st->min[i]) st->min[i] = u[p];
+    if (u[p] > st->max[i]) st->max[i] = u[p];
+  }
+  for (int i = 0; i < ORC_MAX_REGIONS; ++i)
+    st->mean[i] = st->count[i] > 0 ? sum[i] / (double)st->count[i] : 0.0;
+  double ss[ORC_MAX_REGIONS] = {0, 0};
+  for (long long p = 0; p < P; ++p) {
+    int i = orc_region(pr, u[p]);
+    double d = u[p] - st->mean[i];
+    ss[i] += d * d;
+  }
+  for (int i = 0; i < ORC_MAX_REGIONS; ++i)
+    st->var[i] = st->count[i] > 0 ? ss[i] / (double)st->count[i] : 0.0;
+  st->gmean = ensemble_mean(u, P);
+  double g = 0.0;
+  for (long long p = 0; p < P; ++p) g += (u[p] - st->gmean) * (u[p] - st->gmean);
+  st->gvar = g / (double)P;
+}
+
+/* Global mean and variance of a macro state, Sec. 2.2
+ * Eq. (mixture_of_distributions_mean_variance).
+ * reading: the printed Sigma^2, Sigma_i^2 are variances:
+ *   M = sum_i P_i M_i,  V = sum_i P_i (M_i^2 + V_i) - M^2.
+ * With one region the state is (M, V) itself. */
+void orc_mixture(const orc_problem* pr, const orc_macro* r, double* M, double* V) {
+  if (pr->n_regions < 2) {
+    *M = r->mean[0];
+    *V = r->var[0];
+    return;
+  }
+  double m = 0.0, s = 0.0;
+  for (int i = 0; i < pr->n_regions; ++i) m += r->frac[i] * r->mean[i];
+  for (int i = 0; i < pr->n_regions; ++i) s += r->frac[i] * (r->mean[i] * r->mean[i] + r->var[i]);
+  *M = m;
+  *V = s - m * m;
+}
+
+/* Matching T([mu, sigma], u), Sec. 3.4 Eq. (multimodal_M), applied to the
+ * particles of each selected region.
+ * reading: the affine branch is evaluated as
+ *   x + (mu - E u) + (sqrt(sigma / V u) - 1)(x - E u),
+ * algebraically the printed sqrt(sigma/V u)(x - E u) + mu, but the identity
+ * T(S u, u) = u (Lemma 3.1) then holds bit for bit.
+ * reading: the redraw branch (V u = 0) uses tag-2 draws with j = region and
+ * n = target slice, so it repeats in every iteration. */
+void orc_match(const orc_problem* pr, int n, const double* mu, const double* sigma,
+               const int* do_region, const orc_stats* st_u, const double* u, double* u_out) {
+  const long long P = pr->P;
+  for (long long p = 0; p < P; ++p) {
+    int i = orc_region(pr, u[p]);
+    double x = u[p];
+    if (do_region[i]) {
+      double m = st_u->mean[i];
+      double v = st_u->var[i];
+      if (v == 0.0) {
+        x = mu[i] + sqrt(sigma[i]) * orc_normal(pr, 2, (uint32_t)i, (uint32_t)n, p);
+      } else {
+        double s = sqrt(sigma[i] / v);
+        x = x + (mu[i] - m) + (s - 1.0) * (x - m);
+      }
+    }
+    u_out[p] = x;
+  }
+}
+
+/* ------------------------------------------------------------------------
+ * Coarse propagator C_n: moment ODE per region, Sec. 2.1-2.2.
+ * reading: the printed variance equations (2 E[a] + E[b^2], and the
+ * Gaussian model's "2 int a p + int b p") drop the centring and the square;
+ * by Ito, dV/dt = 2 E[(X - M) a] + E[b^2].  Under the Gaussian assumption of
+ * Eq. (Gaussian_model_McK_V_SDE) with polynomial drift the integrals are
+ * closed-form: E[X^3] = m^3 + 3 m v and Cov(X, X^3) = 3 v (m^2 + v), so per
+ * region i, with the mean field M = sum_j P_j m_j held by the frozen
+ * fractions (Def. 3.2: the coarse propagator does not move P_i):
+ *   dm_i/dt = -c3 (m_i^3 + 3 m_i v_i) + c1 m_i + kappa M + c0
+ *   dv_i/dt = 2 (-3 c3 v_i (m_i^2 + v_i) + c1 v_i) + B^2 v_i + (B m_i + BE M + B0)^2
+ * For c3 = 0 this is the Taylor model of Eq. (moment_model_class_1), exact
+ * for linear SDEs (Lemma 2.1).
+ * reading: the paper integrates with adaptive Tsit5; here forward Euler
+ * with n_c = ceil(T/(N coarse_h) - 1e-9) equal substeps.
+ * ---------------------------------------------------------------------- */
+int orc_coarse_steps(const orc_problem* pr) {
+  double dT = pr->T / pr->N;
+  int nc = (int)ceil(dT / pr->coarse_h - 1e-9);
+  return nc < 1 ? 1 : nc;
+}
+
+void orc_coarse_rhs(const orc_problem* pr, const orc_macro* r, double* dm, double* dv) {
+  const int I = pr->n_regions < 2 ? 1 : pr->n_regions;
+  double M = 0.0;
+  if (I == 1) {
+    M = r->mean[0];
+  } else {
+    for (int i = 0; i < I; ++i) M += r->frac[i] * r->mean[i];
+  }
+  for (int i = 0; i < I; ++i) {
+    double m = r->mean[i], v = r->var[i];
+    double ex3 = m * m * m + 3.0 * m * v;
+    double cov3 = 3.0 * v * (m * m + v);
+    double eb = pr->B * m + pr->BE * M + pr->B0;
+    dm[i] = -pr->c3 * ex3 + pr->c1 * m + pr->kappa * M + pr->c0;
+    dv[i] = 2.0 * (-pr->c3 * cov3 + pr->c1 * v) + pr->B * pr->B * v + eb * eb;
+  }
+}
+
+void orc_coarse(const orc_problem* pr, const orc_macro* in, orc_macro* out) {
+  const int I = pr->n_regions < 2 ? 1 : pr->n_regions;
+  const int nc = orc_coarse_steps(pr);
+  const double hc = (pr->T / pr->N) / nc;
+  orc_macro r = *in;
+  for (int s = 0; s < nc; ++s) {
+    double dm[ORC_MAX_REGIONS], dv[ORC_MAX_REGIONS];
+    orc_coarse_rhs(pr, &r, dm, dv);
+    for (int i = 0; i < I; ++i) {
+      r.mean[i] = r.mean[i] + hc * dm[i];
+      r.var[i] = r.var[i] + hc * dv[i];
+    }
+  }
+  *out = r;
+}
+
+/* ------------------------------------------------------------------------
+ * Learning of the particle fractions, Sec. 3.6 Def. 3.4 and App. H.
+ * reading: the two-state model of App. H,
+ *   P(t) = beta + (P(0) - beta) e^{alpha t},
+ * fitted to the fractions of region D_0 at the exact slice ends t_1..t_k
+ * (with P(0) known) by Levenberg-Marquardt; the paper leaves the LM
+ * settings unstated ("implemented in." has no reference), so: start from a
+ * one-step linear regression y_{n+1} = r y_n + c (r = e^{alpha dT},
+ * beta = c / (1 - r)); damping lambda_0 = 1e-3 scaled by diag(J^T J),
+ * /10 on an accepted step, x10 on a rejected one; at most 100 iterations;
+ * stop when the accepted step is below 1e-12 relative or lambda > 1e12.
+ * The fit is rejected (no learning this sweep) unless alpha < 0 and
+ * 0 <= beta <= 1.
+ * ---------------------------------------------------------------------- */
+static double lsq_cost(int n_pts, const double* t, const double* y, double p0, double a, double b) {
+  double s = 0.0;
+  for (int n = 0; n < n_pts; ++n) {
+    double r = y[n] - (b + (p0 - b) * exp(a * t[n]));
+    s += r * r;
+  }
+  return s;
+}
+
+int orc_lsq_fit(int n_pts, const double* t, const double* y, double p0, double dT,
+                double* alpha, double* beta) {
+  if (n_pts < 2) return -1;
+  /* initial guess: regress y_{n+1} on y_n over the sequence p0, y_0.. */
+  double sx = 0, sy = 0, sxx = 0, sxy = 0;
+  for (int n = 0; n < n_pts; ++n) {
+    double xv = n == 0 ? p0 : y[n - 1];
+    double yv = y[n];
+    sx += xv; sy += yv; sxx += xv * xv; sxy += xv * yv;
+  }
+  double cnt = (double)n_pts;
+  double den = sxx - sx * sx / cnt;
+  double a = -1.0 / t[n_pts - 1];
+  double b = y[n_pts - 1];
+  if (den > 0.0) {
+    double r = (sxy - sx * sy / cnt) / den;
+    double c = (sy - r * sx) / cnt;
+    if (r > 0.0 && r < 1.0) {
+      a = log(r) / dT;
+      b = c / (1.0 - r);
+    }
+  }
+  double lambda = 1e-3;
+  double cost = lsq_cost(n_pts, t, y, p0, a, b);
+  for (int it = 0; it < 100; ++it) {
+    double jaa = 0, jab = 0, jbb = 0, ga = 0, gb = 0;
+    for (int n = 0; n < n_pts; ++n) {
+      double e = exp(a * t[n]);
+      double f = b + (p0 - b) * e;
+      double r = y[n] - f;
+      double da = (p0 - b) * t[n] * e; /* d f / d alpha */
+      double db = 1.0 - e;             /* d f / d beta */
+      jaa += da * da; jab += da * db; jbb += db * db;
+      ga += da * r; gb += db * r;
+    }
+    double A = jaa * (1.0 + lambda), D = jbb * (1.0 + lambda), Bm = jab;
+    double det = A * D - Bm * Bm;
+    if (!(det > 0.0) || !isfinite(det)) {
+      lambda *= 10.0;
+      if (lambda > 1e12) break;
+      continue;
+    }
+    double step_a = (D * ga - Bm * gb) / det;
+    double step_b = (A * gb - Bm * ga) / det;
+    double na = a + step_a, nb = b + step_b;
+    double ncost = lsq_cost(n_pts, t, y, p0, na, nb);
+    if (isfinite(ncost) && ncost < cost) {
+      a = na; b = nb; cost = ncost;
+      lambda /= 10.0;
+      double rel = fmax(fabs(step_a) / (fabs(a) + 1e-300), fabs(step_b) / (fabs(b) + 1e-300));
+      if (rel < 1e-12) break;
+    } else {
+      lambda *= 10.0;
+      if (lambda > 1e12) break;
+    }
+  }
+  *alpha = a;
+  *beta = b;
+  if (!(a < 0.0) || !(b >= 0.0) || !(b <= 1.0) || !isfinite(a) || !isfinite(b)) return -2;
+  return 0;
+}
+
+/* H(P_k, m, theta) of Def. 3.4 (App. H form): beta + (P_k - beta) e^{alpha t},
+ * written P_k + (P_k - beta) expm1(alpha t) so that t = 0 returns P_k. */
+double orc_extrapolate(double p_k, double alpha, double beta, double dt_ahead) {
+  return p_k + (p_k - beta) * expm1(alpha * dt_ahead);
+}
+
+/* ------------------------------------------------------------------------
+ * Classical Parareal, Sec. 3.1 Eq. (original_parareal), with the noisy fine
+ * propagator of Lemma 4.1: F(u) = Fm u + Fa + eps.
+ * ---------------------------------------------------------------------- */
+void orc_parareal_scalar(int N, int K, double u0, double Fm, double Fa, double Gm, double Ga,
+                         const double* noise, double* out) {
+  const int W = N + 1;
+  out[0] = u0;
+  for (int n = 0; n < N; ++n) out[n + 1] = Gm * out[n] + Ga;
+  for (int k = 1; k <= K; ++k) {
+    double* cur = out + (size_t)k * W;
+    const double* prev = out + (size_t)(k - 1) * W;
+    cur[0] = u0;
+    for (int n = 0; n < N; ++n) {
+      double fine = Fm * prev[n] + Fa + (noise ? noise[(size_t)k * W + n + 1] : 0.0);
+      double g_new = Gm * cur[n] + Ga;
+      double g_old = Gm * prev[n] + Ga;
+      cur[n + 1] = g_new + fine - g_old;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------
+ * MC-moments Parareal: the generalised iteration Eq. (mM_parareal_other_k_NEW)
+ * with the operators of Def. 3.1 (unimodal), Def. 3.2 (multimodal) and
+ * Def. 3.4 (learning).
+ * ---------------------------------------------------------------------- */
+static void macro_from_stats(const orc_problem* pr, const orc_stats* st, orc_macro* r) {
+  memset(r, 0, sizeof(*r));
+  const int I = pr->n_regions < 2 ? 1 : pr->n_regions;
+  for (int i = 0; i < I; ++i) {
+    r->frac[i] = (double)st->count[i] / (double)pr->P;
+    r->mean[i] = st->mean[i];
+    r->var[i] = st->var[i];
+  }
+}
+
+/* Lifting L(rho) = T(rho, u0) per region, Def. 3.1/3.2.
+ * reading: a region of u0 with no particles is left alone; a negative
+ * coarse variance (which T cannot reach) leaves the region untouched. */
+static void lift(const orc_problem* pr, int n, const orc_macro* rho, const orc_stats* st0,
+                 const double* u0, double* out) {
+  const int I = pr->n_regions < 2 ? 1 : pr->n_regions;
+  int doit[ORC_MAX_REGIONS] = {0, 0};
+  double mu[ORC_MAX_REGIONS] = {0, 0}, sg[ORC_MAX_REGIONS] = {0, 0};
+  for (int i = 0; i < I; ++i) {
+    doit[i] = st0->count[i] > 0 && rho->var[i] >= 0.0;
+    mu[i] = rho->mean[i];
+    sg[i] = rho->var[i];
+  }
+  orc_match(pr, n, mu, sg, doit, st0, u0, out);
+}
+
+static double transformed(double x, double mu, double sigma, double m, double v) {
+  double s = sqrt(sigma / v);
+  return x + (mu - m) + (s - 1.0) * (x - m);
+}
+
+int orc_parareal(const orc_problem* pr, const double* u0_in, double* hist, orc_macro* macro_out,
+                 double* parts_out, orc_result* res) {
+  const int N = pr->N;
+  const long long P = pr->P;
+  const int I = pr->n_regions < 2 ? 1 : pr->n_regions;
+  const int multimodal = pr->variant != ORC_UNIMODAL && I > 1;
+  const int learning = pr->variant == ORC_LEARNING && I == 2;
+  const double dT = pr->T / N;
+  int K = pr->max_iter < N ? pr->max_iter : N;
+  if (K < 1) K = 1;
+
+  double* u0 = (double*)malloc(sizeof(double) * (size_t)P);
+  if (u0_in) memcpy(u0, u0_in, sizeof(double) * (size_t)P);
+  else orc_initial(pr, u0);
+
+  double* U = (double*)malloc(sizeof(double) * (size_t)P * (N + 1));      /* u^k_n */
+  double* Unew = (double*)malloc(sizeof(double) * (size_t)P * (N + 1));   /* u^{k+1}_n */
+  double* Bf = (double*)malloc(sizeof(double) * (size_t)P * N);           /* F_n(u^k_n) */
+  orc_macro* rho = (orc_macro*)calloc((size_t)N + 1, sizeof(orc_macro));
+  orc_macro* rho_new = (orc_macro*)calloc((size_t)N + 1, sizeof(orc_macro));
+  orc_macro* cache = (orc_macro*)calloc((size_t)N, sizeof(orc_macro));    /* C_n(rho^k_n) */
+  orc_stats* rst = (orc_stats*)calloc((size_t)N, sizeof(orc_stats));
+  double* frac0 = (double*)calloc((size_t)N + 1, sizeof(double));
+  double* tpts = (double*)calloc((size_t)N + 1, sizeof(double));
+
+  /* k = 0: rho^0_0 = R(u0); rho^0_{n+1} = C_n(rho^0_n); u^0_n = L(rho^0_n). */
+  orc_stats st0;
+  orc_restrict(pr, u0, &st0);
+  macro_from_stats(pr, &st0, &rho[0]);
+  for (int n = 0; n < N; ++n) {
+    orc_coarse(pr, &rho[n], &rho[n + 1]);
+    cache[n] = rho[n + 1];
+  }
+  memcpy(U, u0, sizeof(double) * (size_t)P);
+  for (int n = 1; n <= N; ++n) lift(pr, n, &rho[n], &st0, u0, U + (size_t)n * P);
+  if (hist) {
+    for (int n = 0; n <= N; ++n) orc_mixture(pr, &rho[n], &hist[2 * n], &hist[2 * n + 1]);
+  }
+
+  orc_result r = {0, 0, 0.0, 0, 0};
+  for (int k = 1; k <= K; ++k) {
+    /* the fine propagator on every slice (parallel in the paper) */
+    for (int n = 0; n < N; ++n) {
+      orc_fine(pr, n, U + (size_t)n * P, Bf + (size_t)n * P, NULL);
+      orc_restrict(pr, Bf + (size_t)n * P, &rst[n]);
+    }
+    /* fractions of the new iterate come from the fine propagator (Def. 3.2) */
+    double* fr = (double*)malloc(sizeof(double) * (size_t)(N + 1) * ORC_MAX_REGIONS);
+    for (int i = 0; i < I; ++i) fr[i] = rho[0].frac[i];
+    for (int n = 0; n < N; ++n)
+      for (int i = 0; i < I; ++i) fr[(n + 1) * ORC_MAX_REGIONS + i] = (double)rst[n].count[i] / (double)P;
+    /* learning (Def. 3.4): after sweep k the slice ends t_0..t_k are exact;
+     * fit on them and extrapolate the fractions beyond t_k. */
+    if (learning && k >= 2) {
+      for (int n = 0; n <= k; ++n) {
+        frac0[n] = fr[n * ORC_MAX_REGIONS + 0];
+        tpts[n] = n * dT;
+      }
+      double al, be;
+      if (orc_lsq_fit(k, tpts + 1, frac0 + 1, frac0[0], dT, &al, &be) == 0) {
+        double pk = frac0[k];
+        for (int n = k + 1; n <= N; ++n) {
+          double p0hat = orc_extrapolate(pk, al, be, (n - k) * dT);
+          fr[n * ORC_MAX_REGIONS + 0] = p0hat;
+          fr[n * ORC_MAX_REGIONS + 1] = 1.0 - p0hat;
+        }
+      }
+    }
+
+    rho_new[0] = rho[0];
+    memcpy(Unew, u0, sizeof(double) * (size_t)P);
+    for (int n = 0; n < N; ++n) {
+      for (int i = 0; i < I; ++i) rho_new[n].frac[i] = fr[n * ORC_MAX_REGIONS + i];
+      orc_macro a;
+      orc_coarse(pr, &rho_new[n], &a);
+      const orc_stats* b = &rst[n];
+      orc_macro nxt;
+      memset(&nxt, 0, sizeof(nxt));
+      int doit[ORC_MAX_REGIONS] = {0, 0};
+      double mu[ORC_MAX_REGIONS] = {0, 0}, sg[ORC_MAX_REGIONS] = {0, 0};
+      for (int i = 0; i < I; ++i) {
+        if (b->count[i] == 0) {
+          /* reading (Def. 3.2/3.4): an empty region carries the coarse
+           * prediction and moves no particle */
+          nxt.mean[i] = a.mean[i];
+          nxt.var[i] = a.var[i];
+          continue;
+        }
+        /* alpha = a + R(b) - c, evaluated as R(b) + (a - c) so that a == c
+         * gives R(b) exactly (Property 3.3 bit for bit) */
+        double am = b->mean[i] + (a.mean[i] - cache[n].mean[i]);
+        double av = b->var[i] + (a.var[i] - cache[n].var[i]);
+        int accept = av >= 0.0;
+        if (multimodal && accept) {
+          /* Def. 3.2: accept only if T leaves the fractions unchanged;
+           * T is monotone, so test the extreme particle of the region.
+           * reading: a region with V = 0 (redraw branch) is not moved. */
+          if (b->var[i] == 0.0) {
+            accept = 0;
+          } else if (i == 0) {
+            accept = transformed(b->max[0], am, av, b->mean[0], b->var[0]) < pr->threshold;
+          } else {
+            accept = transformed(b->min[1], am, av, b->mean[1], b->var[1]) >= pr->threshold;
+          }
+        }
+        if (accept) {
+          nxt.mean[i] = am;
+          nxt.var[i] = av;
+          doit[i] = 1;
+          mu[i] = am;
+          sg[i] = av;
+          r.accepted_total++;
+        } else {
+          nxt.mean[i] = b->mean[i];
+          nxt.var[i] = b->var[i];
+          r.rejected_total++;
+        }
+      }
+      for (int i = 0; i < I; ++i) nxt.frac[i] = fr[(n + 1) * ORC_MAX_REGIONS + i];
+      rho_new[n + 1] = nxt;
+      orc_match(pr, n + 1, mu, sg, doit, b, Bf + (size_t)n * P, Unew + (size_t)(n + 1) * P);
+      cache[n] = a;
+    }
+    free(fr);
+
+    double change = 0.0;
+    for (int n = 0; n <= N; ++n) {
+      double M1, V1, M0, V0;
+      orc_mixture(pr, &rho_new[n], &M1, &V1);
+      orc_mixture(pr, &rho[n], &M0, &V0);
+      change = fmax(change, fmax(fabs(M1 - M0), fabs(V1 - V0)));
+      if (hist) {
+        hist[((size_t)k * (N + 1) + n) * 2] = M1;
+        hist[((size_t)k * (N + 1) + n) * 2 + 1] = V1;
+      }
+    }
+    memcpy(rho, rho_new, sizeof(orc_macro) * (size_t)(N + 1));
+    double* t = U; U = Unew; Unew = t;
+    r.sweeps = k;
+    r.last_change = change;
+    if (change < pr->tol) {
+      r.converged = 1;
+      break;
+    }
+  }
+  if (r.sweeps == N) r.converged = 1;
+  if (macro_out) memcpy(macro_out, rho, sizeof(orc_macro) * (size_t)(N + 1));
+  if (parts_out) memcpy(parts_out, U, sizeof(double) * (size_t)P * (N + 1));
+  if (res) *res = r;
+  free(u0); free(U); free(Unew); free(Bf); free(rho); free(rho_new); free(cache); free(rst);
+  free(frac0); free(tpts);
+  return 0;
+}
+
+void orc_fine_serial(const orc_problem* pr, const double* u0_in, orc_stats* stats, double* parts) {
+  const long long P = pr->P;
+  const int N = pr->N;
+  double* u = (double*)malloc(sizeof(double) * (size_t)P);
+  double* v = (double*)malloc(sizeof(double) * (size_t)P);
+  if (u0_in) memcpy(u, u0_in, sizeof(double) * (size_t)P);
+  else orc_initial(pr, u);
+  for (int n = 0; n <= N; ++n) {
+    if (stats) orc_restrict(pr, u, &stats[n]);
+    if (parts) memcpy(parts + (size_t)n * P, u, sizeof(double) * (size_t)P);
+    if (n == N) break;
+    orc_fine(pr, n, u, v, NULL);
+    double* t = u; u = v; v = t;
+  }
+  free(u);
+  free(v);
+}
