@@ -1,0 +1,334 @@
+"""Benchmark: fine particle-steps/s of MC-moments micro-macro Parareal on the
+nonlinear unimodal workload (cubic drift, P = 1e6 particles, N = 64 slices,
+n_f = 125 steps, FP32 particles with FP64 moments, tol 1e-6).
+
+One step = one complete Parareal solve (lifting, then fine sweeps and
+coarse/iterator sweeps until max_n |d(M, V)| < tol or k = N).  value = the
+fine particle-steps all ranks performed / the max-over-ranks device time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fine particle-steps/s; Parareal time-to-tol, FP32/batched vs FP64 plain"
+UNIT = "particle-steps/s"
+WORKLOAD = "config2: cubic MV SDE dX=(-X^3+kappa(E[X]-X))dt+sigma dW, kappa=1, sigma=0.5, X0~N(0.5,0.2^2), T=8, N=64, dt=1e-3 (n_f=125), P=1e6, Gaussian-closure coarse, tol 1e-6"
+# Algorithmic FP32/INT32 lane operations of one particle-step (mixed path):
+# Philox-4x32-10 shared by 4 particles (10 rounds x (2 wide multiplies +
+# 2 three-input xors) / 4 = 10), the uniform map (3), Box-Muller shared by 2
+# particles (log 2, sqrt 2, sin/cos 3, products 2 -> 4.5), the update x^2 and
+# four fused multiply-adds (5), the running sum (1).
+ALG_OPS_PER_PARTICLE_STEP = 23.5
+SMS = 152
+LANES = 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[1]))
+                smax.append(float(s[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, s[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_baseline(seconds: float = 12.0) -> dict:
+    """The FP64 oracle as it stands, on this host's cores (it is
+    single-threaded): fine particle-steps/s of the config-2 model on a
+    bounded sample (P = 2000 particles, whole slices, until ~`seconds`)."""
+    import oracle
+    from paper_2310_11365_gb300 import workloads as W
+
+    oracle.build()
+    p = W.config2(P=2000, precision="fp64")
+    u = oracle.initial(p)
+    nf = oracle.fine_steps(p)
+    t0 = time.perf_counter()
+    slices = 0
+    while True:
+        u = oracle.fine(p, slices % p.N, u)
+        slices += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    steps = slices * p.P * nf
+    return {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle fine propagator on the config-2 model, P=2000, {slices} slices x {nf} steps ({steps:.3g} particle-steps, {dt:.1f} s)"}
+
+
+def reference_arm(args, world, rank):
+    """The oracle timed as it stands on the host cores: one step = one
+    Parareal iteration (fine propagator on all 64 slices + coarse/iterator
+    sweep) of the config-2 workload on a bounded sample of P = 500 particles."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2310_11365_gb300 import workloads as W
+
+    oracle.build()
+    p = W.config2(P=500, precision="fp64", max_iter=1, tol=0.0)
+    nf = oracle.fine_steps(p)
+    for _ in range(args.warmup):
+        oracle.parareal(p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.parareal(p)
+    dt = time.perf_counter() - t0
+    steps = args.steps * p.N * p.P * nf
+    value = steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "P=500, one Parareal iteration per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one MC-moments Parareal iteration (all {p.N} slices x {nf} steps) at P=500 per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU time-to-tol comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2310_11365_gb300 import build as native_build
+    from paper_2310_11365_gb300 import mmp
+    from paper_2310_11365_gb300 import workloads as W
+
+    native_build.build()
+    # replicas only: every rank solves its own copy (distinct problem tag)
+    p = W.config2(problem_tag=rank)
+    solver = mmp.Solver(p)
+    mmp.mmp_set_timing(solver.ctx, True)
+    plan = solver.plan()
+    for _ in range(max(args.warmup, 3)):
+        solver.run()
+    torch.cuda.synchronize()
+    mmp.mmp_timing(solver.ctx, reset=True)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sweeps = []
+    for _ in range(args.steps):
+        sweeps.append(solver.run())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    tm = mmp.mmp_timing(solver.ctx, reset=True)
+    steps_done = tm["fine_particle_steps"]
+    t_max = max_over_ranks(ms / 1e3, world)
+    total_steps = sum_over_ranks(steps_done, world)
+    value = total_steps / t_max
+    mom = solver.moments()
+
+    # roofline of the dominant kernel (the fused fine kernel): algorithmic
+    # lane-ops per launch / average launch time, against the FP32 issue peak
+    fine_s = tm["fine_ms"] / 1e3
+    achieved = ALG_OPS_PER_PARTICLE_STEP * steps_done / fine_s / 1e12
+    peaks = _peaks()
+    f_clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak = SMS * LANES * f_clk / 1e12
+
+    # end to end through the C-ABI with host buffers: u0 from pinned host
+    # memory in, all moments back to host, every step
+    e2e = None
+    if True:
+        dtype = np.float32
+        u0_host = torch.from_numpy(solver.particles(0).cpu().numpy().astype(dtype)).pin_memory()
+        out_host = np.empty((p.N + 1) * mmp.MOMENT_STRIDE, np.float64)
+        torch.cuda.synchronize()
+        mmp.mmp_timing(solver.ctx, reset=True)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            mmp.mmp_set_initial(solver.ctx, 0, u0_host.data_ptr(), True)
+            mmp.mmp_run(solver.ctx)
+            out = mmp.mmp_get_moments(solver.ctx, 0, p.N)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        tme = mmp.mmp_timing(solver.ctx, reset=True)
+        e2e = {"value": sum_over_ranks(tme["fine_particle_steps"], world) / max_over_ranks(te, world),
+               "unit": UNIT, "h2d_bytes_per_step": int(p.P * 4),
+               "d2h_bytes_per_step": int(out.nbytes)}
+
+    # plain FP64 GPU form: time to the same tolerance (one solve)
+    fp64 = None
+    if not args.no_fp64:
+        p64 = W.config2(precision="fp64", problem_tag=rank)
+        s64 = mmp.Solver(p64)
+        mmp.mmp_set_timing(s64.ctx, True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k64 = s64.run()
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        tm64 = mmp.mmp_timing(s64.ctx, reset=True)
+        m64 = s64.moments()
+        fp64 = {"time_to_tol_s": t64, "sweeps": k64, "particle_steps_per_s": tm64["fine_particle_steps"] / t64,
+                "max_abs_diff_M_vs_mixed": float(np.max(np.abs(m64[:, 6] - mom[:, 6]))),
+                "max_abs_diff_V_vs_mixed": float(np.max(np.abs(m64[:, 7] - mom[:, 7])))}
+        s64.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 particles / f64 moments",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}",
+                       "precision": "mixed", "l2": "inputs larger than L2 (2 x 256 MB particle buffers)",
+                       "plan": plan},
+            "time_to_tol_s": ms / 1e3 / args.steps, "sweeps_to_tol": sweeps[-1],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_fine<float>", "ops_per_particle_step": ALG_OPS_PER_PARTICLE_STEP,
+                         "fine_launches": tm["fine_launches"],
+                         "fine_ms_per_launch": tm["fine_ms"] / max(1, tm["fine_launches"]),
+                         "peak_note": "152 SMs x 128 FP32/INT32 lanes x max SM clock (MEASURED_PEAKS sm_max_mhz)"},
+            "e2e": e2e,
+            "fp64_plain": fp64,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": tm["fine_launches"] + tm["other_launches"],
+            "final_M_T": float(mom[-1, 6]), "final_V_T": float(mom[-1, 7]),
+        }
+        print(json.dumps(line))
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * mmp.h -- C-ABI of the GB300 (sm_103a) MC-moments micro-macro Parareal
+ * library libmmp.so (Bossuyt, Vandewalle, Samaey, arXiv 2310.11365).
+ *
+ * The library runs the data-parallel hot path of the method on one GPU:
+ * the Euler-Maruyama fine propagator of a P-particle mean-field ensemble
+ * (Sec. 1.2 Eq. Euler_Maruyama) for all Parareal slices at once, fused with
+ * the restriction (Sec. 3.4, Eq. multimodal_R) and the matching
+ * (Eq. multimodal_M), and the sequential coarse moment-ODE sweep with the
+ * Parareal iterator (Eq. mM_parareal_other_k_NEW, Defs. 3.1, 3.2, 3.4).
+ *
+ * Conventions for every call:
+ *  - return value: MMP_OK (0) or a negative MMP_ERR_* code; mmp_strerror()
+ *    names it.  Arguments are checked on the host before any launch.
+ *  - memory: the library allocates no device memory.  The caller passes one
+ *    device workspace (size from mmp_workspace_size) and owns it; the
+ *    context only records pointers.  Host pointers passed in are read or
+ *    written before the call returns.
+ *  - streams: `stream` is a cudaStream_t (passed as void*); all device work
+ *    of a context is issued on it, in order.  Calls documented as
+ *    "synchronising" wait for that stream before they return.
+ *  - layout: particle ensembles are contiguous arrays of P values, double
+ *    (MMP_FP64) or float (MMP_MIXED), 16-byte aligned.
+ */
+#ifndef MMP_H
+#define MMP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MMP_OK 0
+#define MMP_ERR_INVALID_ARG (-1) /* a descriptor or argument is out of range  */
+#define MMP_ERR_WORKSPACE (-2)   /* workspace missing, misaligned or too small */
+#define MMP_ERR_UNSUPPORTED (-3) /* valid but not supported (e.g. too large)   */
+#define MMP_ERR_CUDA (-4)        /* a CUDA call failed (see mmp_last_cuda_error) */
+#define MMP_ERR_NUMERIC (-5)     /* device saw NaN/Inf or a negative variance   */
+#define MMP_ERR_TIMEOUT (-6)     /* a bounded device-side wait gave up          */
+#define MMP_ERR_STATE (-7)       /* call out of order (e.g. iterate before lift) */
+
+/* Precision of the particle state.  MMP_FP64: particles, draws and all
+ * moments in double.  MMP_MIXED: particles and their normal draws in float;
+ * per-step means, restriction moments, the coarse ODE, the Parareal
+ * correction, matching parameters and the fraction fit stay in double. */
+#define MMP_FP64 0
+#define MMP_MIXED 1
+
+/* Parareal variant: Def. 3.1 (one region), Def. 3.2 (per region, with the
+ * fractions-unchanged test), Def. 3.4 (Def. 3.2 plus learned fractions). */
+#define MMP_UNIMODAL 0
+#define MMP_MULTIMODAL 1
+#define MMP_LEARNING 2
+
+/* Problem statement (Sec. 1.1 Eq. general_McKean_Vlasov restricted to the
+ * class of Eq. SDE_class_1 with f(x) = x):
+ *   dX = a(X, E[X]) dt + b(X, E[X]) dW,  X(0) ~ N(m0, s0^2)
+ *   a(x, m) = -c3 x^3 + c1 x + kappa m + c0
+ *   b(x, m) = B x + BE m + B0
+ * on [0, T] cut into N Parareal slices; each slice takes
+ * n_f = ceil(T/(N dt) - 1e-9) Euler-Maruyama steps of h = T/(N n_f).
+ * The coarse propagator is the Gaussian-closure moment ODE per region
+ * (exact for c3 = 0, Lemma 2.1) integrated by forward Euler with
+ * n_c = ceil(T/(N coarse_h) - 1e-9) substeps.  With n_regions = 2 the
+ * regions are D_0 = {x < threshold}, D_1 = {x >= threshold}.
+ * Random numbers: Philox-4x32-10 with key (seed mod 2^32, seed div 2^32)
+ * and counter (p div 4, step, slice | tag << 24, problem_tag). */
+typedef struct {
+  double c3, c1, kappa, c0;  /* drift coefficients                           */
+  double B, BE, B0;          /* diffusion coefficients                       */
+  double m0, s0;             /* initial law N(m0, s0^2)                      */
+  double T;                  /* horizon, > 0                                  */
+  int N;                     /* slices, 1..65535                              */
+  double dt;                 /* requested fine step, > 0                      */
+  long long P;               /* particles, 1..2^31                            */
+  double coarse_h;           /* largest coarse step, > 0                      */
+  int n_regions;             /* 1 or 2                                        */
+  double threshold;          /* region boundary (n_regions = 2)               */
+  int variant;               /* MMP_UNIMODAL / MMP_MULTIMODAL / MMP_LEARNING  */
+  int precision;             /* MMP_FP64 / MMP_MIXED                          */
+  unsigned long long seed;
+  unsigned int problem_tag;
+  double tol;                /* stop when max_n max(|dM|,|dV|) < tol          */
+  int max_iter;              /* at most this many fine sweeps; <= 0 means N   */
+} mmp_problem_desc;
+
+typedef struct mmp_ctx mmp_ctx;
+
+/* Number of doubles per slice in the moments returned by mmp_get_moments:
+ * frac_0, mean_0, var_0, frac_1, mean_1, var_1, M, V (region 1 zero when
+ * n_regions = 1). */
+#define MMP_MOMENT_STRIDE 8
+/* Number of doubles per ensemble in restriction records (mmp_fine_serial,
+ * mmp_restrict): count_0, mean_0, var_0, min_0, max_0, count_1, mean_1,
+ * var_1, min_1, max_1, mean, var, region_flips, input_mean, 0, 0. */
+#define MMP_STAT_STRIDE 16
+
+const char* mmp_strerror(int code);
+int mmp_version(void);
+/* Last CUDA error code seen by the library in this process (0 if none). */
+int mmp_last_cuda_error(void);
+
+/* Bytes of device workspace needed for n_problems problems. */
+int mmp_workspace_size(const mmp_problem_desc* descs, int n_problems, size_t* bytes);
+
+/* Create a context over caller-owned device workspace.  Validates every
+ * descriptor, plans the launch shape of the fine kernel per problem and
+ * draws the initial ensembles X0 = m0 + s0 z (tag-1 draws) on `stream`.
+ * Asynchronous.  The context (a small host object) is freed by
+ * mmp_destroy; the workspace stays the caller's. */
+int mmp_create(mmp_ctx** ctx, const mmp_problem_desc* descs, int n_problems, void* workspace,
+               size_t workspace_bytes, void* stream);
+int mmp_destroy(mmp_ctx* ctx);
+
+/* Replace problem `prob`'s initial ensemble by P values (double for
+ * MMP_FP64, float for MMP_MIXED) at `u0`, a host pointer if from_host != 0
+ * else a device pointer.  Copies before returning (host) or on the stream. */
+int mmp_set_initial(mmp_ctx* ctx, int prob, const void* u0, int from_host);
+
+/* Iteration k = 0 (Eq. mM_parareal_0 / generalised form): restriction of
+ * u0, sequential coarse sweep rho^0_{n+1} = C_n(rho^0_n) and lifting
+ * parameters L(rho) = T(rho, u0).  Asynchronous. */
+int mmp_lift(mmp_ctx* ctx);
+
+/* Up to n_iter fine sweeps, each followed by the coarse/iterator sweep
+ * (Eq. mM_parareal_other_k_NEW).  Slices already exact (Property 3.3) are
+ * not recomputed.  Synchronising: reads each problem's convergence word
+ * after every sweep; *all_converged (optional) is set when every problem
+ * met its tolerance or reached max_iter. */
+int mmp_iterate(mmp_ctx* ctx, int n_iter, int* all_converged);
+
+/* mmp_lift followed by mmp_iterate until every problem stops.
+ * Synchronising.  *sweeps_out (optional): the largest sweep count. */
+int mmp_run(mmp_ctx* ctx, int* sweeps_out);
+
+/* Per-problem state after the last sweep.  Synchronising.
+ * dev_err: device status word (0 or an MMP_ERR_* code). */
+int mmp_status(mmp_ctx* ctx, int prob, int* sweeps, int* converged, double* last_change,
+               int* dev_err);
+
+/* Macro state rho^K_n, n = 0..N, to host memory `out`
+ * [(N+1) * MMP_MOMENT_STRIDE].  Synchronising. */
+int mmp_get_moments(mmp_ctx* ctx, int prob, double* out);
+
+/* Particle iterate u^K_n of slice end n (0..N), i.e. the matched fine
+ * output, P values to `dst` (host if to_host != 0, else device).
+ * Synchronising when to_host. */
+int mmp_get_particles(mmp_ctx* ctx, int prob, int n, void* dst, int to_host);
+
+/* Serial reference u_{n+1} = F_n(u_n) from the same u0 and the same
+ * draws, for slices 0 .. n_end-1 (n_end <= 0 or > N means N); restriction
+ * records of u_0..u_{n_end} to host `stats_out` [(n_end+1) * MMP_STAT_STRIDE]
+ * (may be NULL).  If parts_dev is not NULL it receives u_{n_end} (device).
+ * Uses the same launch shape as the Parareal sweeps, so the first k slice
+ * ends after k sweeps match it bit for bit.  Synchronising. */
+int mmp_fine_serial(mmp_ctx* ctx, int prob, int n_end, double* stats_out, void* parts_dev);
+
+/* Launch shape chosen for problem `prob`: quads of 4 particles held per
+ * thread, CTAs per slice (one group barrier spans them), and the largest
+ * number of slices one launch runs concurrently.  Any pointer may be NULL. */
+int mmp_get_plan(mmp_ctx* ctx, int prob, int* quads_per_thread, int* ctas_per_slice,
+                 int* max_concurrent_slices);
+
+/* Device-time accounting.  With timing on, the library records CUDA
+ * events on the context stream around every fine-kernel launch and reads
+ * them at its synchronisation points.  mmp_timing reports, since the last
+ * reset: fine-kernel milliseconds and launches, the particle-steps those
+ * launches performed, and the number of other library kernel launches
+ * (driver, initial ensemble).  Any output pointer may be NULL. */
+int mmp_set_timing(mmp_ctx* ctx, int on);
+int mmp_timing(mmp_ctx* ctx, int reset, double* fine_ms, long long* fine_launches,
+               double* fine_particle_steps, long long* other_launches);
+
+/* One fine propagation F_n of an explicit ensemble (no matching):
+ * reads P values at u_in (device), writes F_n(u_in) to u_out (device,
+ * may not alias u_in) and its restriction record to stats_out (host,
+ * MMP_STAT_STRIDE doubles, may be NULL).  `n` is the slice index used
+ * for the draws.  Synchronising. */
+int mmp_fine(mmp_ctx* ctx, int prob, int n, const void* u_in, void* u_out, double* stats_out);
+
+/* Philox-4x32-10 on n counters: ctr (device, 4n uint32), key (host, 2
+ * uint32) -> out (device, 4n uint32).  Asynchronous on `stream`. */
+int mmp_philox(const unsigned int* ctr, const unsigned int* key, unsigned int* out, long long n,
+               void* stream);
+
+/* The normals the fine propagator uses for (tag, step j, slice n):
+ * out[p] for p < count (device, double or float per `precision`).
+ * Asynchronous on `stream`. */
+int mmp_normals(const mmp_problem_desc* desc, int tag, unsigned int j, unsigned int n,
+                long long count, void* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,661 @@
+// api.cu -- the C-ABI of libmmp: descriptor validation, workspace layout,
+// launch planning of the fine kernel, and the Parareal orchestration
+// (Eq. mM_parareal_other_k_NEW) on one stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "driver.cuh"
+#include "fine.cuh"
+#include "misc.cuh"
+#include "mmp_internal.cuh"
+
+namespace mmp {
+const void* fine_kernel_f32(int nq, bool mult);
+const void* fine_kernel_f64(int nq, bool mult);
+
+const void* fine_kernel(int precision, int nq, bool mult) {
+  return precision == MMP_MIXED ? fine_kernel_f32(nq, mult) : fine_kernel_f64(nq, mult);
+}
+
+cudaError_t launch_fine(int precision, int nq, bool mult, int grid, const FineArgs& args,
+                        cudaStream_t stream) {
+  const void* fn = fine_kernel(precision, nq, mult);
+  if (fn == nullptr) return cudaErrorInvalidValue;
+  FineArgs copy = args;
+  void* params[] = {&copy};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTPB), params, 0, stream);
+}
+}  // namespace mmp
+
+using namespace mmp;
+
+namespace {
+
+int g_last_cuda_error = 0;
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda_error = (int)e;
+  return MMP_ERR_CUDA;
+}
+#define MMP_CUDA(call)                         \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+
+struct Prob {
+  mmp_problem_desc d;
+  int I = 1, nf = 1, nc = 1, max_sweeps = 1;
+  double h = 0, sqrt_h = 0, dT = 0, hc = 0;
+  int Q = 0;
+  long long pitch = 0;
+  size_t esz = 8;
+  bool mult = false;
+  uint32_t key0 = 0, key1 = 0;
+  // launch plan of the fine kernel
+  int nq = 1, G = 1, slots_max = 1;
+  // device memory inside the caller's workspace
+  char* u0 = nullptr;
+  char* B[2] = {nullptr, nullptr};
+  char* S[2] = {nullptr, nullptr};
+  double *stats = nullptr, *stats_u0 = nullptr, *ser_stats = nullptr, *tmp_stats = nullptr;
+  double *rho = nullptr, *cache = nullptr, *aff = nullptr, *ctl = nullptr, *partials = nullptr;
+  unsigned *counters = nullptr, *status = nullptr;
+  // host view of the iteration
+  int sweeps = 0;
+  bool lifted = false, done = false, converged = false;
+  double last_change = 0.0;
+  std::vector<int> out_buf;  // which B buffer holds the latest F_n output of slice n
+};
+
+struct Device {
+  int dev = 0, sms = 0;
+};
+
+int query_device(Device& d) {
+  MMP_CUDA(cudaGetDevice(&d.dev));
+  MMP_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, d.dev));
+  return MMP_OK;
+}
+
+bool finite_all(const mmp_problem_desc& d) {
+  const double v[] = {d.c3, d.c1, d.kappa, d.c0, d.B, d.BE, d.B0, d.m0, d.s0,
+                      d.T, d.dt, d.coarse_h, d.threshold, d.tol};
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
+int validate(const mmp_problem_desc& d) {
+  if (!finite_all(d)) return MMP_ERR_INVALID_ARG;
+  if (!(d.T > 0) || !(d.dt > 0) || !(d.coarse_h > 0) || d.s0 < 0 || d.tol < 0) return MMP_ERR_INVALID_ARG;
+  if (d.N < 1 || d.N > 65535) return MMP_ERR_INVALID_ARG;
+  if (d.P < 1 || d.P > (1LL << 31) - 8) return MMP_ERR_INVALID_ARG;
+  if (d.n_regions < 1 || d.n_regions > 2) return MMP_ERR_INVALID_ARG;
+  if (d.variant < MMP_UNIMODAL || d.variant > MMP_LEARNING) return MMP_ERR_INVALID_ARG;
+  if (d.precision != MMP_FP64 && d.precision != MMP_MIXED) return MMP_ERR_INVALID_ARG;
+  const double steps = std::ceil((d.T / d.N) / d.dt - 1e-9);
+  if (!(steps >= 1) || steps > 2e9) return MMP_ERR_INVALID_ARG;
+  const double csteps = std::ceil((d.T / d.N) / d.coarse_h - 1e-9);
+  if (!(csteps >= 1) || csteps > 1e7) return MMP_ERR_INVALID_ARG;
+  return MMP_OK;
+}
+
+void derive(Prob& p) {
+  const mmp_problem_desc& d = p.d;
+  p.I = d.n_regions;
+  p.dT = d.T / d.N;
+  p.nf = std::max(1, (int)std::ceil(p.dT / d.dt - 1e-9));
+  p.h = p.dT / p.nf;
+  p.sqrt_h = std::sqrt(p.h);
+  p.nc = std::max(1, (int)std::ceil(p.dT / d.coarse_h - 1e-9));
+  p.hc = p.dT / p.nc;
+  p.Q = (int)((d.P + 3) / 4);
+  p.pitch = 4LL * p.Q;
+  p.esz = d.precision == MMP_MIXED ? 4 : 8;
+  p.mult = d.B != 0.0 || d.BE != 0.0;
+  p.key0 = (uint32_t)(d.seed & 0xffffffffull);
+  p.key1 = (uint32_t)(d.seed >> 32);
+  const int mi = d.max_iter > 0 ? d.max_iter : d.N;
+  p.max_sweeps = std::min(d.N, mi);
+  p.out_buf.assign(d.N, -1);
+}
+
+// Launch plan of the fine kernel: quads per thread (nq) and CTAs per slice
+// (G).  The group size is fixed per problem so that every launch reduces in
+// the same order (the serial reference then matches the sweeps bit for
+// bit).  Among the shapes whose group fits in the co-resident CTAs, pick
+// the smallest modelled sweep time: waves of concurrent slices times the
+// per-step time, with the per-SM load in quad-steps and a fixed per-step
+// latency for the group barrier.
+int plan(Prob& p, const Device& dev) {
+  const int max_nq = p.esz == 4 ? 8 : 4;
+  int occ_of[kMaxNQ + 1] = {0};
+  for (int nq = 1; nq <= max_nq; ++nq) {
+    int occ = 0;
+    const void* fn = fine_kernel(p.d.precision, nq, p.mult);
+    if (fn == nullptr) return MMP_ERR_UNSUPPORTED;
+    MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, 0));
+    occ_of[nq] = occ;
+  }
+  const double quad_rate = p.esz == 4 ? 0.8 : 0.02;  // quad-steps per cycle per SM
+  double best = INFINITY;
+  int best_nq = 0, best_G = 0, best_slots = 0;
+  const int N = p.d.N;
+  const int g_max = std::min<long long>((long long)dev.sms * 32, p.Q);
+  for (int G = 1; G <= g_max; ++G) {
+    const long long qpc = (p.Q + G - 1) / G;
+    const int nq = (int)std::max<long long>(1, (qpc + kTPB - 1) / kTPB);
+    if (nq > max_nq || occ_of[nq] < 1) continue;
+    const int S = dev.sms * occ_of[nq];
+    if (G > S) continue;
+    const int slots = std::min(N, S / G);
+    const int waves = (N + slots - 1) / slots;
+    const int per_sm = (slots * G + dev.sms - 1) / dev.sms;
+    const double step = per_sm * (double)kTPB * nq / quad_rate + (G > 1 ? 2500.0 : 400.0);
+    const double cost = waves * step;
+    if (cost < best * (1 - 1e-12)) {
+      best = cost;
+      best_nq = nq;
+      best_G = G;
+      best_slots = S / G;
+    }
+  }
+  if (best_G == 0) return MMP_ERR_UNSUPPORTED;
+  p.nq = best_nq;
+  p.G = best_G;
+  p.slots_max = best_slots;
+  return MMP_OK;
+}
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    const size_t at = off;
+    off += bytes;
+    return at;
+  }
+};
+
+// Lays out (or, with base == nullptr, sizes) one problem's workspace.
+size_t layout(Prob& p, char* base, size_t start) {
+  Carver c{base, start};
+  const int N = p.d.N;
+  const size_t row = (size_t)p.pitch * p.esz;
+  auto ptr = [&](size_t bytes) -> char* {
+    const size_t at = c.take(bytes);
+    return base ? base + at : nullptr;
+  };
+  p.u0 = ptr(row);
+  p.B[0] = ptr(row * N);
+  p.B[1] = ptr(row * N);
+  p.S[0] = ptr(row);
+  p.S[1] = ptr(row);
+  p.stats = (double*)ptr(sizeof(double) * kStat * N);
+  p.stats_u0 = (double*)ptr(sizeof(double) * kStat);
+  p.ser_stats = (double*)ptr(sizeof(double) * kStat * (N + 1));
+  p.tmp_stats = (double*)ptr(sizeof(double) * kStat);
+  p.rho = (double*)ptr(sizeof(double) * kMom * (N + 1));
+  p.cache = (double*)ptr(sizeof(double) * 4 * N);
+  p.aff = (double*)ptr(sizeof(double) * 2 * kAff * (N + 1));
+  p.ctl = (double*)ptr(sizeof(double) * 16);
+  p.partials = (double*)ptr(sizeof(double) * 2 * kNV * (size_t)p.slots_max * p.G);
+  p.counters = (unsigned*)ptr(sizeof(unsigned) * p.slots_max);
+  p.status = (unsigned*)ptr(sizeof(unsigned) * 4);
+  return c.off;
+}
+
+unsigned long long wait_limit_ns() {
+  const char* e = std::getenv("MMP_WAIT_LIMIT_MS");
+  const double ms = e ? std::atof(e) : 5000.0;
+  return (unsigned long long)(std::max(1.0, ms) * 1e6);
+}
+
+}  // namespace
+
+struct mmp_ctx {
+  std::vector<Prob> probs;
+  cudaStream_t stream = nullptr;
+  Device dev;
+  unsigned long long limit_ns = 0;
+  std::vector<double> host_ctl;
+  // device-time accounting of the fine kernel (events on `stream`)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  double fine_ms = 0.0, fine_steps = 0.0;
+  long long fine_launches = 0, other_launches = 0;
+  ~mmp_ctx() {
+    for (auto& pr : pending) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+int prepare(const mmp_problem_desc* descs, int n, std::vector<Prob>& probs, Device& dev) {
+  if (descs == nullptr || n < 1) return MMP_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const int v = validate(descs[i]);
+    if (v) return v;
+  }
+  int rc = query_device(dev);
+  if (rc) return rc;
+  probs.resize(n);
+  for (int i = 0; i < n; ++i) {
+    probs[i].d = descs[i];
+    derive(probs[i]);
+    rc = plan(probs[i], dev);
+    if (rc) return rc;
+  }
+  return MMP_OK;
+}
+
+// One launch of the fused fine kernel over slices [slice_begin, slice_begin + n_tasks).
+int run_fine(mmp_ctx* c, Prob& p, int slice_begin, int n_tasks, int nf, const void* src0, const void* src,
+             void* dst, int dst_fixed, const double* aff, int aff_fixed, double* stats, int stats_fixed) {
+  if (n_tasks < 1) return MMP_OK;
+  FineArgs a;
+  const mmp_problem_desc& d = p.d;
+  a.nc3 = -d.c3; a.c1 = d.c1; a.kappa = d.kappa; a.c0 = d.c0;
+  a.B = d.B; a.BE = d.BE; a.B0 = d.B0;
+  a.h = p.h; a.sqrt_h = p.sqrt_h; a.nf = nf;
+  a.P = d.P; a.Q = p.Q; a.pitch = p.pitch;
+  a.n_regions = p.I; a.thr = d.threshold;
+  a.key0 = p.key0; a.key1 = p.key1; a.ptag = d.problem_tag;
+  a.slice_begin = slice_begin; a.n_tasks = n_tasks;
+  a.src0 = src0; a.src = src; a.dst = dst; a.dst_fixed = dst_fixed;
+  a.aff = aff; a.aff_fixed = aff_fixed;
+  a.stats = stats; a.stats_fixed = stats_fixed;
+  a.G = p.G;
+  a.partials = p.partials; a.counters = p.counters; a.status = p.status;
+  a.wait_limit_ns = c->limit_ns;
+  const int slots = std::min(n_tasks, p.slots_max);
+  MMP_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(unsigned) * slots, c->stream));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->timing) {
+    for (cudaEvent_t* e : {&e0, &e1}) {
+      if (!c->ev_pool.empty()) {
+        *e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+      } else {
+        MMP_CUDA(cudaEventCreate(e));
+      }
+    }
+    MMP_CUDA(cudaEventRecord(e0, c->stream));
+  }
+  MMP_CUDA(launch_fine(d.precision, p.nq, p.mult, slots * p.G, a, c->stream));
+  if (c->timing) {
+    MMP_CUDA(cudaEventRecord(e1, c->stream));
+    c->pending.emplace_back(e0, e1);
+  }
+  c->fine_launches += 1;
+  c->fine_steps += (double)n_tasks * (double)d.P * (double)nf;
+  return MMP_OK;
+}
+
+// Folds finished event pairs into the fine-kernel time (after a stream sync).
+int collect_timing(mmp_ctx* c) {
+  for (auto& pr : c->pending) {
+    float ms = 0.0f;
+    MMP_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    c->fine_ms += ms;
+    c->ev_pool.push_back(pr.first);
+    c->ev_pool.push_back(pr.second);
+  }
+  c->pending.clear();
+  return MMP_OK;
+}
+
+int run_driver(mmp_ctx* c, Prob& p, int sweep) {
+  DriverArgs a;
+  const mmp_problem_desc& d = p.d;
+  a.nc3 = -d.c3; a.c1 = d.c1; a.kappa = d.kappa; a.c0 = d.c0;
+  a.B = d.B; a.BE = d.BE; a.B0 = d.B0;
+  a.N = d.N; a.I = p.I; a.variant = d.variant; a.precision = d.precision;
+  a.dT = p.dT; a.hc = p.hc; a.nc = p.nc; a.thr = d.threshold; a.P = d.P;
+  a.tol = d.tol; a.max_sweeps = p.max_sweeps;
+  a.stats = p.stats; a.stats_u0 = p.stats_u0; a.rho = p.rho; a.cache = p.cache; a.aff = p.aff;
+  a.ctl = p.ctl; a.status = p.status; a.sweep = sweep;
+  MMP_CUDA(launch_driver(a, c->stream));
+  c->other_launches += 1;
+  return MMP_OK;
+}
+
+int status_to_error(unsigned s) {
+  if (s & kStatusTimeout) return MMP_ERR_TIMEOUT;
+  if (s & kStatusNumeric) return MMP_ERR_NUMERIC;
+  return MMP_OK;
+}
+
+int check_prob(mmp_ctx* c, int prob) {
+  if (c == nullptr || prob < 0 || prob >= (int)c->probs.size()) return MMP_ERR_INVALID_ARG;
+  return MMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mmp_strerror(int code) {
+  switch (code) {
+    case MMP_OK: return "ok";
+    case MMP_ERR_INVALID_ARG: return "invalid argument";
+    case MMP_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case MMP_ERR_UNSUPPORTED: return "unsupported configuration";
+    case MMP_ERR_CUDA: return "CUDA error";
+    case MMP_ERR_NUMERIC: return "non-finite value or negative variance on the device";
+    case MMP_ERR_TIMEOUT: return "a bounded device-side wait gave up";
+    case MMP_ERR_STATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+int mmp_version(void) { return 100; }
+
+int mmp_last_cuda_error(void) { return g_last_cuda_error; }
+
+int mmp_workspace_size(const mmp_problem_desc* descs, int n_problems, size_t* bytes) {
+  if (bytes == nullptr) return MMP_ERR_INVALID_ARG;
+  std::vector<Prob> probs;
+  Device dev;
+  const int rc = prepare(descs, n_problems, probs, dev);
+  if (rc) return rc;
+  size_t off = 0;
+  for (Prob& p : probs) off = layout(p, nullptr, off);
+  *bytes = (off + kAlign - 1) / kAlign * kAlign;
+  return MMP_OK;
+}
+
+int mmp_create(mmp_ctx** out, const mmp_problem_desc* descs, int n_problems, void* workspace,
+               size_t workspace_bytes, void* stream) {
+  if (out == nullptr) return MMP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (workspace == nullptr || ((uintptr_t)workspace % kAlign) != 0) return MMP_ERR_WORKSPACE;
+  mmp_ctx* c = new (std::nothrow) mmp_ctx();
+  if (c == nullptr) return MMP_ERR_INVALID_ARG;
+  int rc = prepare(descs, n_problems, c->probs, c->dev);
+  if (rc) {
+    delete c;
+    return rc;
+  }
+  size_t off = 0;
+  for (Prob& p : c->probs) off = layout(p, (char*)workspace, off);
+  if (off > workspace_bytes) {
+    delete c;
+    return MMP_ERR_WORKSPACE;
+  }
+  c->stream = (cudaStream_t)stream;
+  c->limit_ns = wait_limit_ns();
+  c->host_ctl.assign(16, 0.0);
+  for (Prob& p : c->probs) {
+    cudaError_t e = cudaMemsetAsync(p.status, 0, sizeof(unsigned) * 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.ctl, 0, sizeof(double) * 16, c->stream);
+    if (e == cudaSuccess)
+      e = launch_init_u0(p.d.precision, p.u0, p.d.P, p.Q, p.d.m0, p.d.s0, p.key0, p.key1,
+                         p.d.problem_tag, c->stream);
+    c->other_launches += 1;
+    if (e != cudaSuccess) {
+      delete c;
+      return cuda_fail(e);
+    }
+  }
+  *out = c;
+  return MMP_OK;
+}
+
+int mmp_destroy(mmp_ctx* ctx) {
+  delete ctx;
+  return MMP_OK;
+}
+
+int mmp_set_initial(mmp_ctx* ctx, int prob, const void* u0, int from_host) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  if (u0 == nullptr) return MMP_ERR_INVALID_ARG;
+  Prob& p = ctx->probs[prob];
+  const size_t bytes = (size_t)p.d.P * p.esz;
+  MMP_CUDA(cudaMemcpyAsync(p.u0, u0, bytes, from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+  if (from_host) MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  p.lifted = false;
+  p.sweeps = 0;
+  p.done = false;
+  return MMP_OK;
+}
+
+int mmp_lift(mmp_ctx* ctx) {
+  if (ctx == nullptr) return MMP_ERR_INVALID_ARG;
+  for (Prob& p : ctx->probs) {
+    int rc = run_fine(ctx, p, 0, 1, 0, p.u0, nullptr, nullptr, 0, nullptr, 0, p.stats_u0, 1);
+    if (rc) return rc;
+    rc = run_driver(ctx, p, 0);
+    if (rc) return rc;
+    p.lifted = true;
+    p.sweeps = 0;
+    p.done = false;
+    p.converged = false;
+    p.last_change = 0.0;
+    std::fill(p.out_buf.begin(), p.out_buf.end(), -1);
+  }
+  return MMP_OK;
+}
+
+int mmp_iterate(mmp_ctx* ctx, int n_iter, int* all_converged) {
+  if (ctx == nullptr || n_iter < 0) return MMP_ERR_INVALID_ARG;
+  for (Prob& p : ctx->probs)
+    if (!p.lifted) return MMP_ERR_STATE;
+  for (int it = 0; it < n_iter; ++it) {
+    bool any = false;
+    for (Prob& p : ctx->probs) {
+      if (p.done) continue;
+      const int k = p.sweeps + 1;
+      const int first = k - 1;  // slices before k - 1 are exact (Property 3.3)
+      const char* src = k == 1 ? nullptr : p.B[(k - 1) & 1];
+      int rc = run_fine(ctx, p, first, p.d.N - first, p.nf, p.u0, src, p.B[k & 1], 0, p.aff, 0, p.stats, 0);
+      if (rc) return rc;
+      rc = run_driver(ctx, p, k);
+      if (rc) return rc;
+      any = true;
+    }
+    if (!any) break;
+    MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+    {
+      const int trc = collect_timing(ctx);
+      if (trc) return trc;
+    }
+    for (Prob& p : ctx->probs) {
+      if (p.done) continue;
+      double ctl[16];
+      unsigned st[4];
+      MMP_CUDA(cudaMemcpy(ctl, p.ctl, sizeof(ctl), cudaMemcpyDeviceToHost));
+      MMP_CUDA(cudaMemcpy(st, p.status, sizeof(st), cudaMemcpyDeviceToHost));
+      const int k = p.sweeps + 1;
+      for (int n = k - 1; n < p.d.N; ++n) p.out_buf[n] = k & 1;
+      p.sweeps = k;
+      p.last_change = ctl[0];
+      p.converged = ctl[1] != 0.0 || k == p.d.N;
+      p.done = ctl[3] != 0.0;
+      const int err = status_to_error(st[0]);
+      if (err) return err;
+    }
+  }
+  if (all_converged) {
+    bool all = true;
+    for (Prob& p : ctx->probs) all = all && p.done;
+    *all_converged = all ? 1 : 0;
+  }
+  return MMP_OK;
+}
+
+int mmp_run(mmp_ctx* ctx, int* sweeps_out) {
+  int rc = mmp_lift(ctx);
+  if (rc) return rc;
+  int all = 0;
+  while (!all) {
+    rc = mmp_iterate(ctx, 1, &all);
+    if (rc) return rc;
+  }
+  if (sweeps_out) {
+    int m = 0;
+    for (Prob& p : ctx->probs) m = std::max(m, p.sweeps);
+    *sweeps_out = m;
+  }
+  return MMP_OK;
+}
+
+int mmp_status(mmp_ctx* ctx, int prob, int* sweeps, int* converged, double* last_change, int* dev_err) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  Prob& p = ctx->probs[prob];
+  unsigned st[4] = {0, 0, 0, 0};
+  MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  MMP_CUDA(cudaMemcpy(st, p.status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (sweeps) *sweeps = p.sweeps;
+  if (converged) *converged = p.converged ? 1 : 0;
+  if (last_change) *last_change = p.last_change;
+  if (dev_err) *dev_err = status_to_error(st[0]);
+  return MMP_OK;
+}
+
+int mmp_get_moments(mmp_ctx* ctx, int prob, double* out) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  if (out == nullptr) return MMP_ERR_INVALID_ARG;
+  Prob& p = ctx->probs[prob];
+  if (!p.lifted) return MMP_ERR_STATE;
+  MMP_CUDA(cudaMemcpyAsync(out, p.rho, sizeof(double) * kMom * (p.d.N + 1), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+  MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return MMP_OK;
+}
+
+int mmp_get_particles(mmp_ctx* ctx, int prob, int n, void* dst, int to_host) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  Prob& p = ctx->probs[prob];
+  if (dst == nullptr || n < 0 || n > p.d.N) return MMP_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)p.d.P * p.esz;
+  const cudaMemcpyKind kind = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (n == 0) {
+    MMP_CUDA(cudaMemcpyAsync(dst, p.u0, bytes, kind, ctx->stream));
+  } else {
+    if (!p.lifted) return MMP_ERR_STATE;
+    const int buf = p.sweeps == 0 ? -1 : p.out_buf[n - 1];
+    const char* src = buf < 0 ? nullptr : p.B[buf];
+    rc = run_fine(ctx, p, n, 1, 0, p.u0, src, p.S[0], 1, p.aff, 0, p.tmp_stats, 1);
+    if (rc) return rc;
+    MMP_CUDA(cudaMemcpyAsync(dst, p.S[0], bytes, kind, ctx->stream));
+  }
+  if (to_host) MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return MMP_OK;
+}
+
+int mmp_fine_serial(mmp_ctx* ctx, int prob, int n_end, double* stats_out, void* parts_dev) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  Prob& p = ctx->probs[prob];
+  const int N = (n_end <= 0 || n_end > p.d.N) ? p.d.N : n_end;
+  rc = run_fine(ctx, p, 0, 1, 0, p.u0, nullptr, nullptr, 0, nullptr, 0, p.ser_stats, 1);
+  if (rc) return rc;
+  for (int n = 0; n < N; ++n) {
+    const void* in = n == 0 ? (const void*)p.u0 : (const void*)p.S[(n - 1) & 1];
+    rc = run_fine(ctx, p, n, 1, p.nf, in, nullptr, p.S[n & 1], 1, nullptr, 0,
+                  p.ser_stats + (size_t)(n + 1) * kStat, 1);
+    if (rc) return rc;
+  }
+  if (parts_dev)
+    MMP_CUDA(cudaMemcpyAsync(parts_dev, p.S[(N - 1) & 1], (size_t)p.d.P * p.esz, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+  if (stats_out)
+    MMP_CUDA(cudaMemcpyAsync(stats_out, p.ser_stats, sizeof(double) * kStat * (N + 1), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+  MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  unsigned st[4];
+  MMP_CUDA(cudaMemcpy(st, p.status, sizeof(st), cudaMemcpyDeviceToHost));
+  return status_to_error(st[0]);
+}
+
+int mmp_set_timing(mmp_ctx* ctx, int on) {
+  if (ctx == nullptr) return MMP_ERR_INVALID_ARG;
+  ctx->timing = on != 0;
+  return MMP_OK;
+}
+
+int mmp_timing(mmp_ctx* ctx, int reset, double* fine_ms, long long* fine_launches,
+               double* fine_particle_steps, long long* other_launches) {
+  if (ctx == nullptr) return MMP_ERR_INVALID_ARG;
+  MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  const int rc = collect_timing(ctx);
+  if (rc) return rc;
+  if (fine_ms) *fine_ms = ctx->fine_ms;
+  if (fine_launches) *fine_launches = ctx->fine_launches;
+  if (fine_particle_steps) *fine_particle_steps = ctx->fine_steps;
+  if (other_launches) *other_launches = ctx->other_launches;
+  if (reset) {
+    ctx->fine_ms = 0.0;
+    ctx->fine_steps = 0.0;
+    ctx->fine_launches = 0;
+    ctx->other_launches = 0;
+  }
+  return MMP_OK;
+}
+
+int mmp_get_plan(mmp_ctx* ctx, int prob, int* quads_per_thread, int* ctas_per_slice,
+                 int* max_concurrent_slices) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  const Prob& p = ctx->probs[prob];
+  if (quads_per_thread) *quads_per_thread = p.nq;
+  if (ctas_per_slice) *ctas_per_slice = p.G;
+  if (max_concurrent_slices) *max_concurrent_slices = p.slots_max;
+  return MMP_OK;
+}
+
+int mmp_fine(mmp_ctx* ctx, int prob, int n, const void* u_in, void* u_out, double* stats_out) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  Prob& p = ctx->probs[prob];
+  if (u_in == nullptr || u_out == nullptr || u_in == u_out || n < 0 || n >= p.d.N) return MMP_ERR_INVALID_ARG;
+  if (((uintptr_t)u_in % 16) || ((uintptr_t)u_out % 16)) return MMP_ERR_INVALID_ARG;
+  rc = run_fine(ctx, p, n, 1, p.nf, u_in, nullptr, u_out, 1, nullptr, 0, p.tmp_stats, 1);
+  if (rc) return rc;
+  if (stats_out)
+    MMP_CUDA(cudaMemcpyAsync(stats_out, p.tmp_stats, sizeof(double) * kStat, cudaMemcpyDeviceToHost, ctx->stream));
+  MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  unsigned st[4];
+  MMP_CUDA(cudaMemcpy(st, p.status, sizeof(st), cudaMemcpyDeviceToHost));
+  return status_to_error(st[0]);
+}
+
+int mmp_philox(const unsigned int* ctr, const unsigned int* key, unsigned int* out, long long n, void* stream) {
+  if (ctr == nullptr || key == nullptr || out == nullptr || n < 0) return MMP_ERR_INVALID_ARG;
+  if (n == 0) return MMP_OK;
+  if (((uintptr_t)ctr % 16) || ((uintptr_t)out % 16)) return MMP_ERR_INVALID_ARG;
+  MMP_CUDA(launch_philox(ctr, key[0], key[1], out, n, (cudaStream_t)stream));
+  return MMP_OK;
+}
+
+int mmp_normals(const mmp_problem_desc* desc, int tag, unsigned int j, unsigned int n, long long count,
+                void* out, void* stream) {
+  if (desc == nullptr || out == nullptr || count < 0 || tag < 0 || tag > 255 || n >= (1u << 24))
+    return MMP_ERR_INVALID_ARG;
+  if (desc->precision != MMP_FP64 && desc->precision != MMP_MIXED) return MMP_ERR_INVALID_ARG;
+  if (count == 0) return MMP_OK;
+  MMP_CUDA(launch_normals(desc->precision, out, count, (uint32_t)tag, j, n, (uint32_t)(desc->seed & 0xffffffffull),
+                          (uint32_t)(desc->seed >> 32), desc->problem_tag, (cudaStream_t)stream));
+  return MMP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,44 @@
+// fine.cuh -- arguments and launch interface of the fused fine-propagator
+// kernel (matching prologue, Euler-Maruyama steps with the per-step mean
+// field, restriction epilogue).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mmp {
+
+struct FineArgs {
+  // drift a(x, m) = nc3 x^3 + c1 x + kappa m + c0 (nc3 = -c3), diffusion b = B x + BE m + B0
+  double nc3, c1, kappa, c0, B, BE, B0;
+  double h, sqrt_h;            // fine step and its square root
+  int nf;                      // steps per slice (0: matching + restriction only)
+  long long P;                 // particles
+  int Q;                       // quads = ceil(P / 4)
+  long long pitch;             // elements between slice rows (multiple of 4)
+  int n_regions;
+  double thr;
+  uint32_t key0, key1, ptag;   // Philox key and problem tag
+  int slice_begin, n_tasks;    // task t is slice slice_begin + t
+  const void* src0;            // input of slice 0, and of every slice when src == nullptr
+  const void* src;             // rows: input of slice n is row n - 1
+  void* dst;                   // output rows (nullptr: no store)
+  int dst_fixed;               // 1: every task writes row 0
+  const double* aff;           // matching records [row][2][4] (nullptr: identity)
+  int aff_fixed;
+  double* stats;               // restriction records [row][16]
+  int stats_fixed;
+  int G;                       // CTAs per slice
+  double* partials;            // [slot][2][G][kNV] group-reduction scratch
+  unsigned* counters;          // [slot] group-barrier arrival counters (zeroed per launch)
+  unsigned* status;            // device status word
+  unsigned long long wait_limit_ns;
+};
+
+// Occupancy-relevant handle of one kernel instantiation.
+const void* fine_kernel(int precision, int nq, bool mult);
+// Cooperative launch of the instantiation (grid = slots * G CTAs).
+cudaError_t launch_fine(int precision, int nq, bool mult, int grid, const FineArgs& args,
+                        cudaStream_t stream);
+
+}  // namespace mmp

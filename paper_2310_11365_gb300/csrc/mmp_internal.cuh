@@ -1,0 +1,141 @@
+// mmp_internal.cuh -- device helpers shared by the kernels of libmmp.
+//
+// Random numbers: Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), the
+// counter-based generator that lets every Parareal iteration redraw the
+// same noise (Property 3.3 needs identical draws in every iteration).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mmp.h"
+
+namespace mmp {
+
+constexpr int kTPB = 256;          // threads per block of the fine kernel
+constexpr int kWarps = kTPB / 32;
+constexpr int kNV = 8;             // values per group reduction slot
+constexpr int kStat = MMP_STAT_STRIDE;
+constexpr int kMom = MMP_MOMENT_STRIDE;
+constexpr int kAff = 4;            // doubles per (slice, region) matching record
+constexpr int kMaxNQ = 8;          // largest quads-per-thread template
+
+// Device status bits (or-ed into the status word).
+constexpr unsigned kStatusTimeout = 1u;
+constexpr unsigned kStatusNumeric = 2u;
+constexpr unsigned kStatusRegionFlip = 4u;
+
+// Matching modes of a (slice, region) record {mode, a, b, c}:
+//   identity: x unchanged
+//   affine:   x + (a + b (x - c)), a = mu - E u, b = sqrt(sigma / V u) - 1, c = E u
+//   redraw:   a + b xi (tag-2 draw), a = mu, b = sqrt(sigma)       (V u = 0)
+constexpr int kMatchIdentity = 0;
+constexpr int kMatchAffine = 1;
+constexpr int kMatchRedraw = 2;
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10.  One round maps (c0, c1, c2, c3) with key (k0, k1) to
+//   (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0));
+// the key advances by the Weyl increments (W0, W1) between rounds.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t rk0 = k0 + (uint32_t)r * kPhiloxW0;
+    const uint32_t rk1 = k1 + (uint32_t)r * kPhiloxW1;
+    const uint32_t lo0 = kPhiloxM0 * c.x, hi0 = __umulhi(kPhiloxM0, c.x);
+    const uint32_t lo1 = kPhiloxM1 * c.z, hi1 = __umulhi(kPhiloxM1, c.z);
+    c = make_uint4(hi1 ^ c.y ^ rk0, lo1, hi0 ^ c.w ^ rk1, lo0);
+  }
+  return c;
+}
+
+// Uniform u = ((o >> 9) + 1/2) 2^-23 in (0, 1).
+// float: the bit pattern 1.m with m = o >> 9 is 1 + (o >> 9) 2^-23; subtracting
+// 1 - 2^-24 is exact (Sterbenz) and lands on the same grid point.
+__device__ __forceinline__ float uniform_f(uint32_t o) {
+  return __uint_as_float(0x3F800000u | (o >> 9)) - 0x1.fffffep-1f;
+}
+__device__ __forceinline__ double uniform_d(uint32_t o) {
+  return fma((double)(o >> 9), 0x1p-23, 0x1p-24);
+}
+
+// Box-Muller: z = sqrt(-2 ln ua) (cos 2 pi ub, sin 2 pi ub).
+__device__ __forceinline__ void box_muller(float ua, float ub, float& z0, float& z1) {
+  const float r = sqrtf(-2.0f * logf(ua));
+  float s, c;
+  sincospif(2.0f * ub, &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+__device__ __forceinline__ void box_muller(double ua, double ub, double& z0, double& z1) {
+  const double r = sqrt(-2.0 * log(ua));
+  double s, c;
+  sincospi(2.0 * ub, &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+template <typename R>
+__device__ __forceinline__ void normals4(uint4 o, R z[4]);
+template <>
+__device__ __forceinline__ void normals4<float>(uint4 o, float z[4]) {
+  box_muller(uniform_f(o.x), uniform_f(o.y), z[0], z[1]);
+  box_muller(uniform_f(o.z), uniform_f(o.w), z[2], z[3]);
+}
+template <>
+__device__ __forceinline__ void normals4<double>(uint4 o, double z[4]) {
+  box_muller(uniform_d(o.x), uniform_d(o.y), z[0], z[1]);
+  box_muller(uniform_d(o.z), uniform_d(o.w), z[2], z[3]);
+}
+
+// Counter of the draw for particle quad q under (tag, step j, slice n).
+__device__ __forceinline__ uint4 rng_counter(uint32_t q, uint32_t j, uint32_t n, uint32_t tag,
+                                             uint32_t problem_tag) {
+  return make_uint4(q, j, n | (tag << 24), problem_tag);
+}
+
+// ---------------------------------------------------------------------------
+// Matching T (Eq. multimodal_M), affine branch written as
+//   x + (delta + sm1 (x - m)),  delta = mu - E u,  sm1 = sqrt(sigma / V u) - 1,
+// so that delta = sm1 = 0 (T(S u, u), Lemma 3.1) returns x bit for bit.
+// The same function decides acceptance in the driver (Def. 3.2's
+// fractions-unchanged test), so the test and the move agree to the bit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float apply_affine(float x, float delta, float sm1, float m) {
+  return __fadd_rn(x, __fmaf_rn(sm1, __fsub_rn(x, m), delta));
+}
+__device__ __forceinline__ double apply_affine(double x, double delta, double sm1, double m) {
+  return __dadd_rn(x, __fma_rn(sm1, __dsub_rn(x, m), delta));
+}
+
+// ---------------------------------------------------------------------------
+// Memory-model helpers for the cross-CTA group barrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Two-sum of floats (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+}  // namespace mmp

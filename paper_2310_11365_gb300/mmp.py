@@ -1,0 +1,313 @@
+"""Thin Python binding of libmmp.so (C-ABI in include/mmp.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch supplies device memory (the workspace and any
+ensembles) and the stream.  There is no fallback: if libmmp.so is missing
+or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmmp.so")
+
+MMP_OK = 0
+MMP_FP64, MMP_MIXED = 0, 1
+MMP_UNIMODAL, MMP_MULTIMODAL, MMP_LEARNING = 0, 1, 2
+MOMENT_STRIDE = 8
+STAT_STRIDE = 16
+
+ERRORS = {
+    -1: "MMP_ERR_INVALID_ARG", -2: "MMP_ERR_WORKSPACE", -3: "MMP_ERR_UNSUPPORTED",
+    -4: "MMP_ERR_CUDA", -5: "MMP_ERR_NUMERIC", -6: "MMP_ERR_TIMEOUT", -7: "MMP_ERR_STATE",
+}
+
+EXPORTED = [
+    "mmp_strerror", "mmp_version", "mmp_last_cuda_error", "mmp_workspace_size", "mmp_create",
+    "mmp_destroy", "mmp_set_initial", "mmp_lift", "mmp_iterate", "mmp_run", "mmp_status",
+    "mmp_get_moments", "mmp_get_particles", "mmp_fine_serial", "mmp_fine", "mmp_philox",
+    "mmp_normals", "mmp_get_plan", "mmp_set_timing", "mmp_timing",
+]
+
+
+class MMPError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        name = ERRORS.get(code, str(code))
+        msg = _lib.mmp_strerror(code).decode() if _lib is not None else name
+        extra = ""
+        if code == -4 and _lib is not None:
+            extra = f" (cuda error {_lib.mmp_last_cuda_error()})"
+        super().__init__(f"{where}: {name}: {msg}{extra}")
+        self.code = code
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [
+        ("c3", C.c_double), ("c1", C.c_double), ("kappa", C.c_double), ("c0", C.c_double),
+        ("B", C.c_double), ("BE", C.c_double), ("B0", C.c_double),
+        ("m0", C.c_double), ("s0", C.c_double),
+        ("T", C.c_double), ("N", C.c_int), ("dt", C.c_double), ("P", C.c_longlong),
+        ("coarse_h", C.c_double), ("n_regions", C.c_int), ("threshold", C.c_double),
+        ("variant", C.c_int), ("precision", C.c_int), ("seed", C.c_ulonglong),
+        ("problem_tag", C.c_uint), ("tol", C.c_double), ("max_iter", C.c_int),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libmmp.so (building nothing); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libmmp.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i, ll, d = C.c_void_p, C.c_int, C.c_longlong, C.POINTER(C.c_double)
+    pd = C.POINTER(ProblemDesc)
+    sig = {
+        "mmp_strerror": ([i], C.c_char_p),
+        "mmp_version": ([], i),
+        "mmp_last_cuda_error": ([], i),
+        "mmp_workspace_size": ([pd, i, C.POINTER(C.c_size_t)], i),
+        "mmp_create": ([C.POINTER(vp), pd, i, vp, C.c_size_t, vp], i),
+        "mmp_destroy": ([vp], i),
+        "mmp_set_initial": ([vp, i, vp, i], i),
+        "mmp_lift": ([vp], i),
+        "mmp_iterate": ([vp, i, C.POINTER(i)], i),
+        "mmp_run": ([vp, C.POINTER(i)], i),
+        "mmp_status": ([vp, i, C.POINTER(i), C.POINTER(i), d, C.POINTER(i)], i),
+        "mmp_get_moments": ([vp, i, d], i),
+        "mmp_get_particles": ([vp, i, i, vp, i], i),
+        "mmp_fine_serial": ([vp, i, i, d, vp], i),
+        "mmp_fine": ([vp, i, i, vp, vp, d], i),
+        "mmp_philox": ([vp, C.POINTER(C.c_uint), vp, ll, vp], i),
+        "mmp_normals": ([pd, i, C.c_uint, C.c_uint, ll, vp, vp], i),
+        "mmp_get_plan": ([vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(i)], i),
+        "mmp_set_timing": ([vp, i], i),
+        "mmp_timing": ([vp, i, d, C.POINTER(ll), d, C.POINTER(ll)], i),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != MMP_OK:
+        raise MMPError(rc, where)
+
+
+def desc(p: workloads.Problem) -> ProblemDesc:
+    prec = MMP_MIXED if p.precision == "mixed" else MMP_FP64
+    return ProblemDesc(p.c3, p.c1, p.kappa, p.c0, p.B, p.BE, p.B0, p.m0, p.s0, p.T, p.N, p.dt, p.P,
+                       p.coarse_h, p.n_regions, p.threshold, p.variant, prec, p.seed, p.problem_tag,
+                       p.tol, p.max_iter)
+
+
+def _descs(problems) -> C.Array:
+    arr = (ProblemDesc * len(problems))()
+    for k, p in enumerate(problems):
+        arr[k] = desc(p)
+    return arr
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+# ---- one Python function per C entry point --------------------------------
+
+def mmp_strerror(code: int) -> str:
+    return load().mmp_strerror(code).decode()
+
+
+def mmp_version() -> int:
+    return load().mmp_version()
+
+
+def mmp_workspace_size(problems) -> int:
+    arr = _descs(problems)
+    n = C.c_size_t()
+    _check(load().mmp_workspace_size(arr, len(problems), C.byref(n)), "mmp_workspace_size")
+    return n.value
+
+
+def mmp_create(problems, workspace_ptr: int, workspace_bytes: int, stream=None) -> C.c_void_p:
+    arr = _descs(problems)
+    ctx = C.c_void_p()
+    _check(load().mmp_create(C.byref(ctx), arr, len(problems), C.c_void_p(workspace_ptr), workspace_bytes,
+                             C.c_void_p(_stream_handle(stream))), "mmp_create")
+    return ctx
+
+
+def mmp_destroy(ctx) -> None:
+    _check(load().mmp_destroy(ctx), "mmp_destroy")
+
+
+def mmp_set_initial(ctx, prob: int, u0_ptr: int, from_host: bool) -> None:
+    _check(load().mmp_set_initial(ctx, prob, C.c_void_p(u0_ptr), int(from_host)), "mmp_set_initial")
+
+
+def mmp_lift(ctx) -> None:
+    _check(load().mmp_lift(ctx), "mmp_lift")
+
+
+def mmp_iterate(ctx, n_iter: int) -> bool:
+    done = C.c_int()
+    _check(load().mmp_iterate(ctx, n_iter, C.byref(done)), "mmp_iterate")
+    return bool(done.value)
+
+
+def mmp_run(ctx) -> int:
+    k = C.c_int()
+    _check(load().mmp_run(ctx, C.byref(k)), "mmp_run")
+    return k.value
+
+
+def mmp_status(ctx, prob: int) -> dict:
+    s, c, e = C.c_int(), C.c_int(), C.c_int()
+    ch = C.c_double()
+    _check(load().mmp_status(ctx, prob, C.byref(s), C.byref(c), C.byref(ch), C.byref(e)), "mmp_status")
+    return {"sweeps": s.value, "converged": bool(c.value), "last_change": ch.value, "dev_err": e.value}
+
+
+def mmp_get_moments(ctx, prob: int, N: int) -> np.ndarray:
+    out = np.empty((N + 1) * MOMENT_STRIDE, np.float64)
+    _check(load().mmp_get_moments(ctx, prob, out.ctypes.data_as(C.POINTER(C.c_double))), "mmp_get_moments")
+    return out.reshape(N + 1, MOMENT_STRIDE)
+
+
+def mmp_get_particles(ctx, prob: int, n: int, dst_ptr: int, to_host: bool) -> None:
+    _check(load().mmp_get_particles(ctx, prob, n, C.c_void_p(dst_ptr), int(to_host)), "mmp_get_particles")
+
+
+def mmp_fine_serial(ctx, prob: int, n_end: int, parts_ptr: int | None = None) -> np.ndarray:
+    out = np.empty((n_end + 1) * STAT_STRIDE, np.float64)
+    _check(load().mmp_fine_serial(ctx, prob, n_end, out.ctypes.data_as(C.POINTER(C.c_double)),
+                                  C.c_void_p(parts_ptr or 0)), "mmp_fine_serial")
+    return out.reshape(n_end + 1, STAT_STRIDE)
+
+
+def mmp_fine(ctx, prob: int, n: int, u_in_ptr: int, u_out_ptr: int) -> np.ndarray:
+    out = np.empty(STAT_STRIDE, np.float64)
+    _check(load().mmp_fine(ctx, prob, n, C.c_void_p(u_in_ptr), C.c_void_p(u_out_ptr),
+                           out.ctypes.data_as(C.POINTER(C.c_double))), "mmp_fine")
+    return out
+
+
+def mmp_get_plan(ctx, prob: int) -> dict:
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    _check(load().mmp_get_plan(ctx, prob, C.byref(a), C.byref(b), C.byref(c)), "mmp_get_plan")
+    return {"quads_per_thread": a.value, "ctas_per_slice": b.value, "max_concurrent_slices": c.value}
+
+
+def mmp_set_timing(ctx, on: bool) -> None:
+    _check(load().mmp_set_timing(ctx, int(on)), "mmp_set_timing")
+
+
+def mmp_timing(ctx, reset: bool = False) -> dict:
+    ms, steps = C.c_double(), C.c_double()
+    fl, ol = C.c_longlong(), C.c_longlong()
+    _check(load().mmp_timing(ctx, int(reset), C.byref(ms), C.byref(fl), C.byref(steps), C.byref(ol)),
+           "mmp_timing")
+    return {"fine_ms": ms.value, "fine_launches": fl.value, "fine_particle_steps": steps.value,
+            "other_launches": ol.value}
+
+
+def mmp_philox(ctr_ptr: int, key, out_ptr: int, n: int, stream=None) -> None:
+    k = (C.c_uint * 2)(int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF)
+    _check(load().mmp_philox(C.c_void_p(ctr_ptr), k, C.c_void_p(out_ptr), n,
+                             C.c_void_p(_stream_handle(stream))), "mmp_philox")
+
+
+def mmp_normals(p: workloads.Problem, tag: int, j: int, n: int, count: int, out_ptr: int, stream=None) -> None:
+    dsc = desc(p)
+    _check(load().mmp_normals(C.byref(dsc), tag, j, n, count, C.c_void_p(out_ptr),
+                              C.c_void_p(_stream_handle(stream))), "mmp_normals")
+
+
+# ---- convenience wrapper ---------------------------------------------------
+
+class Solver:
+    """Owns a torch workspace and a context for a list of problems."""
+
+    def __init__(self, problems, stream=None):
+        import torch
+
+        self.problems = list(problems) if isinstance(problems, (list, tuple)) else [problems]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        nbytes = mmp_workspace_size(self.problems)
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+        self.ctx = mmp_create(self.problems, self.workspace.data_ptr(), nbytes, self.stream)
+
+    def dtype(self, prob: int = 0):
+        import torch
+        return torch.float32 if self.problems[prob].precision == "mixed" else torch.float64
+
+    def run(self) -> int:
+        return mmp_run(self.ctx)
+
+    def lift(self) -> None:
+        mmp_lift(self.ctx)
+
+    def iterate(self, n: int = 1) -> bool:
+        return mmp_iterate(self.ctx, n)
+
+    def moments(self, prob: int = 0) -> np.ndarray:
+        return mmp_get_moments(self.ctx, prob, self.problems[prob].N)
+
+    def plan(self, prob: int = 0) -> dict:
+        return mmp_get_plan(self.ctx, prob)
+
+    def status(self, prob: int = 0) -> dict:
+        return mmp_status(self.ctx, prob)
+
+    def particles(self, n: int, prob: int = 0):
+        import torch
+        out = torch.empty(self.problems[prob].P + 4, dtype=self.dtype(prob), device="cuda")
+        mmp_get_particles(self.ctx, prob, n, out.data_ptr(), False)
+        torch.cuda.current_stream().synchronize()
+        return out[: self.problems[prob].P]
+
+    def serial(self, prob: int = 0, n_end: int | None = None, want_last: bool = False):
+        """Serial reference through slice end n_end (default N): restriction
+        records of u_0..u_{n_end}, and u_{n_end} itself if want_last."""
+        import torch
+        n_end = self.problems[prob].N if n_end is None else n_end
+        last = None
+        if want_last:
+            last = torch.empty(self.problems[prob].P + 4, dtype=self.dtype(prob), device="cuda")
+        st = mmp_fine_serial(self.ctx, prob, n_end, last.data_ptr() if last is not None else None)
+        return (st, last[: self.problems[prob].P]) if want_last else st
+
+    def set_initial(self, u0, prob: int = 0) -> None:
+        import torch
+        if isinstance(u0, torch.Tensor) and u0.is_cuda:
+            mmp_set_initial(self.ctx, prob, u0.data_ptr(), False)
+        else:
+            arr = np.ascontiguousarray(u0, dtype=np.float32 if self.problems[prob].precision == "mixed" else np.float64)
+            mmp_set_initial(self.ctx, prob, arr.ctypes.data, True)
+
+    def close(self) -> None:
+        if self.ctx is not None:
+            mmp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -18,3 +18,14 @@ def orc():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def mmplib():
+    """The native library, built in-tree if out of date.  Never a fallback:
+    if it cannot be built or loaded the tests fail."""
+    from paper_2310_11365_gb300 import build, mmp
+
+    build.build()
+    mmp.load()
+    return mmp

@@ -1,0 +1,59 @@
+"""The C-ABI library loads and exports every symbol include/mmp.h declares;
+host-side argument checks reject bad descriptors before any CUDA call."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2310_11365_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "mmp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mmp_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(mmplib):
+    lib = C.CDLL(mmplib.LIB_PATH)
+    names = _declared()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(mmplib.EXPORTED)
+
+
+def test_strerror_and_version(mmplib):
+    assert mmplib.mmp_version() >= 100
+    assert mmplib.mmp_strerror(0) == "ok"
+    for code in range(-7, 0):
+        assert mmplib.mmp_strerror(code) not in ("ok", "unknown error")
+
+
+@pytest.mark.parametrize("bad", [
+    dict(N=0), dict(N=70000), dict(P=0), dict(T=-1.0), dict(dt=0.0), dict(coarse_h=0.0),
+    dict(n_regions=3), dict(variant=7), dict(s0=-0.1), dict(c3=float("nan")), dict(tol=-1.0),
+])
+def test_invalid_descriptor_rejected_on_host(mmplib, bad):
+    p = W.config1(**bad)
+    with pytest.raises(mmplib.MMPError) as e:
+        mmplib.mmp_workspace_size([p])
+    assert e.value.code == -1
+
+
+def test_bad_precision_rejected(mmplib):
+    d = mmplib.desc(W.config1())
+    d.precision = 5
+    n = C.c_size_t()
+    assert mmplib.load().mmp_workspace_size(C.byref(d), 1, C.byref(n)) == -1
+
+
+def test_null_arguments(mmplib):
+    lib = mmplib.load()
+    assert lib.mmp_workspace_size(None, 1, None) == -1
+    assert lib.mmp_create(None, None, 0, None, 0, None) == -1
+    assert lib.mmp_lift(None) == -1
+    assert lib.mmp_status(None, 0, None, None, None, None) == -1

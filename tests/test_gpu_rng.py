@@ -1,0 +1,94 @@
+"""GPU generator parity: Philox words against cuRAND's device Philox and the
+oracle (bit-exact); normals against the oracle's FP64 Box-Muller."""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2310_11365_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def curand_probe(tmp_path_factory):
+    from paper_2310_11365_gb300 import build
+
+    out = tmp_path_factory.mktemp("probe") / "libcurand_probe.so"
+    subprocess.check_call([build.nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-shared",
+                           "-Xcompiler", "-fPIC", "-cudart", "shared",
+                           os.path.join(ROOT, "tests", "probes", "curand_philox.cu"), "-o", str(out)])
+    lib = C.CDLL(str(out))
+    lib.curand_philox_ref.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    return lib
+
+
+def test_philox_bit_exact_vs_curand_and_oracle(mmplib, orc, curand_probe):
+    import torch
+
+    rng = np.random.default_rng(2310)
+    n = 4096
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    seed = W.SEED_BASE + 2
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
+    ref = np.zeros((n, 4), np.uint32)
+    assert curand_probe.curand_philox_ref(ctr.ctypes.data, key.ctypes.data, ref.ctypes.data, n) == 0
+    d_ctr = torch.from_numpy(ctr.view(np.int32)).cuda()
+    d_out = torch.zeros(n * 4, dtype=torch.int32, device="cuda")
+    mmplib.mmp_philox(d_ctr.data_ptr(), key, d_out.data_ptr(), n)
+    torch.cuda.synchronize()
+    got = d_out.cpu().numpy().view(np.uint32).reshape(n, 4)
+    assert np.array_equal(got, ref)
+    for i in range(0, n, 97):
+        assert np.array_equal(orc.philox(ctr[i], key), ref[i])
+
+
+def test_normals_fp64_match_oracle(mmplib, orc):
+    import torch
+
+    p = W.config2(precision="fp64")
+    count = 20_003
+    out = torch.empty(count, dtype=torch.float64, device="cuda")
+    mmplib.mmp_normals(p, 0, 7, 3, count, out.data_ptr())
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    idx = list(range(0, 64)) + list(range(count - 7, count)) + list(range(100, count, 997))
+    ref = np.array([orc.normal(p, 0, 7, 3, i) for i in idx])
+    assert np.max(np.abs(got[idx] - ref)) < 1e-13
+
+
+def test_normals_fp32_close_to_oracle(mmplib, orc):
+    import torch
+
+    p = W.config2(precision="mixed")
+    count = 4096
+    out = torch.empty(count, dtype=torch.float32, device="cuda")
+    mmplib.mmp_normals(p, 0, 11, 5, count, out.data_ptr())
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    ref = np.array([orc.normal(p, 0, 11, 5, i) for i in range(count)])
+    err = np.abs(got - ref)
+    assert np.max(err) < 4e-6
+    assert np.max(err / np.maximum(np.abs(ref), 1.0)) < 1e-6
+
+
+def test_initial_ensemble_matches_oracle(mmplib, orc):
+    import torch
+
+    from paper_2310_11365_gb300.mmp import Solver
+
+    for prec in ("fp64", "mixed"):
+        p = W.config2(P=10_001, N=2, precision=prec)
+        s = Solver(p)
+        u0 = s.particles(0).double().cpu().numpy()
+        ref = orc.initial(p)
+        if prec == "fp64":
+            assert np.max(np.abs(u0 - ref)) < 1e-14
+        else:
+            assert np.array_equal(u0, ref.astype(np.float32).astype(np.float64))
+        s.close()
