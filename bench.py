@@ -196,6 +196,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU time-to-tol comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    ap.add_argument("--N", type=int, default=None, help="override the slice count (profiling runs)")
+    ap.add_argument("--P", type=int, default=None, help="override the particle count (profiling runs)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -215,7 +218,10 @@ def main():
 
     native_build.build()
     # replicas only: every rank solves its own copy (distinct problem tag)
-    p = W.config2(problem_tag=rank)
+    overrides = {k: v for k, v in (("N", args.N), ("P", args.P)) if v is not None}
+    if "N" in overrides:
+        overrides["T"] = 8.0 * overrides["N"] / 64  # keep the slice length (n_f = 125)
+    p = W.config2(problem_tag=rank, **overrides)
     solver = mmp.Solver(p)
     mmp.mmp_set_timing(solver.ctx, True)
     plan = solver.plan()
@@ -259,7 +265,7 @@ def main():
     # end to end through the C-ABI with host buffers: u0 from pinned host
     # memory in, all moments back to host, every step
     e2e = None
-    if True:
+    if not args.no_e2e:
         dtype = np.float32
         u0_host = torch.from_numpy(solver.particles(0).cpu().numpy().astype(dtype)).pin_memory()
         out_host = np.empty((p.N + 1) * mmp.MOMENT_STRIDE, np.float64)
@@ -280,7 +286,7 @@ def main():
     # plain FP64 GPU form: time to the same tolerance (one solve)
     fp64 = None
     if not args.no_fp64:
-        p64 = W.config2(precision="fp64", problem_tag=rank)
+        p64 = W.config2(precision="fp64", problem_tag=rank, **overrides)
         s64 = mmp.Solver(p64)
         mmp.mmp_set_timing(s64.ctx, True)
         torch.cuda.synchronize()
@@ -305,7 +311,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 particles / f64 moments",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}",
+            "config": {"workload": WORKLOAD if not overrides else f"{WORKLOAD} with overrides {overrides}",
+                       "parallelism": f"replicas x{world}",
                        "precision": "mixed", "l2": "inputs larger than L2 (2 x 256 MB particle buffers)",
                        "plan": plan},
             "time_to_tol_s": ms / 1e3 / args.steps, "sweeps_to_tol": sweeps[-1],

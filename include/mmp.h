@@ -157,10 +157,12 @@ int mmp_get_particles(mmp_ctx* ctx, int prob, int n, void* dst, int to_host);
 int mmp_fine_serial(mmp_ctx* ctx, int prob, int n_end, double* stats_out, void* parts_dev);
 
 /* Launch shape chosen for problem `prob`: quads of 4 particles held per
- * thread, CTAs per slice (one group barrier spans them), and the largest
- * number of slices one launch runs concurrently.  Any pointer may be NULL. */
+ * thread, CTAs per slice (one group barrier spans them), the largest number
+ * of slices one launch runs concurrently, and whether the particles live in
+ * shared memory (1) or registers (0) between steps.  Any pointer may be
+ * NULL. */
 int mmp_get_plan(mmp_ctx* ctx, int prob, int* quads_per_thread, int* ctas_per_slice,
-                 int* max_concurrent_slices);
+                 int* max_concurrent_slices, int* particles_in_shared);
 
 /* Device-time accounting.  With timing on, the library records CUDA
  * events on the context stream around every fine-kernel launch and reads

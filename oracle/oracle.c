@@ -291,7 +291,9 @@ void orc_coarse(const orc_problem* pr, const orc_macro* in, orc_macro* out) {
  * one-step linear regression y_{n+1} = r y_n + c (r = e^{alpha dT},
  * beta = c / (1 - r)); damping lambda_0 = 1e-3 scaled by diag(J^T J),
  * /10 on an accepted step, x10 on a rejected one; at most 100 iterations;
- * stop when the accepted step is below 1e-12 relative or lambda > 1e12.
+ * stop when the accepted step is below 1e-15 relative or lambda > 1e12,
+ * then three undamped Gauss-Newton steps to land on the minimiser to
+ * rounding level.
  * The fit is rejected (no learning this sweep) unless alpha < 0 and
  * 0 <= beta <= 1.
  * ---------------------------------------------------------------------- */
@@ -354,11 +356,29 @@ int orc_lsq_fit(int n_pts, const double* t, const double* y, double p0, double d
       a = na; b = nb; cost = ncost;
       lambda /= 10.0;
       double rel = fmax(fabs(step_a) / (fabs(a) + 1e-300), fabs(step_b) / (fabs(b) + 1e-300));
-      if (rel < 1e-12) break;
+      if (rel < 1e-15) break;
     } else {
       lambda *= 10.0;
       if (lambda > 1e12) break;
     }
+  }
+  /* near the minimiser the cost stops resolving the remaining step (its
+   * change falls below rounding), so finish with undamped Gauss-Newton steps,
+   * which converge to the minimiser to rounding level */
+  for (int it = 0; it < 3; ++it) {
+    double jaa = 0, jab = 0, jbb = 0, ga = 0, gb = 0;
+    for (int n = 0; n < n_pts; ++n) {
+      double e = exp(a * t[n]);
+      double r = y[n] - (b + (p0 - b) * e);
+      double da = (p0 - b) * t[n] * e;
+      double db = 1.0 - e;
+      jaa += da * da; jab += da * db; jbb += db * db;
+      ga += da * r; gb += db * r;
+    }
+    double det = jaa * jbb - jab * jab;
+    if (!(det > 0.0) || !isfinite(det)) break;
+    a += (jbb * ga - jab * gb) / det;
+    b += (jaa * gb - jab * ga) / det;
   }
   *alpha = a;
   *beta = b;
@@ -600,4 +620,113 @@ void orc_fine_serial(const orc_problem* pr, const double* u0_in, orc_stats* stat
   }
   free(u);
   free(v);
+}
+
+/* ------------------------------------------------------------------------
+ * Adjoint of the serial fine propagator F_{N-1} o ... o F_0 (the limit the
+ * Parareal iteration reproduces, Property 3.3).  Reverse-mode
+ * differentiation of the Euler-Maruyama recursion of Sec. 1.2 with the mean
+ * field m_j = (1/P) sum_q x_{j,q}:
+ *   d x_{j+1,p} / d x_{j,q} = delta_pq (1 + h a_x(x_{j,p})) + h kappa / P,
+ *   a_x(x) = -3 c3 x^2 + c1,
+ * so with lambda_j = dL/dx_j:
+ *   lambda_{j,q} = lambda_{j+1,q} (1 + h a_x(x_{j,q})) + (h kappa / P) sum_p lambda_{j+1,p}
+ *                  + [loss at x_j]
+ * and the explicit parameter derivatives of step j are
+ *   d/dc3 = -h x^3, d/dc1 = h x, d/dkappa = h m_j, d/dc0 = h, d/dB0 = sqrt(h) xi.
+ * The loss at slice end n injects gm/P + gv (2/P)(x - M_n)
+ * (dV/dx_q = (2/P)(x_q - M) for the population variance).
+ * ---------------------------------------------------------------------- */
+int orc_adjoint(const orc_problem* pr, const double* u0_in, const double* gm, const double* gv,
+                double grad[5], double* moments) {
+  if (pr->B != 0.0 || pr->BE != 0.0) return -1;
+  const long long P = pr->P;
+  const int N = pr->N;
+  const int nf = orc_fine_steps(pr);
+  const double h = orc_fine_h(pr);
+  const double sqrt_h = sqrt(h);
+  const long long J = (long long)N * nf;
+  double* X = (double*)malloc(sizeof(double) * (size_t)P * (size_t)(J + 1));
+  double* m = (double*)malloc(sizeof(double) * (size_t)(J + 1));
+  double* lam = (double*)calloc((size_t)P, sizeof(double));
+  double* Mn = (double*)malloc(sizeof(double) * (size_t)(N + 1));
+  double* Vn = (double*)malloc(sizeof(double) * (size_t)(N + 1));
+  if (u0_in) memcpy(X, u0_in, sizeof(double) * (size_t)P);
+  else orc_initial(pr, X);
+  /* forward: the serial fine run, keeping every state and mean */
+  for (long long j = 0; j < J; ++j) {
+    const double* x = X + (size_t)j * P;
+    double* y = X + (size_t)(j + 1) * P;
+    m[j] = ensemble_mean(x, P);
+    const int n = (int)(j / nf), js = (int)(j % nf);
+    for (long long p = 0; p < P; ++p) {
+      double xi = orc_normal(pr, 0, (uint32_t)js, (uint32_t)n, p);
+      y[p] = x[p] + drift(pr, x[p], m[j]) * h + diffusion(pr, x[p], m[j]) * sqrt_h * xi;
+    }
+  }
+  m[J] = ensemble_mean(X + (size_t)J * P, P);
+  for (int n = 0; n <= N; ++n) {
+    const double* x = X + (size_t)n * nf * P;
+    double mm = ensemble_mean(x, P), vv = 0.0;
+    for (long long p = 0; p < P; ++p) vv += (x[p] - mm) * (x[p] - mm);
+    Mn[n] = mm;
+    Vn[n] = vv / (double)P;
+    if (moments) {
+      moments[2 * n] = Mn[n];
+      moments[2 * n + 1] = Vn[n];
+    }
+  }
+  /* reverse */
+  for (int k = 0; k < 5; ++k) grad[k] = 0.0;
+  for (long long j = J - 1; j >= 0; --j) {
+    if ((j + 1) % nf == 0) {
+      const int n = (int)((j + 1) / nf);
+      const double* x1 = X + (size_t)(j + 1) * P;
+      for (long long p = 0; p < P; ++p)
+        lam[p] += gm[n - 1] / (double)P + gv[n - 1] * (2.0 / (double)P) * (x1[p] - Mn[n]);
+    }
+    const double* x = X + (size_t)j * P;
+    const int n = (int)(j / nf), js = (int)(j % nf);
+    double S = 0.0;
+    for (long long p = 0; p < P; ++p) {
+      const double xv = x[p];
+      const double xi = orc_normal(pr, 0, (uint32_t)js, (uint32_t)n, p);
+      grad[0] += lam[p] * (-h * xv * xv * xv);
+      grad[1] += lam[p] * (h * xv);
+      grad[2] += lam[p] * (h * m[j]);
+      grad[3] += lam[p] * h;
+      grad[4] += lam[p] * (sqrt_h * xi);
+      S += lam[p];
+    }
+    for (long long p = 0; p < P; ++p) {
+      const double xv = x[p];
+      const double ax = -3.0 * pr->c3 * xv * xv + pr->c1;
+      lam[p] = lam[p] * (1.0 + h * ax) + (h * pr->kappa / (double)P) * S;
+    }
+  }
+  free(X); free(m); free(lam); free(Mn); free(Vn);
+  return 0;
+}
+
+int orc_adjoint_loss(const orc_problem* pr, const double* u0_in, const double* m_tgt,
+                     const double* v_tgt, double grad[5], double* loss) {
+  const int N = pr->N;
+  double* mom = (double*)malloc(sizeof(double) * 2 * (size_t)(N + 1));
+  double* gm = (double*)calloc((size_t)N, sizeof(double));
+  double* gv = (double*)calloc((size_t)N, sizeof(double));
+  /* the moments first (a zero-cotangent pass), then the cotangents of L */
+  int rc = orc_adjoint(pr, u0_in, gm, gv, grad, mom);
+  if (rc == 0) {
+    double L = 0.0;
+    for (int n = 1; n <= N; ++n) {
+      const double dm = mom[2 * n] - m_tgt[n - 1], dv = mom[2 * n + 1] - v_tgt[n - 1];
+      L += dm * dm + dv * dv;
+      gm[n - 1] = 2.0 * dm;
+      gv[n - 1] = 2.0 * dv;
+    }
+    if (loss) *loss = L;
+    rc = orc_adjoint(pr, u0_in, gm, gv, grad, NULL);
+  }
+  free(mom); free(gm); free(gv);
+  return rc;
 }

@@ -17,23 +17,37 @@ namespace mmp {
 const void* fine_kernel_f32(int nq, bool mult);
 const void* fine_kernel_f64(int nq, bool mult);
 
-const void* fine_kernel(int precision, int nq, bool mult) {
-  return precision == MMP_MIXED ? fine_kernel_f32(nq, mult) : fine_kernel_f64(nq, mult);
+const void* fine_kernel(int precision, int layout, int nq, bool mult) {
+  const int t = layout == kLayoutSmem ? 0 : nq;
+  if (layout != kLayoutSmem && nq < 1) return nullptr;
+  return precision == MMP_MIXED ? fine_kernel_f32(t, mult) : fine_kernel_f64(t, mult);
 }
 
-cudaError_t launch_fine(int precision, int nq, bool mult, int grid, const FineArgs& args,
+size_t fine_smem_bytes(int precision, int layout, int nq) {
+  if (layout != kLayoutSmem) return 0;
+  return (size_t)nq * kTPB * 4 * (precision == MMP_MIXED ? sizeof(float) : sizeof(double));
+}
+
+cudaError_t launch_fine(int precision, int layout, int nq, bool mult, int grid, const FineArgs& args,
                         cudaStream_t stream) {
-  const void* fn = fine_kernel(precision, nq, mult);
+  const void* fn = fine_kernel(precision, layout, nq, mult);
   if (fn == nullptr) return cudaErrorInvalidValue;
   FineArgs copy = args;
   void* params[] = {&copy};
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTPB), params, 0, stream);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTPB), params,
+                                     fine_smem_bytes(precision, layout, nq), stream);
 }
 }  // namespace mmp
 
 using namespace mmp;
 
 namespace {
+
+// Static shared memory of the fine kernel (its reduction state), kept out
+// of the dynamic shared-memory budget.
+struct GroupSharedBytes {
+  char bytes[1024];
+};
 
 int g_last_cuda_error = 0;
 
@@ -59,7 +73,7 @@ struct Prob {
   bool mult = false;
   uint32_t key0 = 0, key1 = 0;
   // launch plan of the fine kernel
-  int nq = 1, G = 1, slots_max = 1;
+  int layout = kLayoutRegs, nq = 1, G = 1, slots_max = 1;
   // device memory inside the caller's workspace
   char* u0 = nullptr;
   char* B[2] = {nullptr, nullptr};
@@ -127,21 +141,35 @@ void derive(Prob& p) {
   p.out_buf.assign(d.N, -1);
 }
 
-// Launch plan of the fine kernel: quads per thread (nq) and CTAs per slice
-// (G).  The group size is fixed per problem so that every launch reduces in
-// the same order (the serial reference then matches the sweeps bit for
-// bit).  Among the shapes whose group fits in the co-resident CTAs, pick
-// the smallest modelled sweep time: waves of concurrent slices times the
-// per-step time, with the per-SM load in quad-steps and a fixed per-step
-// latency for the group barrier.
+// Launch plan of the fine kernel: particle layout (registers or shared
+// memory), quads per thread (nq) and CTAs per slice (G).  The group size is
+// fixed per problem so that every launch reduces in the same order (the
+// serial reference then matches the sweeps bit for bit).  Among the shapes
+// whose group fits in the co-resident CTAs, pick the smallest modelled sweep
+// time: waves of concurrent slices times the per-step time, with the per-SM
+// load in quad-steps and a fixed per-step latency for the group barrier.
+// The layout is the shared-memory one unless MMP_FINE_LAYOUT=regs;
+// MMP_FINE_NQ=<k> restricts the choice to k quads per thread (launch-shape
+// sweeps).
 int plan(Prob& p, const Device& dev) {
-  const int max_nq = p.esz == 4 ? 8 : 4;
-  int occ_of[kMaxNQ + 1] = {0};
+  const char* env = std::getenv("MMP_FINE_LAYOUT");
+  const int layout = (env != nullptr && std::strcmp(env, "regs") == 0) ? kLayoutRegs : kLayoutSmem;
+  const char* env_nq = std::getenv("MMP_FINE_NQ");
+  const int force_nq = env_nq != nullptr ? std::atoi(env_nq) : 0;
+  const int max_nq = layout == kLayoutSmem ? (p.esz == 4 ? 32 : 16) : (p.esz == 4 ? 8 : 4);
+  int occ_of[33] = {0};
+  int smem_optin = 0;
+  MMP_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev.dev));
   for (int nq = 1; nq <= max_nq; ++nq) {
     int occ = 0;
-    const void* fn = fine_kernel(p.d.precision, nq, p.mult);
+    const void* fn = fine_kernel(p.d.precision, layout, nq, p.mult);
     if (fn == nullptr) return MMP_ERR_UNSUPPORTED;
-    MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, 0));
+    const size_t smem = fine_smem_bytes(p.d.precision, layout, nq);
+    if (smem > (size_t)smem_optin - sizeof(GroupSharedBytes)) break;
+    if (layout == kLayoutSmem)
+      MMP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    smem_optin - (int)sizeof(GroupSharedBytes)));
+    MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, smem));
     occ_of[nq] = occ;
   }
   const double quad_rate = p.esz == 4 ? 0.8 : 0.02;  // quad-steps per cycle per SM
@@ -153,6 +181,7 @@ int plan(Prob& p, const Device& dev) {
     const long long qpc = (p.Q + G - 1) / G;
     const int nq = (int)std::max<long long>(1, (qpc + kTPB - 1) / kTPB);
     if (nq > max_nq || occ_of[nq] < 1) continue;
+    if (force_nq > 0 && nq != force_nq) continue;
     const int S = dev.sms * occ_of[nq];
     if (G > S) continue;
     const int slots = std::min(N, S / G);
@@ -168,6 +197,7 @@ int plan(Prob& p, const Device& dev) {
     }
   }
   if (best_G == 0) return MMP_ERR_UNSUPPORTED;
+  p.layout = layout;
   p.nq = best_nq;
   p.G = best_G;
   p.slots_max = best_slots;
@@ -207,7 +237,7 @@ size_t layout(Prob& p, char* base, size_t start) {
   p.cache = (double*)ptr(sizeof(double) * 4 * N);
   p.aff = (double*)ptr(sizeof(double) * 2 * kAff * (N + 1));
   p.ctl = (double*)ptr(sizeof(double) * 16);
-  p.partials = (double*)ptr(sizeof(double) * 2 * kNV * (size_t)p.slots_max * p.G);
+  p.partials = (double*)ptr(sizeof(double) * 2 * (kNV + 1) * (size_t)p.slots_max * p.G);
   p.counters = (unsigned*)ptr(sizeof(unsigned) * p.slots_max);
   p.status = (unsigned*)ptr(sizeof(unsigned) * 4);
   return c.off;
@@ -279,6 +309,7 @@ int run_fine(mmp_ctx* c, Prob& p, int slice_begin, int n_tasks, int nf, const vo
   a.aff = aff; a.aff_fixed = aff_fixed;
   a.stats = stats; a.stats_fixed = stats_fixed;
   a.G = p.G;
+  a.nq = p.nq;
   a.partials = p.partials; a.counters = p.counters; a.status = p.status;
   a.wait_limit_ns = c->limit_ns;
   const int slots = std::min(n_tasks, p.slots_max);
@@ -295,7 +326,7 @@ int run_fine(mmp_ctx* c, Prob& p, int slice_begin, int n_tasks, int nf, const vo
     }
     MMP_CUDA(cudaEventRecord(e0, c->stream));
   }
-  MMP_CUDA(launch_fine(d.precision, p.nq, p.mult, slots * p.G, a, c->stream));
+  MMP_CUDA(launch_fine(d.precision, p.layout, p.nq, p.mult, slots * p.G, a, c->stream));
   if (c->timing) {
     MMP_CUDA(cudaEventRecord(e1, c->stream));
     c->pending.emplace_back(e0, e1);
@@ -613,10 +644,11 @@ int mmp_timing(mmp_ctx* ctx, int reset, double* fine_ms, long long* fine_launche
 }
 
 int mmp_get_plan(mmp_ctx* ctx, int prob, int* quads_per_thread, int* ctas_per_slice,
-                 int* max_concurrent_slices) {
+                 int* max_concurrent_slices, int* particles_in_shared) {
   int rc = check_prob(ctx, prob);
   if (rc) return rc;
   const Prob& p = ctx->probs[prob];
+  if (particles_in_shared) *particles_in_shared = p.layout == kLayoutSmem ? 1 : 0;
   if (quads_per_thread) *quads_per_thread = p.nq;
   if (ctas_per_slice) *ctas_per_slice = p.G;
   if (max_concurrent_slices) *max_concurrent_slices = p.slots_max;
@@ -659,3 +691,4 @@ int mmp_normals(const mmp_problem_desc* desc, int tag, unsigned int j, unsigned 
 }
 
 }  // extern "C"
+

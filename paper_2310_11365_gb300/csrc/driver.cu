@@ -110,8 +110,9 @@ __device__ void matching_record(double* af, double count, double m, double v, do
 // fitted by Levenberg-Marquardt on the exact slice ends t_1..t_k.  Settings
 // (the paper gives none): start from the regression y_{n+1} = r y_n + c,
 // damping 1e-3 scaled by diag(J^T J), /10 on success, x10 on failure, at
-// most 100 iterations, stop on a relative step below 1e-12 or damping above
-// 1e12; the fit is used only if alpha < 0 and 0 <= beta <= 1.
+// most 100 iterations, stop on a relative step below 1e-15 or damping above
+// 1e12, then three undamped Gauss-Newton steps; the fit is used only if
+// alpha < 0 and 0 <= beta <= 1.
 // The sums over points run across the warp (fixed butterfly order), so every
 // lane takes the same decisions.
 // ---------------------------------------------------------------------------
@@ -190,11 +191,31 @@ __device__ bool lsq_fit(const DriverArgs& a, int npts, double p0, double& alpha,
       al = na; be = nb; cost = ncost;
       lambda /= 10.0;
       const double rel = fmax(fabs(sa) / (fabs(al) + 1e-300), fabs(sb) / (fabs(be) + 1e-300));
-      if (rel < 1e-12) break;
+      if (rel < 1e-15) break;
     } else {
       lambda *= 10.0;
       if (lambda > 1e12) break;
     }
+  }
+  // undamped Gauss-Newton refinement to the minimiser (the cost test above
+  // cannot resolve the last step once its change is below rounding)
+  for (int it = 0; it < 3; ++it) {
+    double jaa = 0, jab = 0, jbb = 0, ga = 0, gb = 0;
+    for (int n = 1 + lane; n <= npts; n += 32) {
+      const double t = n * a.dT;
+      const double e = exp(al * t);
+      const double r = frac0_at(a, n) - (be + (p0 - be) * e);
+      const double da = (p0 - be) * t * e;
+      const double db = 1.0 - e;
+      jaa += da * da; jab += da * db; jbb += db * db;
+      ga += da * r; gb += db * r;
+    }
+    jaa = warp_sum(jaa); jab = warp_sum(jab); jbb = warp_sum(jbb);
+    ga = warp_sum(ga); gb = warp_sum(gb);
+    const double det = jaa * jbb - jab * jab;
+    if (!(det > 0.0) || !isfinite(det)) break;
+    al += (jbb * ga - jab * gb) / det;
+    be += (jaa * gb - jab * ga) / det;
   }
   alpha = al;
   beta = be;

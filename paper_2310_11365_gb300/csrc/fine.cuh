@@ -29,16 +29,24 @@ struct FineArgs {
   double* stats;               // restriction records [row][16]
   int stats_fixed;
   int G;                       // CTAs per slice
-  double* partials;            // [slot][2][G][kNV] group-reduction scratch
+  int nq;                      // quads per thread (shared-memory layout)
+  double* partials;            // [slot] x ([2][G][kNV] doubles + [2][G] float2) reduction scratch
   unsigned* counters;          // [slot] group-barrier arrival counters (zeroed per launch)
   unsigned* status;            // device status word
   unsigned long long wait_limit_ns;
 };
 
-// Occupancy-relevant handle of one kernel instantiation.
-const void* fine_kernel(int precision, int nq, bool mult);
+// Particle layouts of the fine kernel: quads in registers (a template per
+// quads-per-thread count) or in dynamic shared memory (any count).
+constexpr int kLayoutRegs = 0;
+constexpr int kLayoutSmem = 1;
+
+// Handle of one kernel instantiation (nq ignored for the shared layout).
+const void* fine_kernel(int precision, int layout, int nq, bool mult);
+// Dynamic shared memory of a launch.
+size_t fine_smem_bytes(int precision, int layout, int nq);
 // Cooperative launch of the instantiation (grid = slots * G CTAs).
-cudaError_t launch_fine(int precision, int nq, bool mult, int grid, const FineArgs& args,
+cudaError_t launch_fine(int precision, int layout, int nq, bool mult, int grid, const FineArgs& args,
                         cudaStream_t stream);
 
 }  // namespace mmp

@@ -10,6 +10,8 @@ namespace mmp {
                 : (const void*)k_fine<float, NQ, false>;
 
 const void* fine_kernel_f32(int nq, bool mult) {
+  if (nq == 0)
+    return mult ? (const void*)k_fine<float, 0, true> : (const void*)k_fine<float, 0, false>;
   switch (nq) {
     MMP_F32_CASE(1)
     MMP_F32_CASE(2)

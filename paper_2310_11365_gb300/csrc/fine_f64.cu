@@ -10,6 +10,8 @@ namespace mmp {
                 : (const void*)k_fine<double, NQ, false>;
 
 const void* fine_kernel_f64(int nq, bool mult) {
+  if (nq == 0)
+    return mult ? (const void*)k_fine<double, 0, true> : (const void*)k_fine<double, 0, false>;
   switch (nq) {
     MMP_F64_CASE(1)
     MMP_F64_CASE(2)

@@ -59,14 +59,23 @@ struct Quad<double> {
 // Per-CTA shared state of the group reductions.
 struct GroupShared {
   double red[kWarps][kNV];  // per-warp partials
+  float2 redf[kWarps];      // per-warp double-float partials of the per-step sum
   double tot[kNV];          // group totals, broadcast
   double uni[4];            // per-step uniforms derived from the mean
+  float unif[4];            // the same, rounded once for float particles
   int abort;
 };
 
+template <typename R>
+__device__ __forceinline__ R uniform_of(const GroupShared& sh, int k);
+template <>
+__device__ __forceinline__ float uniform_of<float>(const GroupShared& sh, int k) { return sh.unif[k]; }
+template <>
+__device__ __forceinline__ double uniform_of<double>(const GroupShared& sh, int k) { return sh.uni[k]; }
+
 // Group-reduction context of one CTA.
 struct Group {
-  double* part;         // [2][G][kNV] for this slot
+  double* part;         // [2][G][kNV] doubles, then [2][G] float2, for this slot
   unsigned* counter;    // arrivals of this slot
   unsigned* status;
   unsigned long long limit_ns;
@@ -77,12 +86,16 @@ struct Group {
 // Warp 0 finishes a group reduction of nv values whose per-warp partials
 // sit in sh.red.  min_mask / max_mask select values combined by min / max
 // (all others are summed).  Returns false if the cross-CTA wait gave up.
-__device__ __forceinline__ bool group_finish(GroupShared& sh, Group& grp, int nv, unsigned min_mask,
+__device__ __forceinline__ bool group_wait(Group& grp);
+
+template <int NV>
+__device__ __forceinline__ bool group_finish(GroupShared& sh, Group& grp, unsigned min_mask,
                                              unsigned max_mask) {
+  constexpr int nv = NV;
   const int lane = threadIdx.x & 31;
-  double v[kNV];
+  double v[NV];
 #pragma unroll
-  for (int k = 0; k < kNV; ++k) {
+  for (int k = 0; k < NV; ++k) {
     const double ident = (min_mask >> k & 1) ? INFINITY : ((max_mask >> k & 1) ? -INFINITY : 0.0);
     v[k] = (k < nv && lane < kWarps) ? sh.red[lane][k] : ident;
   }
@@ -90,7 +103,7 @@ __device__ __forceinline__ bool group_finish(GroupShared& sh, Group& grp, int nv
 #pragma unroll
   for (int off = kWarps / 2; off > 0; off >>= 1) {
 #pragma unroll
-    for (int k = 0; k < kNV; ++k) {
+    for (int k = 0; k < NV; ++k) {
       if (k < nv) {
         const double o = __shfl_xor_sync(0xffffffffu, v[k], off);
         v[k] = (min_mask >> k & 1) ? fmin(v[k], o) : ((max_mask >> k & 1) ? fmax(v[k], o) : v[k] + o);
@@ -103,41 +116,20 @@ __device__ __forceinline__ bool group_finish(GroupShared& sh, Group& grp, int nv
     double* mine = grp.part + ((size_t)parity * grp.G + grp.g) * kNV;
     if (lane == 0) {
 #pragma unroll
-      for (int k = 0; k < kNV; ++k)
+      for (int k = 0; k < NV; ++k)
         if (k < nv) mine[k] = v[k];
       red_release_gpu_add(grp.counter, 1u);
     }
-    const unsigned target = grp.epoch * (unsigned)grp.G;
-    bool ok = true;
-    unsigned long long t0 = 0;
-    int spins = 0;
-    while (ld_acquire_gpu(grp.counter) < target) {
-      if (++spins >= 32) {
-        spins = 0;
-        const unsigned long long now = globaltimer_ns();
-        if (t0 == 0) {
-          t0 = now;
-        } else if (now - t0 > grp.limit_ns) {
-          ok = false;
-        }
-        if (*(volatile unsigned*)grp.status & kStatusTimeout) ok = false;
-        if (!ok) break;
-      }
-    }
-    ok = __all_sync(0xffffffffu, ok);
-    if (!ok) {
-      if (lane == 0) atomicOr(grp.status, kStatusTimeout);
-      return false;
-    }
+    if (!group_wait(grp)) return false;
     const double* all = grp.part + (size_t)parity * grp.G * kNV;
 #pragma unroll
-    for (int k = 0; k < kNV; ++k) {
+    for (int k = 0; k < NV; ++k) {
       const double ident = (min_mask >> k & 1) ? INFINITY : ((max_mask >> k & 1) ? -INFINITY : 0.0);
       v[k] = ident;
     }
     for (int c = lane; c < grp.G; c += 32) {
 #pragma unroll
-      for (int k = 0; k < kNV; ++k) {
+      for (int k = 0; k < NV; ++k) {
         if (k < nv) {
           const double o = __ldcg(all + (size_t)c * kNV + k);
           v[k] = (min_mask >> k & 1) ? fmin(v[k], o) : ((max_mask >> k & 1) ? fmax(v[k], o) : v[k] + o);
@@ -147,7 +139,7 @@ __device__ __forceinline__ bool group_finish(GroupShared& sh, Group& grp, int nv
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-      for (int k = 0; k < kNV; ++k) {
+      for (int k = 0; k < NV; ++k) {
         if (k < nv) {
           const double o = __shfl_xor_sync(0xffffffffu, v[k], off);
           v[k] = (min_mask >> k & 1) ? fmin(v[k], o) : ((max_mask >> k & 1) ? fmax(v[k], o) : v[k] + o);
@@ -157,26 +149,34 @@ __device__ __forceinline__ bool group_finish(GroupShared& sh, Group& grp, int nv
   }
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < kNV; ++k)
+    for (int k = 0; k < NV; ++k)
       if (k < nv) sh.tot[k] = v[k];
   }
   return true;
 }
 
-// Per-warp stage of a sum of one per-thread value, exact to double-float for
-// float input (error-free two-sums) and plain double otherwise.
+// Double-float addition (hi, lo) + (b_hi, b_lo) with error-free two-sums;
+// exact to about 2^-48 relative and free of FP64 instructions, which on
+// this chip issue at a small fraction of the FP32 rate.
+__device__ __forceinline__ float2 dd_add(float2 a, float2 b) {
+  float s, e;
+  two_sum(a.x, b.x, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  float hi, lo;
+  two_sum(s, e, hi, lo);
+  return make_float2(hi, lo);
+}
+__device__ __forceinline__ float2 shfl_xor_dd(float2 v, int off) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off));
+}
+
+// Per-warp stage of the per-step sum: float input is carried as a
+// double-float pair, double input as a double.
 __device__ __forceinline__ void warp_sum_to_shared(GroupShared& sh, float s) {
-  float hi = s, lo = 0.0f;
+  float2 v = make_float2(s, 0.0f);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
-    const float olo = __shfl_xor_sync(0xffffffffu, lo, off);
-    float t, e;
-    two_sum(hi, ohi, t, e);
-    lo = __fadd_rn(__fadd_rn(lo, olo), e);
-    hi = t;
-  }
-  if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5][0] = (double)hi + (double)lo;
+  for (int off = 16; off > 0; off >>= 1) v = dd_add(v, shfl_xor_dd(v, off));
+  if ((threadIdx.x & 31) == 0) sh.redf[threadIdx.x >> 5] = v;
 }
 __device__ __forceinline__ void warp_sum_to_shared(GroupShared& sh, double s) {
 #pragma unroll
@@ -184,13 +184,75 @@ __device__ __forceinline__ void warp_sum_to_shared(GroupShared& sh, double s) {
   if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5][0] = s;
 }
 
+// Bounded wait of warp 0 for all G arrivals of the current epoch.
+__device__ __forceinline__ bool group_wait(Group& grp) {
+  const unsigned target = grp.epoch * (unsigned)grp.G;
+  bool ok = true;
+  unsigned long long t0 = 0;
+  int spins = 0;
+  while (ld_acquire_gpu(grp.counter) < target) {
+    if (++spins >= 32) {
+      spins = 0;
+      const unsigned long long now = globaltimer_ns();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > grp.limit_ns) {
+        ok = false;
+      }
+      if (*(volatile unsigned*)grp.status & kStatusTimeout) ok = false;
+      if (!ok) break;
+    }
+  }
+  ok = __all_sync(0xffffffffu, ok);
+  if (!ok && (threadIdx.x & 31) == 0) atomicOr(grp.status, kStatusTimeout);
+  return ok;
+}
+
+// Warp 0 finishes the per-step sum of float particles entirely in FP32
+// double-float arithmetic (warps in index order, then CTAs in index order)
+// and publishes the per-step uniforms as floats.  Returns false on timeout.
+__device__ __forceinline__ bool step_sum_finish_f(GroupShared& sh, Group& grp, float inv_p, float kappa,
+                                                  float c0, float be, float b0, float sqrt_h) {
+  const int lane = threadIdx.x & 31;
+  float2 v = lane < kWarps ? sh.redf[lane] : make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int off = kWarps / 2; off > 0; off >>= 1) v = dd_add(v, shfl_xor_dd(v, off));
+  if (grp.G > 1) {
+    const unsigned parity = grp.epoch & 1u;
+    grp.epoch += 1;
+    // dense per-step partials after the [2][G][kNV] double area
+    float2* part = reinterpret_cast<float2*>(grp.part + (size_t)2 * grp.G * kNV) + (size_t)parity * grp.G;
+    if (lane == 0) {
+      part[grp.g] = v;
+      red_release_gpu_add(grp.counter, 1u);
+    }
+    if (!group_wait(grp)) return false;
+    v = make_float2(0.0f, 0.0f);
+    for (int c = lane; c < grp.G; c += 32) {
+      const float2 o = __ldcg(part + c);
+      v = dd_add(v, o);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = dd_add(v, shfl_xor_dd(v, off));
+  }
+  if (lane == 0) {
+    const float m = __fmaf_rn(v.x, inv_p, v.y * inv_p);
+    sh.unif[0] = m;
+    sh.unif[1] = __fmaf_rn(kappa, m, c0);
+    sh.unif[2] = __fmaf_rn(be, m, b0) * sqrt_h;
+  }
+  return true;
+}
+
 // General per-warp stage of nv double values.
-__device__ __forceinline__ void warp_reduce_to_shared(GroupShared& sh, double v[kNV], int nv,
-                                                      unsigned min_mask, unsigned max_mask) {
+template <int NV>
+__device__ __forceinline__ void warp_reduce_to_shared(GroupShared& sh, double v[NV], unsigned min_mask,
+                                                      unsigned max_mask) {
+  constexpr int nv = NV;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-    for (int k = 0; k < kNV; ++k) {
+    for (int k = 0; k < NV; ++k) {
       if (k < nv) {
         const double o = __shfl_xor_sync(0xffffffffu, v[k], off);
         v[k] = (min_mask >> k & 1) ? fmin(v[k], o) : ((max_mask >> k & 1) ? fmax(v[k], o) : v[k] + o);
@@ -199,7 +261,7 @@ __device__ __forceinline__ void warp_reduce_to_shared(GroupShared& sh, double v[
   }
   if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-    for (int k = 0; k < kNV; ++k)
+    for (int k = 0; k < NV; ++k)
       if (k < nv) sh.red[threadIdx.x >> 5][k] = v[k];
   }
 }
@@ -212,18 +274,52 @@ __device__ __forceinline__ void publish_uniforms(GroupShared& sh, const FineArgs
   sh.uni[0] = m;
   sh.uni[1] = a.kappa * m + a.c0;
   sh.uni[2] = (a.BE * m + a.B0) * a.sqrt_h;
+  sh.unif[0] = (float)sh.uni[0];
+  sh.unif[1] = (float)sh.uni[1];
+  sh.unif[2] = (float)sh.uni[2];
 }
 
-// Resident CTAs per SM the register budget is sized for: the quads a thread
-// holds dominate its registers, so fewer CTAs fit as NQ grows.
+// Where a thread keeps its quads of particles between steps.
+// NQ > 0: in registers, NQ quads (loops over quads fully unrolled).
+// NQ == 0: in dynamic shared memory, a.nq quads at stride kTPB quads, so a
+// warp touches 512 contiguous bytes per quad (conflict-free 16-byte
+// accesses) and registers stay few, which lets more CTAs share an SM.
+extern __shared__ __align__(16) unsigned char mmp_fine_smem[];
+
+template <typename R, int NQ>
+struct QuadStore {
+  R x[NQ][4];
+  __device__ __forceinline__ void bind() {}
+  __device__ __forceinline__ void get(int i, R v[4]) const {
+#pragma unroll
+    for (int w = 0; w < 4; ++w) v[w] = x[i][w];
+  }
+  __device__ __forceinline__ void put(int i, const R v[4]) {
+#pragma unroll
+    for (int w = 0; w < 4; ++w) x[i][w] = v[w];
+  }
+};
+template <typename R>
+struct QuadStore<R, 0> {
+  R* base;
+  __device__ __forceinline__ void bind() { base = reinterpret_cast<R*>(mmp_fine_smem) + 4 * threadIdx.x; }
+  __device__ __forceinline__ void get(int i, R v[4]) const { Quad<R>::load(base + 4 * (size_t)i * kTPB, v); }
+  __device__ __forceinline__ void put(int i, const R v[4]) { Quad<R>::store(base + 4 * (size_t)i * kTPB, v); }
+};
+
+// Resident CTAs per SM the register budget is sized for.  Register layout:
+// the quads a thread holds dominate its registers, so fewer CTAs fit as NQ
+// grows.  Shared-memory layout (NQ == 0): registers hold one quad in flight.
 template <typename R, int NQ>
 struct FineOccupancy {
-  static constexpr int value = sizeof(R) == 4 ? (NQ <= 2 ? 5 : (NQ <= 4 ? 4 : 3)) : (NQ <= 2 ? 3 : 2);
+  static constexpr int value = NQ == 0 ? (sizeof(R) == 4 ? 5 : 4)
+                                       : (sizeof(R) == 4 ? (NQ <= 2 ? 5 : (NQ <= 4 ? 4 : 3)) : (NQ <= 2 ? 3 : 2));
 };
 
 template <typename R, int NQ, bool MULT>
 __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, NQ>::value)) k_fine(const FineArgs a) {
   __shared__ GroupShared sh;
+  constexpr int kUnroll = NQ > 0 ? NQ : 2;
   const int G = a.G;
   const int n_slots = gridDim.x / G;
   const int slot = blockIdx.x / G;
@@ -233,15 +329,17 @@ __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, NQ>::value)) k_fine(co
   const int warp = tid >> 5;
   if (slot >= n_slots) return;
 
+  const int nq_max = NQ > 0 ? NQ : a.nq;
   const int qb = (int)(((long long)a.Q * g) / G);
   const int qe = (int)(((long long)a.Q * (g + 1)) / G);
   const int span = qe - qb - tid;
-  const int nq = span <= 0 ? 0 : min(NQ, (span + kTPB - 1) / kTPB);
+  const int nq = span <= 0 ? 0 : min(nq_max, (span + kTPB - 1) / kTPB);
   const int qlast = a.Q - 1;
   const int plast = (int)(a.P - 4LL * qlast);  // valid lanes of the last quad, 1..4
+  const int loop_n = NQ > 0 ? NQ : nq;        // quads this thread visits
 
   Group grp;
-  grp.part = a.partials + (size_t)slot * 2 * G * kNV;
+  grp.part = a.partials + (size_t)slot * 2 * G * (kNV + 1);
   grp.counter = a.counters + slot;
   grp.status = a.status;
   grp.limit_ns = a.wait_limit_ns;
@@ -257,47 +355,57 @@ __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, NQ>::value)) k_fine(co
   const R b0sq = (R)(a.B0 * a.sqrt_h);    // additive noise amplitude
   const R thr = (R)a.thr;
   const bool two = a.n_regions > 1;
+  // per-step uniforms of the float path are formed in FP32 by warp 0
+  const float inv_p = (float)(1.0 / (double)a.P);
+  const float kappa_f = (float)a.kappa, c0_f = (float)a.c0, be_f = (float)a.BE, b0_f = (float)a.B0;
+  const float sqrt_h_f = (float)a.sqrt_h;
+
+  QuadStore<R, NQ> xs;
+  xs.bind();
 
   for (int task = slot; task < a.n_tasks; task += n_slots) {
     const int n = a.slice_begin + task;
     const R* src = (a.src == nullptr || n == 0) ? (const R*)a.src0
                                                 : (const R*)a.src + (size_t)(n - 1) * a.pitch;
-    R x[NQ][4];
-    // ---------------- prologue: load and match --------------------------
-#pragma unroll
-    for (int i = 0; i < NQ; ++i) {
-      const int q = qb + tid + i * kTPB;
-      if (i < nq && (q != qlast || plast == 4)) {
-        Quad<R>::load(src + 4 * (size_t)q, x[i]);
-      } else {
-        // past the group's range, or the ragged last quad: guarded scalar
-        // loads so that a buffer of exactly P values is never over-read
-#pragma unroll
-        for (int w = 0; w < 4; ++w) x[i][w] = (i < nq && w < plast) ? src[4 * (size_t)q + w] : (R)0;
-      }
-    }
+    // ---------------- prologue: load, match, first mean ------------------
     double flips = 0.0;
-    if (a.aff != nullptr) {
-      const double* af = a.aff + (size_t)(a.aff_fixed ? 0 : n) * 2 * kAff;
-      const int mode0 = (int)af[0], mode1 = (int)af[kAff];
-      const R a0 = (R)af[1], b0 = (R)af[2], c0m = (R)af[3];
-      const R a1 = (R)af[kAff + 1], b1 = (R)af[kAff + 2], c1m = (R)af[kAff + 3];
-      if (mode0 != kMatchIdentity || (two && mode1 != kMatchIdentity)) {
-        const bool redraw = mode0 == kMatchRedraw || (two && mode1 == kMatchRedraw);
+    R s_in = (R)0;
+    {
+      int mode0 = kMatchIdentity, mode1 = kMatchIdentity;
+      R a0 = 0, b0 = 0, c0m = 0, a1 = 0, b1 = 0, c1m = 0;
+      if (a.aff != nullptr) {
+        const double* af = a.aff + (size_t)(a.aff_fixed ? 0 : n) * 2 * kAff;
+        mode0 = (int)af[0];
+        mode1 = two ? (int)af[kAff] : kMatchIdentity;
+        a0 = (R)af[1]; b0 = (R)af[2]; c0m = (R)af[3];
+        a1 = (R)af[kAff + 1]; b1 = (R)af[kAff + 2]; c1m = (R)af[kAff + 3];
+      }
+      const bool match = mode0 != kMatchIdentity || mode1 != kMatchIdentity;
+      const bool redraw = mode0 == kMatchRedraw || mode1 == kMatchRedraw;
+#pragma unroll kUnroll
+      for (int i = 0; i < loop_n; ++i) {
+        R v[4] = {0, 0, 0, 0};
+        const int q = qb + tid + i * kTPB;
+        if (i < nq) {
+          if (q != qlast || plast == 4) {
+            Quad<R>::load(src + 4 * (size_t)q, v);
+          } else {
+            // the ragged last quad: guarded scalar loads so that a buffer
+            // of exactly P values is never over-read
 #pragma unroll
-        for (int i = 0; i < NQ; ++i) {
-          if (i < nq) {
-            const uint32_t q = (uint32_t)(qb + tid + i * kTPB);
+            for (int w = 0; w < 4; ++w) v[w] = w < plast ? src[4 * (size_t)q + w] : (R)0;
+          }
+          if (match) {
             R z[4] = {0, 0, 0, 0};
             R zr[4] = {0, 0, 0, 0};
             if (redraw) {
-              normals4<R>(philox4x32_10(rng_counter(q, 0u, (uint32_t)n, 2u, a.ptag), a.key0, a.key1), z);
+              normals4<R>(philox4x32_10(rng_counter((uint32_t)q, 0u, (uint32_t)n, 2u, a.ptag), a.key0, a.key1), z);
               if (two)
-                normals4<R>(philox4x32_10(rng_counter(q, 1u, (uint32_t)n, 2u, a.ptag), a.key0, a.key1), zr);
+                normals4<R>(philox4x32_10(rng_counter((uint32_t)q, 1u, (uint32_t)n, 2u, a.ptag), a.key0, a.key1), zr);
             }
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
-              const R xv = x[i][w];
+              const R xv = v[w];
               const int r = (two && !(xv < thr)) ? 1 : 0;
               const int mode = r ? mode1 : mode0;
               R y = xv;
@@ -306,34 +414,29 @@ __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, NQ>::value)) k_fine(co
               } else if (mode == kMatchRedraw) {
                 y = r ? a1 + b1 * zr[w] : a0 + b0 * z[w];
               }
-              x[i][w] = y;
+              v[w] = y;
               if (two && ((!(y < thr)) ? 1 : 0) != r && (4 * (long long)q + w < a.P)) flips += 1.0;
             }
           }
+          // zero the lanes past P so that sums see only real particles
+          if (q == qlast) {
+            if (plast < 4) v[3] = (R)0;
+            if (plast < 3) v[2] = (R)0;
+            if (plast < 2) v[1] = (R)0;
+          }
+          s_in += (v[0] + v[1]) + (v[2] + v[3]);
         }
-      }
-    }
-    // zero the lanes past P so that sums see only real particles
-#pragma unroll
-    for (int i = 0; i < NQ; ++i) {
-      if (i < nq && qb + tid + i * kTPB == qlast) {
-        if (plast < 4) x[i][3] = (R)0;
-        if (plast < 3) x[i][2] = (R)0;
-        if (plast < 2) x[i][1] = (R)0;
+        xs.put(i, v);
       }
     }
     {
-      double v[kNV];
-      R s = (R)0;
-#pragma unroll
-      for (int i = 0; i < NQ; ++i)
-        if (i < nq) s += (x[i][0] + x[i][1]) + (x[i][2] + x[i][3]);
-      v[0] = (double)s;
+      double v[2];
+      v[0] = (double)s_in;
       v[1] = flips;
-      warp_reduce_to_shared(sh, v, 2, 0u, 0u);
+      warp_reduce_to_shared<2>(sh, v, 0u, 0u);
       __syncthreads();
       if (warp == 0) {
-        if (!group_finish(sh, grp, 2, 0u, 0u)) {
+        if (!group_finish<2>(sh, grp, 0u, 0u)) {
           if (lane == 0) sh.abort = 1;
         } else if (lane == 0) {
           publish_uniforms(sh, a);
@@ -347,73 +450,75 @@ __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, NQ>::value)) k_fine(co
 
     // ---------------- Euler-Maruyama steps --------------------------------
     for (int j = 0; j < a.nf; ++j) {
-      const R base = (R)sh.uni[1];   // kappa m_j + c0
-      const R boff = (R)sh.uni[2];   // (BE m_j + B0) sqrt(h)
+      const R base = uniform_of<R>(sh, 1);  // kappa m_j + c0
+      const R boff = uniform_of<R>(sh, 2);  // (BE m_j + B0) sqrt(h)
       R s = (R)0;
-#pragma unroll
-      for (int i = 0; i < NQ; ++i) {
+#pragma unroll kUnroll
+      for (int i = 0; i < loop_n; ++i) {
         if (i < nq) {
           const uint32_t q = (uint32_t)(qb + tid + i * kTPB);
+          R v[4];
+          xs.get(i, v);
           R z[4];
           normals4<R>(philox4x32_10(rng_counter(q, (uint32_t)j, (uint32_t)n, 0u, a.ptag), a.key0, a.key1), z);
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
-            const R xv = x[i][w];
-            const R drift = fma(fma(nc3, xv * xv, c1), xv, base);
-            const R amp = MULT ? fma(bsq, xv, boff) : b0sq;
-            x[i][w] = fma(amp, z[w], fma(h, drift, xv));
+            const R xv = v[w];
+            const R drift = fmaR(fmaR(nc3, xv * xv, c1), xv, base);
+            const R amp = MULT ? fmaR(bsq, xv, boff) : b0sq;
+            v[w] = fmaR(amp, z[w], fmaR(h, drift, xv));
           }
           if (q == (uint32_t)qlast) {
-            if (plast < 4) x[i][3] = (R)0;
-            if (plast < 3) x[i][2] = (R)0;
-            if (plast < 2) x[i][1] = (R)0;
+            if (plast < 4) v[3] = (R)0;
+            if (plast < 3) v[2] = (R)0;
+            if (plast < 2) v[1] = (R)0;
           }
-          s += (x[i][0] + x[i][1]) + (x[i][2] + x[i][3]);
+          s += (v[0] + v[1]) + (v[2] + v[3]);
+          xs.put(i, v);
         }
       }
       warp_sum_to_shared(sh, s);
       __syncthreads();
       if (warp == 0) {
-        if (!group_finish(sh, grp, 1, 0u, 0u)) {
-          if (lane == 0) sh.abort = 1;
-        } else if (lane == 0) {
-          publish_uniforms(sh, a);
+        bool ok;
+        if constexpr (sizeof(R) == 4) {
+          ok = step_sum_finish_f(sh, grp, inv_p, kappa_f, c0_f, be_f, b0_f, sqrt_h_f);
+        } else {
+          ok = group_finish<1>(sh, grp, 0u, 0u);
+          if (ok && lane == 0) publish_uniforms(sh, a);
         }
+        if (!ok && lane == 0) sh.abort = 1;
       }
       __syncthreads();
       if (sh.abort) return;
     }
 
     // ---------------- epilogue: store and restrict -----------------------
-    if (a.dst != nullptr) {
-      R* dst = (R*)a.dst + (size_t)(a.dst_fixed ? 0 : n) * a.pitch;
-#pragma unroll
-      for (int i = 0; i < NQ; ++i) {
-        const int q = qb + tid + i * kTPB;
-        if (i < nq && (q != qlast || plast == 4)) {
-          Quad<R>::store(dst + 4 * (size_t)q, x[i]);
-        } else if (i < nq) {
-#pragma unroll
-          for (int w = 0; w < 4; ++w)
-            if (w < plast) dst[4 * (size_t)q + w] = x[i][w];
-        }
-      }
-    }
-    // pass 1: counts and sums per region
+    // pass 1 (with the store): counts and sums per region
     {
-      double v[kNV];
-#pragma unroll
-      for (int k = 0; k < kNV; ++k) v[k] = 0.0;
-#pragma unroll
-      for (int i = 0; i < NQ; ++i) {
+      R* dst = a.dst != nullptr ? (R*)a.dst + (size_t)(a.dst_fixed ? 0 : n) * a.pitch : nullptr;
+      double v[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll kUnroll
+      for (int i = 0; i < loop_n; ++i) {
         if (i < nq) {
           const int q = qb + tid + i * kTPB;
+          R x4[4];
+          xs.get(i, x4);
+          if (dst != nullptr) {
+            if (q != qlast || plast == 4) {
+              Quad<R>::store(dst + 4 * (size_t)q, x4);
+            } else {
+#pragma unroll
+              for (int w = 0; w < 4; ++w)
+                if (w < plast) dst[4 * (size_t)q + w] = x4[w];
+            }
+          }
           const int valid = q == qlast ? plast : 4;
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
             if (w < valid) {
-              const double xv = (double)x[i][w];
-              if (two && !(x[i][w] < thr)) {
+              const double xv = (double)x4[w];
+              if (two && !(x4[w] < thr)) {
                 v[2] += 1.0;
                 v[3] += xv;
               } else {
@@ -424,9 +529,9 @@ __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, NQ>::value)) k_fine(co
           }
         }
       }
-      warp_reduce_to_shared(sh, v, 4, 0u, 0u);
+      warp_reduce_to_shared<4>(sh, v, 0u, 0u);
       __syncthreads();
-      if (warp == 0 && !group_finish(sh, grp, 4, 0u, 0u) && lane == 0) sh.abort = 1;
+      if (warp == 0 && !group_finish<4>(sh, grp, 0u, 0u) && lane == 0) sh.abort = 1;
       __syncthreads();
       if (sh.abort) return;
     }
@@ -437,22 +542,23 @@ __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, NQ>::value)) k_fine(co
     __syncthreads();
     // pass 2: centred sums and extremes
     {
-      double v[kNV];
+      double v[7];
       v[0] = 0.0; v[1] = 0.0; v[2] = 0.0;
       v[3] = INFINITY; v[4] = -INFINITY; v[5] = INFINITY; v[6] = -INFINITY;
-      v[7] = 0.0;
-#pragma unroll
-      for (int i = 0; i < NQ; ++i) {
+#pragma unroll kUnroll
+      for (int i = 0; i < loop_n; ++i) {
         if (i < nq) {
           const int q = qb + tid + i * kTPB;
           const int valid = q == qlast ? plast : 4;
+          R x4[4];
+          xs.get(i, x4);
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
             if (w < valid) {
-              const double xv = (double)x[i][w];
+              const double xv = (double)x4[w];
               const double dg = xv - gmean;
               v[2] += dg * dg;
-              if (two && !(x[i][w] < thr)) {
+              if (two && !(x4[w] < thr)) {
                 const double d = xv - mean1;
                 v[1] += d * d;
                 v[5] = fmin(v[5], xv);
@@ -468,9 +574,9 @@ __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, NQ>::value)) k_fine(co
         }
       }
       const unsigned mn = (1u << 3) | (1u << 5), mx = (1u << 4) | (1u << 6);
-      warp_reduce_to_shared(sh, v, 7, mn, mx);
+      warp_reduce_to_shared<7>(sh, v, mn, mx);
       __syncthreads();
-      if (warp == 0 && !group_finish(sh, grp, 7, mn, mx) && lane == 0) sh.abort = 1;
+      if (warp == 0 && !group_finish<7>(sh, grp, mn, mx) && lane == 0) sh.abort = 1;
       __syncthreads();
       if (sh.abort) return;
     }

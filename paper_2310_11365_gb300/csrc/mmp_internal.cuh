@@ -62,16 +62,26 @@ __device__ __forceinline__ float uniform_f(uint32_t o) {
   return __uint_as_float(0x3F800000u | (o >> 9)) - 0x1.fffffep-1f;
 }
 __device__ __forceinline__ double uniform_d(uint32_t o) {
-  return fma((double)(o >> 9), 0x1p-23, 0x1p-24);
+  return __fma_rn((double)(o >> 9), 0x1p-23, 0x1p-24);
 }
 
+// Fused multiply-add in the particle precision (never promoted to FP64).
+__device__ __forceinline__ float fmaR(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmaR(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Box-Muller: z = sqrt(-2 ln ua) (cos 2 pi ub, sin 2 pi ub).
+// FP32 form on the special-function unit: ln ua from the hardware log2,
+// sqrt t as t * rsqrt(t), and sin/cos of theta = 2 pi (ub - 1/2), which lies
+// in (-pi, pi) where the hardware sin/cos are accurate; then
+// cos 2 pi ub = -cos theta and sin 2 pi ub = -sin theta.  The draws differ
+// from the FP64 definition by a few 1e-6 absolute (bounded in the tests).
 __device__ __forceinline__ void box_muller(float ua, float ub, float& z0, float& z1) {
-  const float r = sqrtf(-2.0f * logf(ua));
+  const float t = -1.38629436f * __log2f(ua);  // -2 ln 2 log2(ua) > 0 for ua < 1
+  const float r = t * rsqrtf(t);
   float s, c;
-  sincospif(2.0f * ub, &s, &c);
-  z0 = r * c;
-  z1 = r * s;
+  __sincosf(6.28318531f * (ub - 0.5f), &s, &c);
+  z0 = -r * c;
+  z1 = -r * s;
 }
 __device__ __forceinline__ void box_muller(double ua, double ub, double& z0, double& z1) {
   const double r = sqrt(-2.0 * log(ua));

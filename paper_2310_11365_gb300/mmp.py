@@ -90,7 +90,7 @@ def load():
         "mmp_fine": ([vp, i, i, vp, vp, d], i),
         "mmp_philox": ([vp, C.POINTER(C.c_uint), vp, ll, vp], i),
         "mmp_normals": ([pd, i, C.c_uint, C.c_uint, ll, vp, vp], i),
-        "mmp_get_plan": ([vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(i)], i),
+        "mmp_get_plan": ([vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)], i),
         "mmp_set_timing": ([vp, i], i),
         "mmp_timing": ([vp, i, d, C.POINTER(ll), d, C.POINTER(ll)], i),
     }
@@ -209,9 +209,10 @@ def mmp_fine(ctx, prob: int, n: int, u_in_ptr: int, u_out_ptr: int) -> np.ndarra
 
 
 def mmp_get_plan(ctx, prob: int) -> dict:
-    a, b, c = C.c_int(), C.c_int(), C.c_int()
-    _check(load().mmp_get_plan(ctx, prob, C.byref(a), C.byref(b), C.byref(c)), "mmp_get_plan")
-    return {"quads_per_thread": a.value, "ctas_per_slice": b.value, "max_concurrent_slices": c.value}
+    a, b, c, e = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(load().mmp_get_plan(ctx, prob, C.byref(a), C.byref(b), C.byref(c), C.byref(e)), "mmp_get_plan")
+    return {"quads_per_thread": a.value, "ctas_per_slice": b.value, "max_concurrent_slices": c.value,
+            "particles_in_shared": bool(e.value)}
 
 
 def mmp_set_timing(ctx, on: bool) -> None:

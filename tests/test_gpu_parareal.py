@@ -22,14 +22,16 @@ def _gpu_run(p, max_iter=None):
 
 def _assert_moments_close(mom, orc_res, rtol=1e-10):
     """rho^K_n per region and globally, tolerance relative to the natural
-    scale: sqrt(v) for means, v for variances; fractions exact."""
+    scale: sqrt(v) for means, v for variances.  Fractions counted from
+    particles match exactly; fractions extrapolated by the learned model
+    (Def. 3.4, an iterative LM fit) match to rtol."""
     N1 = mom.shape[0]
     I = 2 if np.any(orc_res["frac"][:, 1] != 0) else 1
     for n in range(N1):
         for i in range(I):
             fo, mo, vo = orc_res["frac"][n][i], orc_res["mean"][n][i], orc_res["var"][n][i]
             f, m, v = mom[n, 3 * i], mom[n, 3 * i + 1], mom[n, 3 * i + 2]
-            assert abs(f - fo) <= 1e-12, (n, i, f, fo)
+            assert abs(f - fo) <= rtol, (n, i, f, fo)
             if fo == 0 and I > 1:
                 continue
             assert abs(m - mo) <= rtol * max(abs(mo), np.sqrt(abs(vo))), (n, i, m, mo)
@@ -63,7 +65,7 @@ def test_intermediate_iterates_match_oracle(mmplib, orc, kmax):
 
 @pytest.mark.parametrize("variant", [W.MULTIMODAL, W.LEARNING])
 def test_multimodal_matches_oracle(mmplib, orc, variant):
-    p = W.config3(N=8, P=4003, T=4.0, dt=5e-3, variant=variant, s0=0.6, m0=0.2, precision="fp64",
+    p = W.config3(N=8, P=6001, T=6.0, dt=5e-3, variant=variant, s0=0.3, m0=1.0, B0=1.0, precision="fp64",
                   max_iter=5, tol=0.0)
     s, k, mom, st = _gpu_run(p)
     ref = orc.parareal(p)

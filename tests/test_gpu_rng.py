@@ -63,18 +63,46 @@ def test_normals_fp64_match_oracle(mmplib, orc):
 
 
 def test_normals_fp32_close_to_oracle(mmplib, orc):
+    """FP32 Box-Muller on the special-function unit against the FP64
+    definition.  With radius r = sqrt(-2 ln u_a) of the pair: 3e-6 relative to
+    max(|z|, 1) wherever r > 0.05; when u_a is close to 1 (r -> 0) the
+    hardware log is accurate only in absolute terms, so the error there is
+    bounded by 1e-3 absolute (these pairs have |z| < 0.05)."""
     import torch
 
     p = W.config2(precision="mixed")
-    count = 4096
+    count = 20_000
     out = torch.empty(count, dtype=torch.float32, device="cuda")
     mmplib.mmp_normals(p, 0, 11, 5, count, out.data_ptr())
     torch.cuda.synchronize()
     got = out.cpu().numpy().astype(np.float64)
     ref = np.array([orc.normal(p, 0, 11, 5, i) for i in range(count)])
     err = np.abs(got - ref)
-    assert np.max(err) < 4e-6
-    assert np.max(err / np.maximum(np.abs(ref), 1.0)) < 1e-6
+    pairs = ref.reshape(-1, 2)
+    r = np.repeat(np.sqrt((pairs ** 2).sum(axis=1)), 2)
+    far = r > 0.05
+    assert far.mean() > 0.99
+    assert np.max(err[far] / np.maximum(np.abs(ref[far]), 1.0)) < 3e-6
+    assert np.max(err) < 1e-3
+
+
+def test_normals_fp32_statistics(mmplib):
+    """4M FP32 draws: mean, variance, fourth moment within 5 standard errors
+    and no value beyond the radius cap sqrt(-2 ln 2^-24)."""
+    import math
+
+    import torch
+
+    p = W.config2(precision="mixed")
+    count = 4_000_000
+    out = torch.empty(count, dtype=torch.float32, device="cuda")
+    mmplib.mmp_normals(p, 0, 3, 9, count, out.data_ptr())
+    z = out.double()
+    n = count
+    assert abs(z.mean().item()) < 5 / math.sqrt(n)
+    assert abs(z.var().item() - 1.0) < 5 * math.sqrt(2.0 / n)
+    assert abs((z**4).mean().item() - 3.0) < 5 * math.sqrt(96.0 / n)
+    assert z.abs().max().item() < math.sqrt(-2 * math.log(2.0**-24)) + 1e-3
 
 
 def test_initial_ensemble_matches_oracle(mmplib, orc):

@@ -65,7 +65,9 @@ def _small_unimodal():
 
 
 def _small_multimodal(variant):
-    return W.config3(N=8, P=403, T=4.0, dt=5e-3, variant=variant, s0=0.6, m0=0.2)
+    # all mass starts in one well and relaxes into the other, so the region
+    # fractions follow the two-state model of App. H and the fit is accepted
+    return W.config3(N=8, P=6001, T=6.0, dt=5e-3, variant=variant, s0=0.3, m0=1.0, B0=1.0)
 
 
 @pytest.mark.parametrize("make", [
@@ -140,3 +142,11 @@ def test_learning_changes_only_extrapolated_fractions(orc):
     rl = orc.parareal(pl)
     assert np.array_equal(rm["hist"][3, :4], rl["hist"][3, :4])
     assert not np.array_equal(rm["frac"][5:], rl["frac"][5:])
+    # the extrapolated fractions follow the fitted relaxation towards beta
+    ser = orc.fine_serial(pl)
+    fr = [st["count"][0] / pl.P for st in ser["stats"]]
+    dT = pl.T / pl.N
+    rc, alpha, beta = orc.lsq_fit(dT * np.arange(1, 4), np.array(fr[1:4]), fr[0], dT)
+    assert rc == 0 and alpha < 0 and 0 <= beta <= 1
+    for n in range(4, pl.N + 1):
+        assert abs(rl["frac"][n][0] - orc.extrapolate(fr[3], alpha, beta, (n - 3) * dT)) < 1e-15
