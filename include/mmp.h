@@ -192,6 +192,37 @@ int mmp_philox(const unsigned int* ctr, const unsigned int* key, unsigned int* o
 int mmp_normals(const mmp_problem_desc* desc, int tag, unsigned int j, unsigned int n,
                 long long count, void* out, void* stream);
 
+/* One fine propagation F_n of an explicit ensemble, like mmp_fine, for
+ * callers that cannot allocate device memory where they need it: work
+ * issued while a stream is being captured into a CUDA graph (allocation is
+ * not allowed inside a capture), hosts whose device pool belongs to another
+ * allocator, latency-bound loops where an allocation could stall.  The
+ * paper has no counterpart; this is a property of the library.
+ *
+ * No context, no workspace, no allocation: the scratch of the kernel's
+ * cross-CTA mean reduction comes from one fixed array inside libmmp.so
+ * (about 171 KB of device memory, held on every GPU that loads the library
+ * until the process exits), serving at most MMP_STATIC_MAX_CTAS CTAs per
+ * slice; larger problems (above roughly 9.9e6 float or 4.9e6 double
+ * particles, depending on the launch shape) return MMP_ERR_UNSUPPORTED.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.
+ *
+ * desc      problem (only one slice is propagated; n in 0..N-1 selects the
+ *           draws)
+ * u_in      device, P values (double for MMP_FP64, float for MMP_MIXED),
+ *           16-byte aligned; u_out device, P values, must not alias u_in
+ * stats_dev device, MMP_STAT_STRIDE doubles or NULL: the restriction of
+ *           F_n(u_in); element 14 receives the device status bits
+ *           (0 = ok, 1 = a bounded wait gave up, 2 = non-finite result)
+ * stream    cudaStream_t; asynchronous.
+ * Every call shares the array and leaves its contents behind: the call
+ * clears what must start at zero, and calls that overlap on the GPU (on
+ * different streams, or from different host threads) race on it. */
+#define MMP_STATIC_MAX_CTAS 1216
+int mmp_fine_static(const mmp_problem_desc* desc, int n, const void* u_in, void* u_out,
+                    double* stats_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

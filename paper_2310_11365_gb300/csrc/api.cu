@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -692,3 +693,99 @@ int mmp_normals(const mmp_problem_desc* desc, int tag, unsigned int j, unsigned 
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// Fine propagation without any device allocation (mmp_fine_static).
+//
+// Some callers cannot allocate device memory where they need a fine
+// propagation: code issuing work while a stream is being captured into a
+// CUDA graph (allocation calls are not allowed inside a capture), hosts that
+// hand the whole device pool to another allocator and forbid allocations in
+// their inner loop, and latency-bound loops where an allocation could stall.
+// They own their ensembles; what they cannot provide is the scratch that the
+// fine kernel's cross-CTA mean reduction needs (partial sums and arrival
+// counters).  This entry point takes that scratch from one fixed array
+// compiled into the library instead of a caller workspace.
+// ---------------------------------------------------------------------------
+
+// CTAs per slice the array serves: partials [2][MMP_STATIC_MAX_CTAS][kNV]
+// doubles, then an arrival counter, a status word and one restriction row.
+static_assert(MMP_STATIC_MAX_CTAS == 1216, "keep the header and the array in step");
+constexpr size_t kStaticPartialDoubles = 2 * (size_t)MMP_STATIC_MAX_CTAS * (kNV + 1);
+constexpr size_t kStaticDoubles = kStaticPartialDoubles + 8 + kStat;
+static __device__ __align__(256) double mmp_static_scratch[kStaticDoubles];
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+double* g_static_addr[kStaticMaxDevices] = {nullptr};
+
+// The device address of the array on the current device, looked up once per
+// device (the host-side name of a __device__ array is not a device address).
+int static_scratch(double** out) {
+  int dev = 0;
+  MMP_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) return MMP_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (g_static_addr[dev] == nullptr) {
+    void* p = nullptr;
+    MMP_CUDA(cudaGetSymbolAddress(&p, mmp_static_scratch));
+    g_static_addr[dev] = (double*)p;
+  }
+  *out = g_static_addr[dev];
+  return MMP_OK;
+}
+
+__global__ void k_status_to_stats(const unsigned* status, double* stats) {
+  stats[14] = (double)status[0];
+}
+
+}  // namespace
+
+extern "C" int mmp_fine_static(const mmp_problem_desc* desc, int n, const void* u_in, void* u_out,
+                               double* stats_dev, void* stream) {
+  if (desc == nullptr || u_in == nullptr || u_out == nullptr || u_in == u_out) return MMP_ERR_INVALID_ARG;
+  if (((uintptr_t)u_in % 16) || ((uintptr_t)u_out % 16)) return MMP_ERR_INVALID_ARG;
+  int rc = validate(*desc);
+  if (rc) return rc;
+  if (n < 0 || n >= desc->N) return MMP_ERR_INVALID_ARG;
+  Prob p;
+  p.d = *desc;
+  derive(p);
+  Device dev;
+  rc = query_device(dev);
+  if (rc) return rc;
+  rc = plan(p, dev);
+  if (rc) return rc;
+  if (p.G > MMP_STATIC_MAX_CTAS) return MMP_ERR_UNSUPPORTED;
+  double* base = nullptr;
+  rc = static_scratch(&base);
+  if (rc) return rc;
+  unsigned* ctl = (unsigned*)(base + kStaticPartialDoubles);  // [0] counter, [1] status
+  double* stats = stats_dev != nullptr ? stats_dev : base + kStaticPartialDoubles + 8;
+  cudaStream_t s = (cudaStream_t)stream;
+  // every call shares the array: clear what must start at zero
+  MMP_CUDA(cudaMemsetAsync(ctl, 0, 8 * sizeof(double), s));
+  FineArgs a;
+  const mmp_problem_desc& d = p.d;
+  a.nc3 = -d.c3; a.c1 = d.c1; a.kappa = d.kappa; a.c0 = d.c0;
+  a.B = d.B; a.BE = d.BE; a.B0 = d.B0;
+  a.h = p.h; a.sqrt_h = p.sqrt_h; a.nf = p.nf;
+  a.P = d.P; a.Q = p.Q; a.pitch = p.pitch;
+  a.n_regions = p.I; a.thr = d.threshold;
+  a.key0 = p.key0; a.key1 = p.key1; a.ptag = d.problem_tag;
+  a.slice_begin = n; a.n_tasks = 1;
+  a.src0 = u_in; a.src = nullptr; a.dst = u_out; a.dst_fixed = 1;
+  a.aff = nullptr; a.aff_fixed = 0;
+  a.stats = stats; a.stats_fixed = 1;
+  a.G = p.G;
+  a.nq = p.nq;
+  a.partials = base; a.counters = ctl; a.status = ctl + 1;
+  a.wait_limit_ns = wait_limit_ns();
+  MMP_CUDA(launch_fine(d.precision, p.layout, p.nq, p.mult, p.G, a, s));
+  if (stats_dev != nullptr) {
+    k_status_to_stats<<<1, 1, 0, s>>>(ctl + 1, stats_dev);
+    MMP_CUDA(cudaGetLastError());
+  }
+  return MMP_OK;
+}

@@ -32,7 +32,7 @@ EXPORTED = [
     "mmp_strerror", "mmp_version", "mmp_last_cuda_error", "mmp_workspace_size", "mmp_create",
     "mmp_destroy", "mmp_set_initial", "mmp_lift", "mmp_iterate", "mmp_run", "mmp_status",
     "mmp_get_moments", "mmp_get_particles", "mmp_fine_serial", "mmp_fine", "mmp_philox",
-    "mmp_normals", "mmp_get_plan", "mmp_set_timing", "mmp_timing",
+    "mmp_normals", "mmp_get_plan", "mmp_set_timing", "mmp_timing", "mmp_fine_static",
 ]
 
 
@@ -93,6 +93,7 @@ def load():
         "mmp_get_plan": ([vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)], i),
         "mmp_set_timing": ([vp, i], i),
         "mmp_timing": ([vp, i, d, C.POINTER(ll), d, C.POINTER(ll)], i),
+        "mmp_fine_static": ([pd, i, vp, vp, vp, vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -226,6 +227,16 @@ def mmp_timing(ctx, reset: bool = False) -> dict:
            "mmp_timing")
     return {"fine_ms": ms.value, "fine_launches": fl.value, "fine_particle_steps": steps.value,
             "other_launches": ol.value}
+
+
+def mmp_fine_static(p: workloads.Problem, n: int, u_in_ptr: int, u_out_ptr: int, stats_ptr: int | None,
+                    stream=None) -> None:
+    """One fine propagation with no device allocation (scratch from the
+    library's static array); asynchronous on `stream`."""
+    dsc = desc(p)
+    _check(load().mmp_fine_static(C.byref(dsc), n, C.c_void_p(u_in_ptr), C.c_void_p(u_out_ptr),
+                                  C.c_void_p(stats_ptr or 0), C.c_void_p(_stream_handle(stream))),
+           "mmp_fine_static")
 
 
 def mmp_philox(ctr_ptr: int, key, out_ptr: int, n: int, stream=None) -> None:
