@@ -155,6 +155,37 @@ def cpu_baseline(seconds: float = 12.0) -> dict:
             "sample": f"FP64 oracle fine propagator on the config-2 model, P=2000, {slices} slices x {nf} steps ({steps:.3g} particle-steps, {dt:.1f} s)"}
 
 
+def batched_run(n_problems: int, sweeps: int, rank: int) -> dict:
+    """Config 5 (batched): n problems of the linear / double-well forms with
+    P log-uniform in [1e4, 2e6] and N in 16..128, one cooperative launch per
+    sweep; the first `sweeps` fine sweeps are timed (device time)."""
+    import torch
+
+    from paper_2310_11365_gb300 import mmp
+    from paper_2310_11365_gb300 import workloads as W
+
+    probs = W.config5(n_problems)
+    s = mmp.Solver(probs)
+    mmp.mmp_set_timing(s.ctx, True)
+    s.lift()
+    s.iterate(1)  # warm-up sweep
+    torch.cuda.synchronize()
+    mmp.mmp_timing(s.ctx, reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    s.iterate(sweeps)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    tm = mmp.mmp_timing(s.ctx, reset=True)
+    out = {"problems": n_problems, "sweeps_timed": sweeps, "ms": ms,
+           "particle_steps": tm["fine_particle_steps"], "value": tm["fine_particle_steps"] / (ms / 1e3),
+           "unit": UNIT, "fine_launches_per_sweep": tm["fine_launches"] / max(1, sweeps),
+           "sum_P": int(sum(p.P for p in probs)), "max_P": int(max(p.P for p in probs))}
+    s.close()
+    return out
+
+
 def reference_arm(args, world, rank):
     """The oracle timed as it stands on the host cores: one step = one
     Parareal iteration (fine propagator on all 64 slices + coarse/iterator
@@ -199,6 +230,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--N", type=int, default=None, help="override the slice count (profiling runs)")
     ap.add_argument("--P", type=int, default=None, help="override the particle count (profiling runs)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="also time config 5 (batched problems): number of problems (0: skip)")
+    ap.add_argument("--batch-sweeps", type=int, default=2, help="fine sweeps timed for the batched workload")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -301,6 +335,10 @@ def main():
                 "max_abs_diff_V_vs_mixed": float(np.max(np.abs(m64[:, 7] - mom[:, 7])))}
         s64.close()
 
+    batch = None
+    if args.batch > 0:
+        batch = batched_run(args.batch, args.batch_sweeps, rank)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -324,6 +362,7 @@ def main():
                          "peak_note": "152 SMs x 128 FP32/INT32 lanes x max SM clock (MEASURED_PEAKS sm_max_mhz)"},
             "e2e": e2e,
             "fp64_plain": fp64,
+            "batched_config5": batch,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": tm["fine_launches"] + tm["other_launches"],

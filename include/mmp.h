@@ -164,6 +164,41 @@ int mmp_fine_serial(mmp_ctx* ctx, int prob, int n_end, double* stats_out, void* 
 int mmp_get_plan(mmp_ctx* ctx, int prob, int* quads_per_thread, int* ctas_per_slice,
                  int* max_concurrent_slices, int* particles_in_shared);
 
+/* Replace problem `prob`'s drift and diffusion coefficients by
+ * theta = (c3, c1, kappa, c0, B0) (host, 5 doubles, finite).  The launch
+ * shape does not depend on them, so nothing is re-planned; a recorded
+ * adjoint forward run is invalidated. */
+int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta);
+
+/* Adjoint of the serial fine propagator F_{N-1} o ... o F_0 (the run the
+ * Parareal iteration converges to exactly, Property 3.3).  The paper has no
+ * adjoint; this is the reverse mode of its Euler-Maruyama recursion
+ * (Sec. 1.2), mean-field coupling included, for calibrating the model
+ * coefficients to moment targets.
+ *
+ * mmp_adjoint_workspace_size: bytes of caller-owned device workspace for a
+ * checkpoint every `ckpt_every` fine steps: one particle row per checkpoint,
+ * 3 recorded values per step, ckpt_every + 1 state rows and ckpt_every
+ * draw rows for the segment being reversed.
+ *
+ * mmp_adjoint_forward: runs the serial fine propagation from u0 with the
+ * current coefficients, recording checkpoints and per-step mean-field values
+ * into `ws`; writes the slice-end moments (M_n, V_n), n = 0..N, to host
+ * `moments_out` [(N+1) * 2] (may be NULL).  Synchronising.  Additive noise
+ * only (B = BE = 0), else MMP_ERR_UNSUPPORTED.
+ *
+ * mmp_adjoint_backward: given cotangents gm[n-1] = dL/dM_n, gv[n-1] = dL/dV_n
+ * for n = 1..N (host, N doubles each), writes dL/d(c3, c1, kappa, c0, B0)
+ * to host `grad_out` [5].  Needs the workspace of the last forward run of
+ * this problem (else MMP_ERR_STATE).  Each segment of ckpt_every steps is
+ * recomputed from its checkpoint with the same draws, then reversed with one
+ * group sum of the adjoint per step.  Synchronising. */
+int mmp_adjoint_workspace_size(mmp_ctx* ctx, int prob, int ckpt_every, size_t* bytes);
+int mmp_adjoint_forward(mmp_ctx* ctx, int prob, int ckpt_every, void* ws, size_t ws_bytes,
+                        double* moments_out);
+int mmp_adjoint_backward(mmp_ctx* ctx, int prob, const double* gm, const double* gv, void* ws,
+                         size_t ws_bytes, double* grad_out);
+
 /* Device-time accounting.  With timing on, the library records CUDA
  * events on the context stream around every fine-kernel launch and reads
  * them at its synchronisation points.  mmp_timing reports, since the last

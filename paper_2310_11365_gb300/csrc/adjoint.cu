@@ -1,0 +1,288 @@
+// adjoint.cu -- reverse-mode derivative of the serial fine propagator
+// F_{N-1} o ... o F_0 (the Euler-Maruyama particle system of Sec. 1.2 with
+// the mean field m_j = (1/P) sum_q x_{j,q}) with respect to the model
+// coefficients (c3, c1, kappa, c0, B0), for cotangents on the slice-end
+// means and population variances.
+//
+// With lambda_j = dL/dx_j:
+//   lambda_{j,q} = lambda_{j+1,q} (1 + h a_x(x_{j,q})) + (h kappa / P) sum_p lambda_{j+1,p}
+//                  + [slice-end loss at x_j],  a_x(x) = -3 c3 x^2 + c1,
+//   dL/dc3 = -h sum_{j,p} lambda_{j+1,p} x_{j,p}^3,  dL/dc1 = h sum lambda_{j+1} x_j,
+//   dL/dkappa = h sum_j m_j S_j,  dL/dc0 = h sum_j S_j,  S_j = sum_p lambda_{j+1,p},
+//   dL/dB0 = sqrt(h) sum lambda_{j+1} xi_j,
+// and a cotangent (gm, gv) on (M_n, V_n) injects gm/P + gv (2/P)(x - M_n).
+//
+// The forward run (the fine kernel with recording on) leaves a particle
+// checkpoint every c steps and the per-step uniforms it used.  Per segment,
+// in reverse: each thread recomputes its own particles over the c steps from
+// the checkpoint (no reduction is needed: the means are recorded), storing
+// states and draws, then sweeps backward with one group sum of lambda per
+// step.  The replay evaluates the step exactly as the forward kernel did,
+// so it reproduces the forward states bit for bit.
+#include <cmath>
+
+#include "adjoint.cuh"
+#include "fine_kernel.cuh"
+
+namespace mmp {
+
+namespace {
+
+// Group sum of one per-thread float as a double-float pair (same stages as
+// the forward per-step mean): the pair lands in sh.unif[0..1].
+__device__ __forceinline__ bool group_sum_f(GroupShared& sh, Group& grp) {
+  const int lane = threadIdx.x & 31;
+  float2 v = lane < kWarps ? sh.redf[lane] : make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int off = kWarps / 2; off > 0; off >>= 1) v = dd_add(v, shfl_xor_dd(v, off));
+  if (grp.G > 1) {
+    const unsigned parity = grp.epoch & 1u;
+    grp.epoch += 1;
+    float2* part = reinterpret_cast<float2*>(grp.part + (size_t)2 * grp.G * kNV) + (size_t)parity * grp.G;
+    if (lane == 0) {
+      part[grp.g] = v;
+      red_release_gpu_add(grp.counter, 1u);
+    }
+    if (!group_wait(grp)) return false;
+    v = make_float2(0.0f, 0.0f);
+    for (int c = lane; c < grp.G; c += 32) v = dd_add(v, __ldcg(part + c));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = dd_add(v, shfl_xor_dd(v, off));
+  }
+  if (lane == 0) {
+    sh.unif[0] = v.x;
+    sh.unif[1] = v.y;
+  }
+  return true;
+}
+
+}  // namespace
+
+template <typename R>
+__global__ void __launch_bounds__(kTPB, 4) k_adjoint(const AdjointArgs a) {
+  __shared__ GroupShared sh;
+  const int G = a.G;
+  const int g = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int qb = (int)(((long long)a.Q * g) / G);
+  const int qe = (int)(((long long)a.Q * (g + 1)) / G);
+  const int span = qe - qb - tid;
+  const int nq = span <= 0 ? 0 : min(a.nq, (span + kTPB - 1) / kTPB);
+  const int qlast = a.Q - 1;
+  const int plast = (int)(a.P - 4LL * qlast);
+
+  Group grp;
+  grp.part = a.partials;
+  grp.counter = a.counters;
+  grp.status = a.status;
+  grp.limit_ns = a.wait_limit_ns;
+  grp.G = G;
+  grp.g = g;
+  grp.epoch = 0;
+  if (tid == 0) sh.abort = 0;
+
+  QuadStore<R, 0> lam;  // lambda of this thread's quads, in shared memory
+  lam.bind();
+  for (int i = 0; i < nq; ++i) {
+    const R zero[4] = {0, 0, 0, 0};
+    lam.put(i, zero);
+  }
+
+  // coefficients rounded once per CTA (keeps FP64 conversions out of the loops)
+  if (sizeof(R) == 4 && tid == 0) {
+    sh.cf[0] = (float)a.h;
+    sh.cf[1] = (float)a.nc3;
+    sh.cf[2] = (float)a.c1;
+    sh.cf[3] = (float)(a.kappa * a.h / (double)a.P);
+    sh.cf[4] = (float)a.sqrt_h;
+  }
+  __syncthreads();
+  const bool fl = sizeof(R) == 4;
+  const R h = fl ? (R)sh.cf[0] : (R)a.h;
+  const R nc3 = fl ? (R)sh.cf[1] : (R)a.nc3;
+  const R c1 = fl ? (R)sh.cf[2] : (R)a.c1;
+  const R kh_p = fl ? (R)sh.cf[3] : (R)(a.kappa * a.h / (double)a.P);
+  const R sqh = fl ? (R)sh.cf[4] : (R)a.sqrt_h;
+  const R* uni = (const R*)a.uni;
+  R* segx = (R*)a.segx;
+  R* segz = (R*)a.segz;
+
+  Acc<R> acc3, acc1, accb;         // -h x^3, h x, sqrt(h) xi terms
+  double acc_k = 0.0, acc_c0 = 0.0;  // h m_j S_j, h S_j (thread 0 of CTA 0)
+
+  auto zero_tail = [&](int q, R v[4]) {
+    if (q == qlast) {
+      if (plast < 4) v[3] = (R)0;
+      if (plast < 3) v[2] = (R)0;
+      if (plast < 2) v[1] = (R)0;
+    }
+  };
+  // slice-end cotangent at global step j (a multiple of nf, j >= 1)
+  auto inject = [&](long long j, int q, const R x[4], R l[4]) {
+    const int n = (int)(j / a.nf);
+    const double M = a.mom[(size_t)n * kStat + 10];
+    const R ca = (R)(a.gm[n - 1] / (double)a.P);
+    const R cb = (R)(2.0 * a.gv[n - 1] / (double)a.P);
+    const R Mr = (R)M;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) l[w] += ca + cb * (x[w] - Mr);
+    zero_tail(q, l);
+  };
+
+  for (int seg = a.n_seg - 1; seg >= 0; --seg) {
+    const long long j0 = (long long)seg * a.c;
+    const long long j1 = min(a.J, j0 + a.c);
+    const int L = (int)(j1 - j0);
+    // ---- replay the segment from its checkpoint (thread-private) --------
+    const R* ck = (const R*)a.ckpt + (size_t)seg * a.pitch;
+    for (int i = 0; i < nq; ++i) {
+      const int q = qb + tid + i * kTPB;
+      R x[4];
+      Quad<R>::load(ck + 4 * (size_t)q, x);
+      for (int jj = 0; jj < L; ++jj) {
+        const long long j = j0 + jj;
+        Quad<R>::store(segx + (size_t)jj * a.pitch + 4 * (size_t)q, x);
+        R z[4];
+        normals4<R>(philox4x32_10(rng_counter((uint32_t)q, (uint32_t)(j % a.nf), (uint32_t)(j / a.nf), 0u,
+                                              a.ptag), a.key0, a.key1), z);
+        Quad<R>::store(segz + (size_t)jj * a.pitch + 4 * (size_t)q, z);
+        const R base = uni[3 * j + 1];  // kappa m_j + c0 as the forward used it
+        const R amp = uni[3 * j + 2];   // B0 sqrt(h) as the forward used it
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const R xv = x[w];
+          const R drift = fmaR(fmaR(nc3, xv * xv, c1), xv, base);
+          x[w] = fmaR(amp, z[w], fmaR(h, drift, xv));
+        }
+        zero_tail(q, x);
+      }
+      Quad<R>::store(segx + (size_t)L * a.pitch + 4 * (size_t)q, x);
+    }
+    // ---- backward through the segment ----------------------------------
+    R S_part = (R)0, p3 = (R)0, p1 = (R)0, pb = (R)0;
+    for (int i = 0; i < nq; ++i) {
+      const int q = qb + tid + i * kTPB;
+      R l[4], x[4], z[4];
+      lam.get(i, l);
+      // the last slice end enters here; every earlier slice end j1 < J was
+      // injected when the later segment's sweep reached its first step
+      if (j1 == a.J) {
+        Quad<R>::load(segx + (size_t)L * a.pitch + 4 * (size_t)q, x);
+        inject(j1, q, x, l);
+        lam.put(i, l);
+      }
+      Quad<R>::load(segx + (size_t)(L - 1) * a.pitch + 4 * (size_t)q, x);
+      Quad<R>::load(segz + (size_t)(L - 1) * a.pitch + 4 * (size_t)q, z);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        p3 -= l[w] * x[w] * x[w] * x[w];
+        p1 += l[w] * x[w];
+        pb += l[w] * z[w];
+        S_part += l[w];
+      }
+    }
+    for (int jj = L - 1; jj >= 0; --jj) {
+      const long long j = j0 + jj;
+      acc3.add(h * p3);
+      acc1.add(h * p1);
+      accb.add(sqh * pb);
+      // S_j = sum_p lambda_{j+1,p} over the whole ensemble
+      warp_sum_to_shared(sh, S_part);
+      __syncthreads();
+      if (warp == 0) {
+        bool ok;
+        if constexpr (sizeof(R) == 4) {
+          ok = group_sum_f(sh, grp);
+        } else {
+          ok = group_finish<1>(sh, grp, 0u, 0u);
+          if (ok && lane == 0) {
+            sh.unif[0] = 0.0f;
+            sh.uni[0] = sh.tot[0];
+          }
+        }
+        if (!ok && lane == 0) sh.abort = 1;
+      }
+      __syncthreads();
+      if (sh.abort) return;
+      double S_d;
+      R S;
+      if constexpr (sizeof(R) == 4) {
+        S = sh.unif[0] + sh.unif[1];
+        S_d = (double)sh.unif[0] + (double)sh.unif[1];
+      } else {
+        S = (R)sh.uni[0];
+        S_d = sh.uni[0];
+      }
+      if (g == 0 && tid == 0) {
+        acc_k += a.h * (double)uni[3 * j] * S_d;
+        acc_c0 += a.h * S_d;
+      }
+      __syncthreads();
+      // lambda_j, then the partials of step j - 1
+      S_part = (R)0;
+      p3 = (R)0;
+      p1 = (R)0;
+      pb = (R)0;
+      const R shift = kh_p * S;
+      const bool end_j = j > 0 && j % a.nf == 0;
+      for (int i = 0; i < nq; ++i) {
+        const int q = qb + tid + i * kTPB;
+        R l[4], x[4];
+        lam.get(i, l);
+        Quad<R>::load(segx + (size_t)jj * a.pitch + 4 * (size_t)q, x);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const R ax = fmaR((R)3 * nc3, x[w] * x[w], c1);  // -3 c3 x^2 + c1
+          l[w] = fmaR(l[w], fmaR(h, ax, (R)1), shift);
+        }
+        zero_tail(q, l);
+        if (end_j) inject(j, q, x, l);
+        lam.put(i, l);
+        if (jj > 0) {
+          R xp[4], zp[4];
+          Quad<R>::load(segx + (size_t)(jj - 1) * a.pitch + 4 * (size_t)q, xp);
+          Quad<R>::load(segz + (size_t)(jj - 1) * a.pitch + 4 * (size_t)q, zp);
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            p3 -= l[w] * xp[w] * xp[w] * xp[w];
+            p1 += l[w] * xp[w];
+            pb += l[w] * zp[w];
+            S_part += l[w];
+          }
+        }
+      }
+    }
+  }
+  // ---- reduce the parameter partials over the group (FP64) -------------
+  {
+    double v[5] = {acc3.get(), acc1.get(), acc_k, acc_c0, accb.get()};
+    warp_reduce_to_shared<5>(sh, v, 0u, 0u);
+    __syncthreads();
+    if (warp == 0 && !group_finish<5>(sh, grp, 0u, 0u) && lane == 0) sh.abort = 1;
+    __syncthreads();
+    if (sh.abort) return;
+    if (g == 0 && tid == 0) {
+      for (int k = 0; k < 5; ++k) a.grad[k] = sh.tot[k];
+      if (!(fabs(sh.tot[0]) < INFINITY) || !(fabs(sh.tot[4]) < INFINITY)) atomicOr(a.status, kStatusNumeric);
+    }
+  }
+}
+
+const void* adjoint_kernel(int precision) {
+  return precision == MMP_MIXED ? (const void*)k_adjoint<float> : (const void*)k_adjoint<double>;
+}
+
+size_t adjoint_smem_bytes(int precision, int nq) {
+  return (size_t)nq * kTPB * 4 * (precision == MMP_MIXED ? sizeof(float) : sizeof(double));
+}
+
+cudaError_t launch_adjoint(int precision, const AdjointArgs& args, cudaStream_t stream) {
+  AdjointArgs copy = args;
+  void* params[] = {&copy};
+  return cudaLaunchCooperativeKernel(adjoint_kernel(precision), dim3(args.G), dim3(kTPB), params,
+                                     adjoint_smem_bytes(precision, args.nq), stream);
+}
+
+}  // namespace mmp

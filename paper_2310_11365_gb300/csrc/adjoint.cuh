@@ -1,0 +1,39 @@
+// adjoint.cuh -- arguments of the reverse (adjoint) kernel of the serial fine
+// propagator.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mmp {
+
+struct AdjointArgs {
+  double nc3, c1, kappa, h, sqrt_h;  // model (nc3 = -c3), step
+  int nf;                            // steps per slice
+  long long J;                       // total steps N * nf
+  int c;                             // checkpoint interval
+  int n_seg;                         // ceil(J / c)
+  long long P;
+  int Q;
+  long long pitch;
+  uint32_t key0, key1, ptag;
+  int G, nq;                         // CTAs (one group), quads per thread
+  const void* ckpt;                  // rows at steps 0, c, 2c, ... (n_seg rows)
+  const void* uni;                   // [J][3] recorded (m_j, kappa m_j + c0, b offset)
+  void* segx;                        // (c + 1) rows: states of the segment being reversed
+  void* segz;                        // c rows: its normal draws
+  const double* mom;                 // [(N+1)][16] restriction records of the serial run
+  const double* gm;                  // [N] cotangents of the slice-end means (n = 1..N)
+  const double* gv;                  // [N] cotangents of the slice-end variances
+  double* grad;                      // [5] out: d/d(c3, c1, kappa, c0, B0)
+  double* partials;
+  unsigned* counters;
+  unsigned* status;
+  unsigned long long wait_limit_ns;
+};
+
+const void* adjoint_kernel(int precision);
+size_t adjoint_smem_bytes(int precision, int nq);
+cudaError_t launch_adjoint(int precision, const AdjointArgs& args, cudaStream_t stream);
+
+}  // namespace mmp

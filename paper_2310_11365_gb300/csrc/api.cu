@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include "adjoint.cuh"
+#include "batch.cuh"
 #include "driver.cuh"
 #include "fine.cuh"
 #include "misc.cuh"
@@ -44,11 +46,6 @@ using namespace mmp;
 
 namespace {
 
-// Static shared memory of the fine kernel (its reduction state), kept out
-// of the dynamic shared-memory budget.
-struct GroupSharedBytes {
-  char bytes[1024];
-};
 
 int g_last_cuda_error = 0;
 
@@ -63,6 +60,20 @@ int cuda_fail(cudaError_t e) {
   } while (0)
 
 constexpr size_t kAlign = 256;
+
+// Raises a kernel's dynamic shared-memory limit to what its static shared
+// memory leaves of the per-block opt-in maximum; returns that limit.
+int allow_dynamic_smem(const void* fn, int device, size_t* limit) {
+  int optin = 0;
+  MMP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  cudaFuncAttributes attr;
+  MMP_CUDA(cudaFuncGetAttributes(&attr, fn));
+  const int dyn = optin - (int)attr.sharedSizeBytes;
+  if (dyn <= 0) return MMP_ERR_UNSUPPORTED;
+  MMP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+  *limit = (size_t)dyn;
+  return MMP_OK;
+}
 
 struct Prob {
   mmp_problem_desc d;
@@ -87,6 +98,10 @@ struct Prob {
   bool lifted = false, done = false, converged = false;
   double last_change = 0.0;
   std::vector<int> out_buf;  // which B buffer holds the latest F_n output of slice n
+  // adjoint state: the forward run recorded into adj_ws
+  bool adj_ready = false;
+  void* adj_ws = nullptr;
+  int adj_ckpt_every = 1;
 };
 
 struct Device {
@@ -152,24 +167,33 @@ void derive(Prob& p) {
 // The layout is the shared-memory one unless MMP_FINE_LAYOUT=regs;
 // MMP_FINE_NQ=<k> restricts the choice to k quads per thread (launch-shape
 // sweeps).
-int plan(Prob& p, const Device& dev) {
+int plan(Prob& p, const Device& dev, int batch_nq = 0) {
+  if (batch_nq > 0) {
+    // many problems share one launch: the most particles per thread (the
+    // fewest CTAs, hence group barriers, per slice) within the cap
+    p.layout = kLayoutSmem;
+    p.nq = (int)std::min<long long>(batch_nq, std::max<long long>(1, ((long long)p.Q + kTPB - 1) / kTPB));
+    p.G = (int)(((long long)p.Q + (long long)p.nq * kTPB - 1) / ((long long)p.nq * kTPB));
+    p.slots_max = 1;
+    return MMP_OK;
+  }
   const char* env = std::getenv("MMP_FINE_LAYOUT");
   const int layout = (env != nullptr && std::strcmp(env, "regs") == 0) ? kLayoutRegs : kLayoutSmem;
   const char* env_nq = std::getenv("MMP_FINE_NQ");
   const int force_nq = env_nq != nullptr ? std::atoi(env_nq) : 0;
   const int max_nq = layout == kLayoutSmem ? (p.esz == 4 ? 32 : 16) : (p.esz == 4 ? 8 : 4);
   int occ_of[33] = {0};
-  int smem_optin = 0;
-  MMP_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev.dev));
   for (int nq = 1; nq <= max_nq; ++nq) {
     int occ = 0;
     const void* fn = fine_kernel(p.d.precision, layout, nq, p.mult);
     if (fn == nullptr) return MMP_ERR_UNSUPPORTED;
     const size_t smem = fine_smem_bytes(p.d.precision, layout, nq);
-    if (smem > (size_t)smem_optin - sizeof(GroupSharedBytes)) break;
-    if (layout == kLayoutSmem)
-      MMP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    smem_optin - (int)sizeof(GroupSharedBytes)));
+    if (layout == kLayoutSmem) {
+      size_t limit = 0;
+      const int rc = allow_dynamic_smem(fn, dev.dev, &limit);
+      if (rc) return rc;
+      if (smem > limit) break;
+    }
     MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, smem));
     occ_of[nq] = occ;
   }
@@ -264,6 +288,23 @@ struct mmp_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
   double fine_ms = 0.0, fine_steps = 0.0;
   long long fine_launches = 0, other_launches = 0;
+  // batched sweeps (several problems of one precision and noise form)
+  bool batch = false;
+  int batch_grid = 0;
+  size_t batch_smem = 0;
+  FineArgs* b_probs = nullptr;
+  void** b_bufs = nullptr;
+  BatchTask* b_tasks = nullptr;
+  int* b_header = nullptr;
+  unsigned* b_seat = nullptr;
+  unsigned* b_counters = nullptr;
+  double* b_partials = nullptr;
+  DriverArgs* b_dargs = nullptr;
+  int* b_sweep = nullptr;
+  double* b_summary = nullptr;
+  std::vector<BatchTask> h_tasks;
+  std::vector<int> h_sweep;
+  std::vector<double> h_summary;
   ~mmp_ctx() {
     for (auto& pr : pending) {
       cudaEventDestroy(pr.first);
@@ -275,6 +316,14 @@ struct mmp_ctx {
 
 namespace {
 
+// Quads per thread of every problem when several problems are batched:
+// MMP_BATCH_NQ overrides (launch-shape sweeps).
+int batch_nq_cap(int precision) {
+  const char* e = std::getenv("MMP_BATCH_NQ");
+  if (e != nullptr && std::atoi(e) > 0) return std::atoi(e);
+  return precision == MMP_MIXED ? 26 : 13;
+}
+
 int prepare(const mmp_problem_desc* descs, int n, std::vector<Prob>& probs, Device& dev) {
   if (descs == nullptr || n < 1) return MMP_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) {
@@ -284,35 +333,139 @@ int prepare(const mmp_problem_desc* descs, int n, std::vector<Prob>& probs, Devi
   int rc = query_device(dev);
   if (rc) return rc;
   probs.resize(n);
+  const int bnq = n > 1 ? batch_nq_cap(descs[0].precision) : 0;
   for (int i = 0; i < n; ++i) {
     probs[i].d = descs[i];
     derive(probs[i]);
-    rc = plan(probs[i], dev);
+    rc = plan(probs[i], dev, bnq);
     if (rc) return rc;
   }
   return MMP_OK;
 }
 
-// One launch of the fused fine kernel over slices [slice_begin, slice_begin + n_tasks).
-int run_fine(mmp_ctx* c, Prob& p, int slice_begin, int n_tasks, int nf, const void* src0, const void* src,
-             void* dst, int dst_fixed, const double* aff, int aff_fixed, double* stats, int stats_fixed) {
-  if (n_tasks < 1) return MMP_OK;
+// The problem-constant part of the fine kernel's arguments.
+FineArgs make_fine_args(mmp_ctx* c, const Prob& p) {
   FineArgs a;
   const mmp_problem_desc& d = p.d;
   a.nc3 = -d.c3; a.c1 = d.c1; a.kappa = d.kappa; a.c0 = d.c0;
   a.B = d.B; a.BE = d.BE; a.B0 = d.B0;
-  a.h = p.h; a.sqrt_h = p.sqrt_h; a.nf = nf;
+  a.h = p.h; a.sqrt_h = p.sqrt_h; a.nf = p.nf;
   a.P = d.P; a.Q = p.Q; a.pitch = p.pitch;
   a.n_regions = p.I; a.thr = d.threshold;
   a.key0 = p.key0; a.key1 = p.key1; a.ptag = d.problem_tag;
-  a.slice_begin = slice_begin; a.n_tasks = n_tasks;
-  a.src0 = src0; a.src = src; a.dst = dst; a.dst_fixed = dst_fixed;
-  a.aff = aff; a.aff_fixed = aff_fixed;
-  a.stats = stats; a.stats_fixed = stats_fixed;
+  a.slice_begin = 0; a.n_tasks = 0;
+  a.src0 = p.u0; a.src = nullptr; a.dst = nullptr; a.dst_fixed = 0;
+  a.aff = p.aff; a.aff_fixed = 0;
+  a.stats = p.stats; a.stats_fixed = 0;
   a.G = p.G;
   a.nq = p.nq;
   a.partials = p.partials; a.counters = p.counters; a.status = p.status;
   a.wait_limit_ns = c->limit_ns;
+  return a;
+}
+
+DriverArgs make_driver_args(const Prob& p, int sweep) {
+  DriverArgs a;
+  const mmp_problem_desc& d = p.d;
+  a.nc3 = -d.c3; a.c1 = d.c1; a.kappa = d.kappa; a.c0 = d.c0;
+  a.B = d.B; a.BE = d.BE; a.B0 = d.B0;
+  a.N = d.N; a.I = p.I; a.variant = d.variant; a.precision = d.precision;
+  a.dT = p.dT; a.hc = p.hc; a.nc = p.nc; a.thr = d.threshold; a.P = d.P;
+  a.tol = d.tol; a.max_sweeps = p.max_sweeps;
+  a.stats = p.stats; a.stats_u0 = p.stats_u0; a.rho = p.rho; a.cache = p.cache; a.aff = p.aff;
+  a.ctl = p.ctl; a.status = p.status; a.sweep = sweep;
+  return a;
+}
+
+// Batch region of the workspace (several problems of one precision and
+// noise form): per-problem kernel and driver records, the sweep's task
+// list, arrival counters and the reduction scratch of every seat.
+struct BatchLayout {
+  bool on = false;
+  int grid = 0;
+  size_t smem = 0, seats_cap = 0;
+  int tasks_cap = 0;
+};
+
+int batch_plan(const std::vector<Prob>& probs, const Device& dev, BatchLayout& B) {
+  B = BatchLayout();
+  const int n = (int)probs.size();
+  if (n < 2) return MMP_OK;
+  const char* e = std::getenv("MMP_BATCH");
+  if (e != nullptr && std::strcmp(e, "0") == 0) return MMP_OK;
+  for (const Prob& p : probs)
+    if (p.d.precision != probs[0].d.precision || p.mult != probs[0].mult) return MMP_OK;
+  int nq_max = 1;
+  for (const Prob& p : probs) {
+    nq_max = std::max(nq_max, p.nq);
+    B.tasks_cap += p.d.N;
+    B.seats_cap += (size_t)p.d.N * p.G;
+  }
+  const void* fn = fine_batch_kernel(probs[0].d.precision, probs[0].mult);
+  int occ = 0;
+  B.smem = fine_smem_bytes(probs[0].d.precision, kLayoutSmem, nq_max);
+  size_t limit = 0;
+  const int rc = allow_dynamic_smem(fn, dev.dev, &limit);
+  if (rc) return rc;
+  if (B.smem > limit) return MMP_ERR_UNSUPPORTED;
+  MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, B.smem));
+  if (occ < 1) return MMP_ERR_UNSUPPORTED;
+  B.grid = occ * dev.sms;
+  for (const Prob& p : probs)
+    if (p.G > B.grid) return MMP_ERR_UNSUPPORTED;
+  B.on = true;
+  return MMP_OK;
+}
+
+size_t batch_layout(const std::vector<Prob>& probs, const BatchLayout& B, char* base, size_t start, mmp_ctx* c) {
+  if (!B.on) return start;
+  Carver cv{base, start};
+  const int n = (int)probs.size();
+  auto ptr = [&](size_t b) -> char* {
+    const size_t at = cv.take(b);
+    return base ? base + at : nullptr;
+  };
+  char* probs_p = ptr(sizeof(FineArgs) * n);
+  char* bufs_p = ptr(sizeof(void*) * 2 * n);
+  char* tasks_p = ptr(sizeof(BatchTask) * B.tasks_cap);
+  char* header_p = ptr(sizeof(int) * 4);
+  char* seat_p = ptr(sizeof(unsigned) * 4);
+  char* counters_p = ptr(sizeof(unsigned) * B.tasks_cap);
+  char* partials_p = ptr(sizeof(double) * 2 * (kNV + 1) * B.seats_cap);
+  char* dargs_p = ptr(sizeof(DriverArgs) * n);
+  char* sweep_p = ptr(sizeof(int) * n);
+  char* summary_p = ptr(sizeof(double) * 5 * n);
+  if (c != nullptr) {
+    c->b_probs = (FineArgs*)probs_p;
+    c->b_bufs = (void**)bufs_p;
+    c->b_tasks = (BatchTask*)tasks_p;
+    c->b_header = (int*)header_p;
+    c->b_seat = (unsigned*)seat_p;
+    c->b_counters = (unsigned*)counters_p;
+    c->b_partials = (double*)partials_p;
+    c->b_dargs = (DriverArgs*)dargs_p;
+    c->b_sweep = (int*)sweep_p;
+    c->b_summary = (double*)summary_p;
+  }
+  return cv.off;
+}
+
+// One launch of the fused fine kernel over slices [slice_begin, slice_begin + n_tasks).
+int run_fine(mmp_ctx* c, Prob& p, int slice_begin, int n_tasks, int nf, const void* src0, const void* src,
+             void* dst, int dst_fixed, const double* aff, int aff_fixed, double* stats, int stats_fixed,
+             void* rec_uni = nullptr, void* rec_ckpt = nullptr, int ckpt_every = 1, long long step_offset = 0) {
+  if (n_tasks < 1) return MMP_OK;
+  const mmp_problem_desc& d = p.d;
+  FineArgs a = make_fine_args(c, p);
+  a.nf = nf;
+  a.slice_begin = slice_begin; a.n_tasks = n_tasks;
+  a.src0 = src0; a.src = src; a.dst = dst; a.dst_fixed = dst_fixed;
+  a.aff = aff; a.aff_fixed = aff_fixed;
+  a.stats = stats; a.stats_fixed = stats_fixed;
+  a.rec_uni = rec_uni;
+  a.rec_ckpt = rec_ckpt;
+  a.ckpt_every = ckpt_every;
+  a.step_offset = step_offset;
   const int slots = std::min(n_tasks, p.slots_max);
   MMP_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(unsigned) * slots, c->stream));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -351,16 +504,87 @@ int collect_timing(mmp_ctx* c) {
 }
 
 int run_driver(mmp_ctx* c, Prob& p, int sweep) {
-  DriverArgs a;
-  const mmp_problem_desc& d = p.d;
-  a.nc3 = -d.c3; a.c1 = d.c1; a.kappa = d.kappa; a.c0 = d.c0;
-  a.B = d.B; a.BE = d.BE; a.B0 = d.B0;
-  a.N = d.N; a.I = p.I; a.variant = d.variant; a.precision = d.precision;
-  a.dT = p.dT; a.hc = p.hc; a.nc = p.nc; a.thr = d.threshold; a.P = d.P;
-  a.tol = d.tol; a.max_sweeps = p.max_sweeps;
-  a.stats = p.stats; a.stats_u0 = p.stats_u0; a.rho = p.rho; a.cache = p.cache; a.aff = p.aff;
-  a.ctl = p.ctl; a.status = p.status; a.sweep = sweep;
-  MMP_CUDA(launch_driver(a, c->stream));
+  MMP_CUDA(launch_driver(make_driver_args(p, sweep), c->stream));
+  c->other_launches += 1;
+  return MMP_OK;
+}
+
+// Device records of a batched context (after layout and before any sweep).
+int batch_setup(mmp_ctx* c) {
+  const int n = (int)c->probs.size();
+  std::vector<FineArgs> fa(n);
+  std::vector<void*> bufs(2 * n);
+  std::vector<DriverArgs> da(n);
+  for (int i = 0; i < n; ++i) {
+    fa[i] = make_fine_args(c, c->probs[i]);
+    bufs[2 * i] = c->probs[i].B[0];
+    bufs[2 * i + 1] = c->probs[i].B[1];
+    da[i] = make_driver_args(c->probs[i], 0);
+  }
+  MMP_CUDA(cudaMemcpyAsync(c->b_probs, fa.data(), sizeof(FineArgs) * n, cudaMemcpyHostToDevice, c->stream));
+  MMP_CUDA(cudaMemcpyAsync(c->b_bufs, bufs.data(), sizeof(void*) * 2 * n, cudaMemcpyHostToDevice, c->stream));
+  MMP_CUDA(cudaMemcpyAsync(c->b_dargs, da.data(), sizeof(DriverArgs) * n, cudaMemcpyHostToDevice, c->stream));
+  MMP_CUDA(cudaStreamSynchronize(c->stream));
+  return MMP_OK;
+}
+
+// One batched sweep: every unconverged problem's slices k-1..N-1 in one
+// cooperative launch (largest tasks first), then every driver in one launch.
+int batch_sweep(mmp_ctx* c) {
+  const int n = (int)c->probs.size();
+  std::vector<BatchTask>& tasks = c->h_tasks;
+  std::vector<int>& sweep = c->h_sweep;
+  tasks.clear();
+  sweep.assign(n, -1);
+  for (int i = 0; i < n; ++i) {
+    Prob& p = c->probs[i];
+    if (p.done) continue;
+    const int k = p.sweeps + 1;
+    sweep[i] = k;
+    for (int sl = k - 1; sl < p.d.N; ++sl) tasks.push_back({i, sl, k == 1 ? -1 : ((k - 1) & 1), k & 1, 0, p.G});
+  }
+  if (tasks.empty()) return MMP_OK;
+  std::stable_sort(tasks.begin(), tasks.end(), [&](const BatchTask& x, const BatchTask& y) {
+    const Prob& px = c->probs[x.prob];
+    const Prob& py = c->probs[y.prob];
+    return (double)px.d.P * px.nf > (double)py.d.P * py.nf;
+  });
+  int seats = 0;
+  double steps = 0.0;
+  for (BatchTask& t : tasks) {
+    t.seat0 = seats;
+    seats += t.G;
+    steps += (double)c->probs[t.prob].d.P * c->probs[t.prob].nf;
+  }
+  const int nt = (int)tasks.size();
+  int header[4] = {nt, seats, 0, 0};
+  MMP_CUDA(cudaMemcpyAsync(c->b_tasks, tasks.data(), sizeof(BatchTask) * nt, cudaMemcpyHostToDevice, c->stream));
+  MMP_CUDA(cudaMemcpyAsync(c->b_header, header, sizeof(header), cudaMemcpyHostToDevice, c->stream));
+  MMP_CUDA(cudaMemcpyAsync(c->b_sweep, sweep.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
+  MMP_CUDA(cudaMemsetAsync(c->b_seat, 0, sizeof(unsigned) * 4, c->stream));
+  MMP_CUDA(cudaMemsetAsync(c->b_counters, 0, sizeof(unsigned) * nt, c->stream));
+  BatchArgs b;
+  b.probs = c->b_probs;
+  b.bufs = c->b_bufs;
+  b.tasks = c->b_tasks;
+  b.header = c->b_header;
+  b.seat_counter = c->b_seat;
+  b.counters = c->b_counters;
+  b.partials = c->b_partials;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->timing) {
+    MMP_CUDA(cudaEventCreate(&e0));
+    MMP_CUDA(cudaEventCreate(&e1));
+    MMP_CUDA(cudaEventRecord(e0, c->stream));
+  }
+  MMP_CUDA(launch_fine_batch(c->probs[0].d.precision, c->probs[0].mult, c->batch_grid, c->batch_smem, b, c->stream));
+  if (c->timing) {
+    MMP_CUDA(cudaEventRecord(e1, c->stream));
+    c->pending.emplace_back(e0, e1);
+  }
+  c->fine_launches += 1;
+  c->fine_steps += steps;
+  MMP_CUDA(launch_driver_batch(c->b_dargs, c->b_sweep, c->b_summary, n, c->stream));
   c->other_launches += 1;
   return MMP_OK;
 }
@@ -368,6 +592,59 @@ int run_driver(mmp_ctx* c, Prob& p, int sweep) {
 int status_to_error(unsigned s) {
   if (s & kStatusTimeout) return MMP_ERR_TIMEOUT;
   if (s & kStatusNumeric) return MMP_ERR_NUMERIC;
+  return MMP_OK;
+}
+
+// Layout of the adjoint workspace: checkpoint rows, recorded uniforms, the
+// segment buffers, cotangents, gradient and the reverse kernel's group
+// scratch; also the reverse kernel's launch shape (all particles in one
+// co-resident group, the fewest quads per thread that fit).
+struct AdjLayout {
+  size_t bytes = 0;
+  int n_seg = 0, G = 1, nq = 1;
+  void *ckpt = nullptr, *uni = nullptr, *segx = nullptr, *segz = nullptr;
+  double *gm = nullptr, *gv = nullptr, *grad = nullptr, *partials = nullptr;
+  unsigned* counters = nullptr;
+};
+
+int adjoint_layout(mmp_ctx* c, Prob& p, int ckpt_every, char* base, AdjLayout& L) {
+  const long long J = (long long)p.d.N * p.nf;
+  L.n_seg = (int)((J + ckpt_every - 1) / ckpt_every);
+  const void* fn = adjoint_kernel(p.d.precision);
+  size_t limit = 0;
+  const int arc = allow_dynamic_smem(fn, c->dev.dev, &limit);
+  if (arc) return arc;
+  const int max_nq = p.esz == 4 ? 32 : 16;
+  L.G = 0;
+  for (int nq = 1; nq <= max_nq; ++nq) {
+    int occ = 0;
+    const size_t smem = adjoint_smem_bytes(p.d.precision, nq);
+    if (smem > limit) break;
+    MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, smem));
+    const long long G = ((long long)p.Q + (long long)nq * kTPB - 1) / ((long long)nq * kTPB);
+    if (occ >= 1 && G <= (long long)occ * c->dev.sms) {
+      L.nq = nq;
+      L.G = (int)G;
+      break;
+    }
+  }
+  if (L.G == 0) return MMP_ERR_UNSUPPORTED;
+  Carver cv{base, 0};
+  const size_t row = (size_t)p.pitch * p.esz;
+  auto ptr = [&](size_t b) -> char* {
+    const size_t at = cv.take(b);
+    return base ? base + at : nullptr;
+  };
+  L.ckpt = ptr(row * L.n_seg);
+  L.uni = ptr(p.esz * 3 * (size_t)J);
+  L.segx = ptr(row * (size_t)(ckpt_every + 1));
+  L.segz = ptr(row * (size_t)ckpt_every);
+  L.gm = (double*)ptr(sizeof(double) * p.d.N);
+  L.gv = (double*)ptr(sizeof(double) * p.d.N);
+  L.grad = (double*)ptr(sizeof(double) * 8);
+  L.partials = (double*)ptr(sizeof(double) * 2 * (kNV + 1) * (size_t)L.G);
+  L.counters = (unsigned*)ptr(sizeof(unsigned) * 4);
+  L.bytes = (cv.off + kAlign - 1) / kAlign * kAlign;
   return MMP_OK;
 }
 
@@ -406,6 +683,10 @@ int mmp_workspace_size(const mmp_problem_desc* descs, int n_problems, size_t* by
   if (rc) return rc;
   size_t off = 0;
   for (Prob& p : probs) off = layout(p, nullptr, off);
+  BatchLayout B;
+  const int brc = batch_plan(probs, dev, B);
+  if (brc) return brc;
+  off = batch_layout(probs, B, nullptr, off, nullptr);
   *bytes = (off + kAlign - 1) / kAlign * kAlign;
   return MMP_OK;
 }
@@ -424,6 +705,16 @@ int mmp_create(mmp_ctx** out, const mmp_problem_desc* descs, int n_problems, voi
   }
   size_t off = 0;
   for (Prob& p : c->probs) off = layout(p, (char*)workspace, off);
+  BatchLayout B;
+  rc = batch_plan(c->probs, c->dev, B);
+  if (rc) {
+    delete c;
+    return rc;
+  }
+  off = batch_layout(c->probs, B, (char*)workspace, off, c);
+  c->batch = B.on;
+  c->batch_grid = B.grid;
+  c->batch_smem = B.smem;
   if (off > workspace_bytes) {
     delete c;
     return MMP_ERR_WORKSPACE;
@@ -441,6 +732,13 @@ int mmp_create(mmp_ctx** out, const mmp_problem_desc* descs, int n_problems, voi
     if (e != cudaSuccess) {
       delete c;
       return cuda_fail(e);
+    }
+  }
+  if (c->batch) {
+    rc = batch_setup(c);
+    if (rc) {
+      delete c;
+      return rc;
     }
   }
   *out = c;
@@ -488,6 +786,43 @@ int mmp_iterate(mmp_ctx* ctx, int n_iter, int* all_converged) {
   if (ctx == nullptr || n_iter < 0) return MMP_ERR_INVALID_ARG;
   for (Prob& p : ctx->probs)
     if (!p.lifted) return MMP_ERR_STATE;
+  if (ctx->batch) {
+    const int n = (int)ctx->probs.size();
+    ctx->h_summary.assign((size_t)5 * n, 0.0);
+    for (int it = 0; it < n_iter; ++it) {
+      bool any = false;
+      for (Prob& p : ctx->probs) any = any || !p.done;
+      if (!any) break;
+      int rc = batch_sweep(ctx);
+      if (rc) return rc;
+      MMP_CUDA(cudaMemcpyAsync(ctx->h_summary.data(), ctx->b_summary, sizeof(double) * 5 * n, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+      MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+      rc = collect_timing(ctx);
+      if (rc) return rc;
+      int err = MMP_OK;
+      for (int i = 0; i < n; ++i) {
+        Prob& p = ctx->probs[i];
+        if (ctx->h_sweep[i] < 0) continue;
+        const double* sm = &ctx->h_summary[(size_t)5 * i];
+        const int k = ctx->h_sweep[i];
+        for (int sl = k - 1; sl < p.d.N; ++sl) p.out_buf[sl] = k & 1;
+        p.sweeps = k;
+        p.last_change = sm[0];
+        p.converged = sm[1] != 0.0 || k == p.d.N;
+        p.done = sm[3] != 0.0;
+        const int e = status_to_error((unsigned)sm[4]);
+        if (e && !err) err = e;
+      }
+      if (err) return err;
+    }
+    if (all_converged) {
+      bool all = true;
+      for (Prob& p : ctx->probs) all = all && p.done;
+      *all_converged = all ? 1 : 0;
+    }
+    return MMP_OK;
+  }
   for (int it = 0; it < n_iter; ++it) {
     bool any = false;
     for (Prob& p : ctx->probs) {
@@ -617,6 +952,110 @@ int mmp_fine_serial(mmp_ctx* ctx, int prob, int n_end, double* stats_out, void* 
   unsigned st[4];
   MMP_CUDA(cudaMemcpy(st, p.status, sizeof(st), cudaMemcpyDeviceToHost));
   return status_to_error(st[0]);
+}
+
+int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  if (theta == nullptr) return MMP_ERR_INVALID_ARG;
+  for (int k = 0; k < 5; ++k)
+    if (!std::isfinite(theta[k])) return MMP_ERR_INVALID_ARG;
+  Prob& p = ctx->probs[prob];
+  p.d.c3 = theta[0];
+  p.d.c1 = theta[1];
+  p.d.kappa = theta[2];
+  p.d.c0 = theta[3];
+  p.d.B0 = theta[4];
+  p.adj_ready = false;
+  return MMP_OK;
+}
+
+int mmp_adjoint_workspace_size(mmp_ctx* ctx, int prob, int ckpt_every, size_t* bytes) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  if (bytes == nullptr || ckpt_every < 1) return MMP_ERR_INVALID_ARG;
+  Prob& p = ctx->probs[prob];
+  AdjLayout L;
+  rc = adjoint_layout(ctx, p, ckpt_every, nullptr, L);
+  if (rc) return rc;
+  *bytes = L.bytes;
+  return MMP_OK;
+}
+
+int mmp_adjoint_forward(mmp_ctx* ctx, int prob, int ckpt_every, void* ws, size_t ws_bytes, double* moments_out) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  if (ws == nullptr || ((uintptr_t)ws % kAlign) != 0 || ckpt_every < 1) return MMP_ERR_INVALID_ARG;
+  Prob& p = ctx->probs[prob];
+  if (p.mult) return MMP_ERR_UNSUPPORTED;
+  AdjLayout L;
+  rc = adjoint_layout(ctx, p, ckpt_every, (char*)ws, L);
+  if (rc) return rc;
+  if (L.bytes > ws_bytes) return MMP_ERR_WORKSPACE;
+  const int N = p.d.N;
+  // the serial fine run with recording; slice ends restricted into ser_stats
+  rc = run_fine(ctx, p, 0, 1, 0, p.u0, nullptr, nullptr, 0, nullptr, 0, p.ser_stats, 1);
+  if (rc) return rc;
+  for (int n = 0; n < N; ++n) {
+    const void* in = n == 0 ? (const void*)p.u0 : (const void*)p.S[(n - 1) & 1];
+    rc = run_fine(ctx, p, n, 1, p.nf, in, nullptr, p.S[n & 1], 1, nullptr, 0,
+                  p.ser_stats + (size_t)(n + 1) * kStat, 1, L.uni, L.ckpt, ckpt_every, (long long)n * p.nf);
+    if (rc) return rc;
+  }
+  if (moments_out) {
+    std::vector<double> st((size_t)kStat * (N + 1));
+    MMP_CUDA(cudaMemcpyAsync(st.data(), p.ser_stats, sizeof(double) * st.size(), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int n = 0; n <= N; ++n) {
+      moments_out[2 * n] = st[(size_t)n * kStat + 10];
+      moments_out[2 * n + 1] = st[(size_t)n * kStat + 11];
+    }
+  } else {
+    MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  unsigned stw[4];
+  MMP_CUDA(cudaMemcpy(stw, p.status, sizeof(stw), cudaMemcpyDeviceToHost));
+  rc = status_to_error(stw[0]);
+  if (rc) return rc;
+  p.adj_ready = true;
+  p.adj_ws = ws;
+  p.adj_ckpt_every = ckpt_every;
+  return MMP_OK;
+}
+
+int mmp_adjoint_backward(mmp_ctx* ctx, int prob, const double* gm, const double* gv, void* ws, size_t ws_bytes,
+                         double* grad_out) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  if (gm == nullptr || gv == nullptr || grad_out == nullptr || ws == nullptr) return MMP_ERR_INVALID_ARG;
+  Prob& p = ctx->probs[prob];
+  if (!p.adj_ready || p.adj_ws != ws) return MMP_ERR_STATE;
+  AdjLayout L;
+  rc = adjoint_layout(ctx, p, p.adj_ckpt_every, (char*)ws, L);
+  if (rc) return rc;
+  if (L.bytes > ws_bytes) return MMP_ERR_WORKSPACE;
+  const int N = p.d.N;
+  MMP_CUDA(cudaMemcpyAsync(L.gm, gm, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
+  MMP_CUDA(cudaMemcpyAsync(L.gv, gv, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
+  MMP_CUDA(cudaMemsetAsync(L.counters, 0, sizeof(unsigned) * 4, ctx->stream));
+  AdjointArgs a;
+  a.nc3 = -p.d.c3; a.c1 = p.d.c1; a.kappa = p.d.kappa; a.h = p.h; a.sqrt_h = p.sqrt_h;
+  a.nf = p.nf; a.J = (long long)N * p.nf; a.c = p.adj_ckpt_every; a.n_seg = L.n_seg;
+  a.P = p.d.P; a.Q = p.Q; a.pitch = p.pitch;
+  a.key0 = p.key0; a.key1 = p.key1; a.ptag = p.d.problem_tag;
+  a.G = L.G; a.nq = L.nq;
+  a.ckpt = L.ckpt; a.uni = L.uni; a.segx = L.segx; a.segz = L.segz;
+  a.mom = p.ser_stats; a.gm = L.gm; a.gv = L.gv; a.grad = L.grad;
+  a.partials = L.partials; a.counters = L.counters; a.status = p.status;
+  a.wait_limit_ns = ctx->limit_ns;
+  MMP_CUDA(launch_adjoint(p.d.precision, a, ctx->stream));
+  ctx->other_launches += 1;
+  MMP_CUDA(cudaMemcpyAsync(grad_out, L.grad, sizeof(double) * 5, cudaMemcpyDeviceToHost, ctx->stream));
+  MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  unsigned stw[4];
+  MMP_CUDA(cudaMemcpy(stw, p.status, sizeof(stw), cudaMemcpyDeviceToHost));
+  return status_to_error(stw[0]);
 }
 
 int mmp_set_timing(mmp_ctx* ctx, int on) {

@@ -1,0 +1,86 @@
+// batch.cu -- the batched fine sweep: all slices of all unconverged problems
+// in one cooperative launch.
+//
+// Seats: task t needs G_t CTAs.  Every CTA of the launch repeatedly takes the
+// next seat from a global counter; seat s belongs to the task t with
+// seat0_t <= s < seat0_t + G_t and makes the CTA rank s - seat0_t of that
+// task's group.  Seats are handed out in task order, so at most one group is
+// incomplete at any time and its members only wait for CTAs that are busy
+// with earlier, complete groups: every wait ends (and is bounded in time
+// anyway).  Tasks come largest first, so small tasks fill the tail.  A rank
+// works on the same particle range as in a per-problem launch with the same
+// group size, so a batched sweep reproduces the per-problem results bit for
+// bit.
+#include "batch.cuh"
+#include "fine_kernel.cuh"
+
+namespace mmp {
+
+template <typename R, bool MULT>
+__global__ void __launch_bounds__(kTPB, (FineOccupancy<R, 0>::value)) k_fine_batch(const BatchArgs b) {
+  __shared__ GroupShared sh;
+  __shared__ FineArgs sa;  // the current task's arguments
+  __shared__ int s_task, s_rank;
+  const int tid = threadIdx.x;
+  if (tid == 0) sh.abort = 0;
+  QuadStore<R, 0> xs;
+  xs.bind();
+  const int n_tasks = b.header[0];
+  const int total = b.header[1];
+  for (;;) {
+    if (tid == 0) {
+      const int seat = (int)atomicAdd(b.seat_counter, 1u);
+      int t = -1;
+      if (seat < total) {
+        int lo = 0, hi = n_tasks - 1;  // last task with seat0 <= seat
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (b.tasks[mid].seat0 <= seat) lo = mid;
+          else hi = mid - 1;
+        }
+        t = lo;
+        s_rank = seat - b.tasks[t].seat0;
+      }
+      s_task = t;
+    }
+    __syncthreads();
+    const int t = s_task;
+    if (t < 0) return;
+    const BatchTask tk = b.tasks[t];
+    if (tid == 0) {
+      sa = b.probs[tk.prob];
+      sa.src = tk.src_buf < 0 ? nullptr : b.bufs[2 * tk.prob + tk.src_buf];
+      sa.dst = b.bufs[2 * tk.prob + tk.dst_buf];
+      sa.dst_fixed = 0;
+      sa.aff_fixed = 0;
+      sa.stats_fixed = 0;
+    }
+    __syncthreads();
+    Group grp;
+    grp.part = b.partials + (size_t)tk.seat0 * 2 * (kNV + 1);
+    grp.counter = b.counters + t;
+    grp.status = sa.status;
+    grp.limit_ns = sa.wait_limit_ns;
+    grp.G = tk.G;
+    grp.g = s_rank;
+    grp.epoch = 0;
+    if (!fine_task<R, 0, MULT>(sa, tk.slice, s_rank, grp, sh, xs)) return;
+    __syncthreads();
+  }
+}
+
+const void* fine_batch_kernel(int precision, bool mult) {
+  if (precision == MMP_MIXED)
+    return mult ? (const void*)k_fine_batch<float, true> : (const void*)k_fine_batch<float, false>;
+  return mult ? (const void*)k_fine_batch<double, true> : (const void*)k_fine_batch<double, false>;
+}
+
+cudaError_t launch_fine_batch(int precision, bool mult, int grid, size_t smem, const BatchArgs& args,
+                              cudaStream_t stream) {
+  BatchArgs copy = args;
+  void* params[] = {&copy};
+  return cudaLaunchCooperativeKernel(fine_batch_kernel(precision, mult), dim3(grid), dim3(kTPB), params, smem,
+                                     stream);
+}
+
+}  // namespace mmp

@@ -226,7 +226,7 @@ __device__ bool lsq_fit(const DriverArgs& a, int npts, double p0, double& alpha,
 
 // One warp per problem.  sweep == 0: lifting (k = 0).  sweep k >= 1: the
 // coarse/iterator sweep after fine sweep k, Eq. (mM_parareal_other_k_NEW).
-__global__ void __launch_bounds__(32) k_driver(const DriverArgs a) {
+__device__ void driver_body(const DriverArgs& a) {
   const int lane = threadIdx.x & 31;
   const int N = a.N, I = a.I;
   double* ctl = a.ctl;
@@ -363,8 +363,36 @@ __global__ void __launch_bounds__(32) k_driver(const DriverArgs a) {
   ctl[8] = learn ? 1.0 : 0.0;
 }
 
+__global__ void __launch_bounds__(32) k_driver(const DriverArgs a) { driver_body(a); }
+
+// Batched form: block b drives problem b if its sweep index is >= 0 this
+// round, then copies (change, converged, sweeps, done, status) into
+// summary[5 b ..].
+__global__ void __launch_bounds__(32) k_driver_batch(const DriverArgs* args, const int* sweep, double* summary,
+                                                     int n) {
+  const int b = blockIdx.x;
+  if (b >= n) return;
+  const int k = sweep[b];
+  if (k < 0) return;
+  DriverArgs a = args[b];
+  a.sweep = k;
+  driver_body(a);
+  __syncwarp();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 4; ++i) summary[5 * b + i] = a.ctl[i];
+    summary[5 * b + 4] = (double)*(volatile unsigned*)a.status;
+  }
+}
+
 cudaError_t launch_driver(const DriverArgs& args, cudaStream_t stream) {
   k_driver<<<1, 32, 0, stream>>>(args);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_driver_batch(const DriverArgs* args, const int* sweep, double* summary, int n,
+                                cudaStream_t stream) {
+  if (n < 1) return cudaSuccess;
+  k_driver_batch<<<n, 32, 0, stream>>>(args, sweep, summary, n);
   return cudaGetLastError();
 }
 

@@ -25,5 +25,10 @@ struct DriverArgs {
 };
 
 cudaError_t launch_driver(const DriverArgs& args, cudaStream_t stream);
+// One warp per problem over a device array of arguments; sweep[b] < 0 skips
+// problem b.  summary[5 b ..] receives (change, converged, sweeps, done,
+// status word).
+cudaError_t launch_driver_batch(const DriverArgs* args, const int* sweep, double* summary, int n,
+                                cudaStream_t stream);
 
 }  // namespace mmp

@@ -34,6 +34,11 @@ struct FineArgs {
   unsigned* counters;          // [slot] group-barrier arrival counters (zeroed per launch)
   unsigned* status;            // device status word
   unsigned long long wait_limit_ns;
+  // optional recording for the adjoint (serial runs only, one task):
+  void* rec_uni = nullptr;     // [global step][3] (m_j, kappa m_j + c0, (BE m_j + B0) sqrt h), precision R
+  void* rec_ckpt = nullptr;    // particle rows at global steps 0, c, 2c, ... (row gstep / c)
+  int ckpt_every = 1;          // c
+  long long step_offset = 0;   // global index of this slice's first step
 };
 
 // Particle layouts of the fine kernel: quads in registers (a template per

@@ -33,6 +33,7 @@ EXPORTED = [
     "mmp_destroy", "mmp_set_initial", "mmp_lift", "mmp_iterate", "mmp_run", "mmp_status",
     "mmp_get_moments", "mmp_get_particles", "mmp_fine_serial", "mmp_fine", "mmp_philox",
     "mmp_normals", "mmp_get_plan", "mmp_set_timing", "mmp_timing", "mmp_fine_static",
+    "mmp_set_params", "mmp_adjoint_workspace_size", "mmp_adjoint_forward", "mmp_adjoint_backward",
 ]
 
 
@@ -94,6 +95,10 @@ def load():
         "mmp_set_timing": ([vp, i], i),
         "mmp_timing": ([vp, i, d, C.POINTER(ll), d, C.POINTER(ll)], i),
         "mmp_fine_static": ([pd, i, vp, vp, vp, vp], i),
+        "mmp_set_params": ([vp, i, d], i),
+        "mmp_adjoint_workspace_size": ([vp, i, i, C.POINTER(C.c_size_t)], i),
+        "mmp_adjoint_forward": ([vp, i, i, vp, C.c_size_t, d], i),
+        "mmp_adjoint_backward": ([vp, i, d, d, vp, C.c_size_t, d], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -239,6 +244,34 @@ def mmp_fine_static(p: workloads.Problem, n: int, u_in_ptr: int, u_out_ptr: int,
            "mmp_fine_static")
 
 
+def mmp_set_params(ctx, prob: int, theta) -> None:
+    t = np.ascontiguousarray(theta, dtype=np.float64)
+    _check(load().mmp_set_params(ctx, prob, t.ctypes.data_as(C.POINTER(C.c_double))), "mmp_set_params")
+
+
+def mmp_adjoint_workspace_size(ctx, prob: int, ckpt_every: int) -> int:
+    n = C.c_size_t()
+    _check(load().mmp_adjoint_workspace_size(ctx, prob, ckpt_every, C.byref(n)), "mmp_adjoint_workspace_size")
+    return n.value
+
+
+def mmp_adjoint_forward(ctx, prob: int, ckpt_every: int, ws_ptr: int, ws_bytes: int, N: int) -> np.ndarray:
+    mom = np.empty(2 * (N + 1), np.float64)
+    _check(load().mmp_adjoint_forward(ctx, prob, ckpt_every, C.c_void_p(ws_ptr), ws_bytes,
+                                      mom.ctypes.data_as(C.POINTER(C.c_double))), "mmp_adjoint_forward")
+    return mom.reshape(N + 1, 2)
+
+
+def mmp_adjoint_backward(ctx, prob: int, gm, gv, ws_ptr: int, ws_bytes: int) -> np.ndarray:
+    gma = np.ascontiguousarray(gm, dtype=np.float64)
+    gva = np.ascontiguousarray(gv, dtype=np.float64)
+    grad = np.empty(5, np.float64)
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    _check(load().mmp_adjoint_backward(ctx, prob, dp(gma), dp(gva), C.c_void_p(ws_ptr), ws_bytes, dp(grad)),
+           "mmp_adjoint_backward")
+    return grad
+
+
 def mmp_philox(ctr_ptr: int, key, out_ptr: int, n: int, stream=None) -> None:
     k = (C.c_uint * 2)(int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF)
     _check(load().mmp_philox(C.c_void_p(ctr_ptr), k, C.c_void_p(out_ptr), n,
@@ -323,3 +356,70 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ---- adjoint as a torch.autograd.Function -----------------------------------
+
+THETA_NAMES = ("c3", "c1", "kappa", "c0", "B0")
+
+
+class Adjoint:
+    """Caller-owned adjoint workspace for one problem of a Solver."""
+
+    def __init__(self, solver: Solver, prob: int = 0, ckpt_every: int = 64):
+        import torch
+
+        self.solver, self.prob, self.ckpt_every = solver, prob, ckpt_every
+        self.nbytes = mmp_adjoint_workspace_size(solver.ctx, prob, ckpt_every)
+        self.ws = torch.empty(max(self.nbytes, 256), dtype=torch.uint8, device="cuda")
+
+    def forward(self, theta) -> np.ndarray:
+        mmp_set_params(self.solver.ctx, self.prob, theta)
+        return mmp_adjoint_forward(self.solver.ctx, self.prob, self.ckpt_every, self.ws.data_ptr(), self.nbytes,
+                                   self.solver.problems[self.prob].N)
+
+    def backward(self, gm, gv) -> np.ndarray:
+        return mmp_adjoint_backward(self.solver.ctx, self.prob, gm, gv, self.ws.data_ptr(), self.nbytes)
+
+
+def _autograd_function():
+    import torch
+
+    class FineMoments(torch.autograd.Function):
+        """theta = (c3, c1, kappa, c0, B0) -> slice-end moments [(N+1), 2]
+        (mean, population variance) of the serial fine run; the backward is
+        the library's adjoint kernel."""
+
+        @staticmethod
+        def forward(ctx, theta, adj):
+            mom = adj.forward(theta.detach().cpu().double().numpy())
+            ctx.adj = adj
+            return torch.from_numpy(mom).to(theta.dtype)
+
+        @staticmethod
+        def backward(ctx, g):
+            g = g.detach().cpu().double().numpy()
+            grad = ctx.adj.backward(g[1:, 0], g[1:, 1])
+            return torch.from_numpy(grad), None
+
+    return FineMoments
+
+
+FineMoments = None
+
+
+def fine_moments(theta, adj: Adjoint):
+    """Differentiable slice-end moments of the serial fine run."""
+    global FineMoments
+    if FineMoments is None:
+        FineMoments = _autograd_function()
+    return FineMoments.apply(theta, adj)
+
+
+def double_well_theta(kappa, sigma, a, b):
+    """theta of dX = (-V'(X) + kappa (E[X] - X)) dt + sigma dW, V = a x^4 - b x^2,
+    built with torch operations so that gradients flow to (kappa, sigma, a, b)."""
+    import torch
+
+    zero = torch.zeros((), dtype=torch.float64)
+    return torch.stack([4 * a, 2 * b - kappa, kappa, zero, sigma])
