@@ -13,7 +13,8 @@
 // and a cotangent (gm, gv) on (M_n, V_n) injects gm/P + gv (2/P)(x - M_n).
 //
 // The forward run (the fine kernel with recording on) leaves a particle
-// checkpoint every c steps and the per-step uniforms it used.  Per segment,
+// checkpoint every c steps and the per-step uniforms it used (the mean m_j,
+// the common shift d_j = h (kappa m_j + c0) and the noise amplitude).  Per segment,
 // in reverse: each thread recomputes its own particles over the c steps from
 // the checkpoint (no reduction is needed: the means are recorded), storing
 // states and draws, then sweeps backward with one group sum of lambda per
@@ -25,38 +26,6 @@
 #include "fine_kernel.cuh"
 
 namespace mmp {
-
-namespace {
-
-// Group sum of one per-thread float as a double-float pair (same stages as
-// the forward per-step mean): the pair lands in sh.unif[0..1].
-__device__ __forceinline__ bool group_sum_f(GroupShared& sh, Group& grp) {
-  const int lane = threadIdx.x & 31;
-  float2 v = lane < kWarps ? sh.redf[lane] : make_float2(0.0f, 0.0f);
-#pragma unroll
-  for (int off = kWarps / 2; off > 0; off >>= 1) v = dd_add(v, shfl_xor_dd(v, off));
-  if (grp.G > 1) {
-    const unsigned parity = grp.epoch & 1u;
-    grp.epoch += 1;
-    float2* part = reinterpret_cast<float2*>(grp.part + (size_t)2 * grp.G * kNV) + (size_t)parity * grp.G;
-    if (lane == 0) {
-      part[grp.g] = v;
-      red_release_gpu_add(grp.counter, 1u);
-    }
-    if (!group_wait(grp)) return false;
-    v = make_float2(0.0f, 0.0f);
-    for (int c = lane; c < grp.G; c += 32) v = dd_add(v, __ldcg(part + c));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = dd_add(v, shfl_xor_dd(v, off));
-  }
-  if (lane == 0) {
-    sh.unif[0] = v.x;
-    sh.unif[1] = v.y;
-  }
-  return true;
-}
-
-}  // namespace
 
 template <typename R>
 __global__ void __launch_bounds__(kTPB, 4) k_adjoint(const AdjointArgs a) {
@@ -75,7 +44,8 @@ __global__ void __launch_bounds__(kTPB, 4) k_adjoint(const AdjointArgs a) {
 
   Group grp;
   grp.part = a.partials;
-  grp.counter = a.counters;
+  grp.flags = a.flags;
+  grp.tags = a.tags;
   grp.status = a.status;
   grp.limit_ns = a.wait_limit_ns;
   grp.G = G;
@@ -97,6 +67,8 @@ __global__ void __launch_bounds__(kTPB, 4) k_adjoint(const AdjointArgs a) {
     sh.cf[2] = (float)a.c1;
     sh.cf[3] = (float)(a.kappa * a.h / (double)a.P);
     sh.cf[4] = (float)a.sqrt_h;
+    sh.cf[5] = (float)(a.h * a.nc3);
+    sh.cf[6] = (float)(a.h * a.c1);
   }
   __syncthreads();
   const bool fl = sizeof(R) == 4;
@@ -105,6 +77,8 @@ __global__ void __launch_bounds__(kTPB, 4) k_adjoint(const AdjointArgs a) {
   const R c1 = fl ? (R)sh.cf[2] : (R)a.c1;
   const R kh_p = fl ? (R)sh.cf[3] : (R)(a.kappa * a.h / (double)a.P);
   const R sqh = fl ? (R)sh.cf[4] : (R)a.sqrt_h;
+  const R hn3 = fl ? (R)sh.cf[5] : (R)(a.h * a.nc3);  // as the forward rounds them
+  const R hc1 = fl ? (R)sh.cf[6] : (R)(a.h * a.c1);
   const R* uni = (const R*)a.uni;
   R* segx = (R*)a.segx;
   R* segz = (R*)a.segz;
@@ -148,14 +122,10 @@ __global__ void __launch_bounds__(kTPB, 4) k_adjoint(const AdjointArgs a) {
         normals4<R>(philox4x32_10(rng_counter((uint32_t)q, (uint32_t)(j % a.nf), (uint32_t)(j / a.nf), 0u,
                                               a.ptag), a.key0, a.key1), z);
         Quad<R>::store(segz + (size_t)jj * a.pitch + 4 * (size_t)q, z);
-        const R base = uni[3 * j + 1];  // kappa m_j + c0 as the forward used it
-        const R amp = uni[3 * j + 2];   // B0 sqrt(h) as the forward used it
+        const R d = uni[3 * j + 1];    // h (kappa m_j + c0) as the forward used it
+        const R amp = uni[3 * j + 2];  // B0 sqrt(h) as the forward used it
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const R xv = x[w];
-          const R drift = fmaR(fmaR(nc3, xv * xv, c1), xv, base);
-          x[w] = fmaR(amp, z[w], fmaR(h, drift, xv));
-        }
+        for (int w = 0; w < 4; ++w) x[w] = addR(em_partial(x[w], z[w], hn3, hc1, amp), d);
         zero_tail(q, x);
       }
       Quad<R>::store(segx + (size_t)L * a.pitch + 4 * (size_t)q, x);
@@ -188,38 +158,38 @@ __global__ void __launch_bounds__(kTPB, 4) k_adjoint(const AdjointArgs a) {
       acc3.add(h * p3);
       acc1.add(h * p1);
       accb.add(sqh * pb);
-      // S_j = sum_p lambda_{j+1,p} over the whole ensemble
-      warp_sum_to_shared(sh, S_part);
+      // S_j = sum_p lambda_{j+1,p} over the whole ensemble (warp 0 does the
+      // cross-CTA exchange; the other warps wait at the second barrier)
+      step_sum_warp<R>(sh, jj & 1, S_part);
       __syncthreads();
-      if (warp == 0) {
-        bool ok;
-        if constexpr (sizeof(R) == 4) {
-          ok = group_sum_f(sh, grp);
-        } else {
-          ok = group_finish<1>(sh, grp, 0u, 0u);
-          if (ok && lane == 0) {
-            sh.unif[0] = 0.0f;
-            sh.uni[0] = sh.tot[0];
+      {
+        const unsigned e = grp.epoch++;
+        if (warp == 0) {
+          typename StepSum<R>::T sum = step_sum_cta<R>(sh, jj & 1);
+          if (G > 1 && lane == 0) StepSum<R>::publish(grp, e, sum);
+          const bool ok = G == 1 || StepSum<R>::fetch(grp, e, sum);
+          if (lane == 0) {
+            StepSum<R>::gsum(sh, jj & 1) = sum;
+            if (!ok) sh.abort = 1;
           }
         }
-        if (!ok && lane == 0) sh.abort = 1;
       }
       __syncthreads();
       if (sh.abort) return;
+      const typename StepSum<R>::T Ssum = StepSum<R>::gsum(sh, jj & 1);
       double S_d;
       R S;
       if constexpr (sizeof(R) == 4) {
-        S = sh.unif[0] + sh.unif[1];
-        S_d = (double)sh.unif[0] + (double)sh.unif[1];
+        S = Ssum.x + Ssum.y;
+        S_d = (double)Ssum.x + (double)Ssum.y;
       } else {
-        S = (R)sh.uni[0];
-        S_d = sh.uni[0];
+        S = (R)Ssum;
+        S_d = Ssum;
       }
       if (g == 0 && tid == 0) {
         acc_k += a.h * (double)uni[3 * j] * S_d;
         acc_c0 += a.h * S_d;
       }
-      __syncthreads();
       // lambda_j, then the partials of step j - 1
       S_part = (R)0;
       p3 = (R)0;
@@ -260,7 +230,9 @@ __global__ void __launch_bounds__(kTPB, 4) k_adjoint(const AdjointArgs a) {
     double v[5] = {acc3.get(), acc1.get(), acc_k, acc_c0, accb.get()};
     warp_reduce_to_shared<5>(sh, v, 0u, 0u);
     __syncthreads();
-    if (warp == 0 && !group_finish<5>(sh, grp, 0u, 0u) && lane == 0) sh.abort = 1;
+    if (sh.abort) return;
+    const unsigned e = grp.epoch++;
+    if (warp == 0 && !group_finish<5>(sh, grp, e, 0u, 0u) && lane == 0) sh.abort = 1;
     __syncthreads();
     if (sh.abort) return;
     if (g == 0 && tid == 0) {

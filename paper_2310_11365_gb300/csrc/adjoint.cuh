@@ -19,15 +19,16 @@ struct AdjointArgs {
   uint32_t key0, key1, ptag;
   int G, nq;                         // CTAs (one group), quads per thread
   const void* ckpt;                  // rows at steps 0, c, 2c, ... (n_seg rows)
-  const void* uni;                   // [J][3] recorded (m_j, kappa m_j + c0, b offset)
+  const void* uni;                   // [J][3] recorded (m_j, h (kappa m_j + c0), B0 sqrt h)
   void* segx;                        // (c + 1) rows: states of the segment being reversed
   void* segz;                        // c rows: its normal draws
   const double* mom;                 // [(N+1)][16] restriction records of the serial run
   const double* gm;                  // [N] cotangents of the slice-end means (n = 1..N)
   const double* gv;                  // [N] cotangents of the slice-end variances
   double* grad;                      // [5] out: d/d(c3, c1, kappa, c0, B0)
-  double* partials;
-  unsigned* counters;
+  double* partials;                  // [G][kSlots][kNV] group publication slots
+  unsigned* flags;                   // [G] epoch flags (zeroed per launch)
+  unsigned long long* tags;          // [kSlots][G] tagged step words (zeroed per launch)
   unsigned* status;
   unsigned long long wait_limit_ns;
 };

@@ -92,7 +92,8 @@ struct Prob {
   char* S[2] = {nullptr, nullptr};
   double *stats = nullptr, *stats_u0 = nullptr, *ser_stats = nullptr, *tmp_stats = nullptr;
   double *rho = nullptr, *cache = nullptr, *aff = nullptr, *ctl = nullptr, *partials = nullptr;
-  unsigned *counters = nullptr, *status = nullptr;
+  unsigned *flags = nullptr, *status = nullptr;
+  unsigned long long* tags = nullptr;  // followed by flags: one block, cleared per launch
   // host view of the iteration
   int sweeps = 0;
   bool lifted = false, done = false, converged = false;
@@ -240,6 +241,12 @@ struct Carver {
   }
 };
 
+// Bytes of a problem's synchronisation block: tagged step words
+// [slot][kSlots][G], then epoch flags [slot][G].
+size_t sync_bytes(const Prob& p) {
+  return (sizeof(unsigned long long) * kSlots + sizeof(unsigned)) * (size_t)p.slots_max * p.G;
+}
+
 // Lays out (or, with base == nullptr, sizes) one problem's workspace.
 size_t layout(Prob& p, char* base, size_t start) {
   Carver c{base, start};
@@ -262,8 +269,9 @@ size_t layout(Prob& p, char* base, size_t start) {
   p.cache = (double*)ptr(sizeof(double) * 4 * N);
   p.aff = (double*)ptr(sizeof(double) * 2 * kAff * (N + 1));
   p.ctl = (double*)ptr(sizeof(double) * 16);
-  p.partials = (double*)ptr(sizeof(double) * 2 * (kNV + 1) * (size_t)p.slots_max * p.G);
-  p.counters = (unsigned*)ptr(sizeof(unsigned) * p.slots_max);
+  p.partials = (double*)ptr(sizeof(double) * kSeatDoubles * (size_t)p.slots_max * p.G);
+  p.tags = (unsigned long long*)ptr(sync_bytes(p));
+  p.flags = base ? (unsigned*)(p.tags + (size_t)p.slots_max * kSlots * p.G) : nullptr;
   p.status = (unsigned*)ptr(sizeof(unsigned) * 4);
   return c.off;
 }
@@ -297,7 +305,8 @@ struct mmp_ctx {
   BatchTask* b_tasks = nullptr;
   int* b_header = nullptr;
   unsigned* b_seat = nullptr;
-  unsigned* b_counters = nullptr;
+  unsigned* b_flags = nullptr;
+  unsigned long long* b_tags = nullptr;
   double* b_partials = nullptr;
   DriverArgs* b_dargs = nullptr;
   int* b_sweep = nullptr;
@@ -359,7 +368,7 @@ FineArgs make_fine_args(mmp_ctx* c, const Prob& p) {
   a.stats = p.stats; a.stats_fixed = 0;
   a.G = p.G;
   a.nq = p.nq;
-  a.partials = p.partials; a.counters = p.counters; a.status = p.status;
+  a.partials = p.partials; a.flags = p.flags; a.tags = p.tags; a.status = p.status;
   a.wait_limit_ns = c->limit_ns;
   return a;
 }
@@ -379,7 +388,7 @@ DriverArgs make_driver_args(const Prob& p, int sweep) {
 
 // Batch region of the workspace (several problems of one precision and
 // noise form): per-problem kernel and driver records, the sweep's task
-// list, arrival counters and the reduction scratch of every seat.
+// list, and the epoch flags and publication slots of every seat.
 struct BatchLayout {
   bool on = false;
   int grid = 0;
@@ -430,8 +439,9 @@ size_t batch_layout(const std::vector<Prob>& probs, const BatchLayout& B, char* 
   char* tasks_p = ptr(sizeof(BatchTask) * B.tasks_cap);
   char* header_p = ptr(sizeof(int) * 4);
   char* seat_p = ptr(sizeof(unsigned) * 4);
-  char* counters_p = ptr(sizeof(unsigned) * B.tasks_cap);
-  char* partials_p = ptr(sizeof(double) * 2 * (kNV + 1) * B.seats_cap);
+  char* flags_p = ptr(sizeof(unsigned) * B.seats_cap);
+  char* tags_p = ptr(sizeof(unsigned long long) * kSlots * B.seats_cap);
+  char* partials_p = ptr(sizeof(double) * kSeatDoubles * B.seats_cap);
   char* dargs_p = ptr(sizeof(DriverArgs) * n);
   char* sweep_p = ptr(sizeof(int) * n);
   char* summary_p = ptr(sizeof(double) * 5 * n);
@@ -441,7 +451,8 @@ size_t batch_layout(const std::vector<Prob>& probs, const BatchLayout& B, char* 
     c->b_tasks = (BatchTask*)tasks_p;
     c->b_header = (int*)header_p;
     c->b_seat = (unsigned*)seat_p;
-    c->b_counters = (unsigned*)counters_p;
+    c->b_flags = (unsigned*)flags_p;
+    c->b_tags = (unsigned long long*)tags_p;
     c->b_partials = (double*)partials_p;
     c->b_dargs = (DriverArgs*)dargs_p;
     c->b_sweep = (int*)sweep_p;
@@ -467,7 +478,7 @@ int run_fine(mmp_ctx* c, Prob& p, int slice_begin, int n_tasks, int nf, const vo
   a.ckpt_every = ckpt_every;
   a.step_offset = step_offset;
   const int slots = std::min(n_tasks, p.slots_max);
-  MMP_CUDA(cudaMemsetAsync(p.counters, 0, sizeof(unsigned) * slots, c->stream));
+  MMP_CUDA(cudaMemsetAsync(p.tags, 0, sync_bytes(p), c->stream));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
     for (cudaEvent_t* e : {&e0, &e1}) {
@@ -562,14 +573,16 @@ int batch_sweep(mmp_ctx* c) {
   MMP_CUDA(cudaMemcpyAsync(c->b_header, header, sizeof(header), cudaMemcpyHostToDevice, c->stream));
   MMP_CUDA(cudaMemcpyAsync(c->b_sweep, sweep.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
   MMP_CUDA(cudaMemsetAsync(c->b_seat, 0, sizeof(unsigned) * 4, c->stream));
-  MMP_CUDA(cudaMemsetAsync(c->b_counters, 0, sizeof(unsigned) * nt, c->stream));
+  MMP_CUDA(cudaMemsetAsync(c->b_flags, 0, sizeof(unsigned) * seats, c->stream));
+  MMP_CUDA(cudaMemsetAsync(c->b_tags, 0, sizeof(unsigned long long) * kSlots * seats, c->stream));
   BatchArgs b;
   b.probs = c->b_probs;
   b.bufs = c->b_bufs;
   b.tasks = c->b_tasks;
   b.header = c->b_header;
   b.seat_counter = c->b_seat;
-  b.counters = c->b_counters;
+  b.flags = c->b_flags;
+  b.tags = c->b_tags;
   b.partials = c->b_partials;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
@@ -604,7 +617,8 @@ struct AdjLayout {
   int n_seg = 0, G = 1, nq = 1;
   void *ckpt = nullptr, *uni = nullptr, *segx = nullptr, *segz = nullptr;
   double *gm = nullptr, *gv = nullptr, *grad = nullptr, *partials = nullptr;
-  unsigned* counters = nullptr;
+  unsigned* flags = nullptr;
+  unsigned long long* tags = nullptr;  // followed by flags
 };
 
 int adjoint_layout(mmp_ctx* c, Prob& p, int ckpt_every, char* base, AdjLayout& L) {
@@ -642,8 +656,9 @@ int adjoint_layout(mmp_ctx* c, Prob& p, int ckpt_every, char* base, AdjLayout& L
   L.gm = (double*)ptr(sizeof(double) * p.d.N);
   L.gv = (double*)ptr(sizeof(double) * p.d.N);
   L.grad = (double*)ptr(sizeof(double) * 8);
-  L.partials = (double*)ptr(sizeof(double) * 2 * (kNV + 1) * (size_t)L.G);
-  L.counters = (unsigned*)ptr(sizeof(unsigned) * 4);
+  L.partials = (double*)ptr(sizeof(double) * kSeatDoubles * (size_t)L.G);
+  L.tags = (unsigned long long*)ptr((sizeof(unsigned long long) * kSlots + sizeof(unsigned)) * (size_t)L.G);
+  L.flags = base ? (unsigned*)(L.tags + (size_t)kSlots * L.G) : nullptr;
   L.bytes = (cv.off + kAlign - 1) / kAlign * kAlign;
   return MMP_OK;
 }
@@ -1038,7 +1053,8 @@ int mmp_adjoint_backward(mmp_ctx* ctx, int prob, const double* gm, const double*
   const int N = p.d.N;
   MMP_CUDA(cudaMemcpyAsync(L.gm, gm, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
   MMP_CUDA(cudaMemcpyAsync(L.gv, gv, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
-  MMP_CUDA(cudaMemsetAsync(L.counters, 0, sizeof(unsigned) * 4, ctx->stream));
+  MMP_CUDA(cudaMemsetAsync(L.tags, 0, (sizeof(unsigned long long) * kSlots + sizeof(unsigned)) * L.G,
+                           ctx->stream));
   AdjointArgs a;
   a.nc3 = -p.d.c3; a.c1 = p.d.c1; a.kappa = p.d.kappa; a.h = p.h; a.sqrt_h = p.sqrt_h;
   a.nf = p.nf; a.J = (long long)N * p.nf; a.c = p.adj_ckpt_every; a.n_seg = L.n_seg;
@@ -1047,7 +1063,7 @@ int mmp_adjoint_backward(mmp_ctx* ctx, int prob, const double* gm, const double*
   a.G = L.G; a.nq = L.nq;
   a.ckpt = L.ckpt; a.uni = L.uni; a.segx = L.segx; a.segz = L.segz;
   a.mom = p.ser_stats; a.gm = L.gm; a.gv = L.gv; a.grad = L.grad;
-  a.partials = L.partials; a.counters = L.counters; a.status = p.status;
+  a.partials = L.partials; a.flags = L.flags; a.tags = L.tags; a.status = p.status;
   a.wait_limit_ns = ctx->limit_ns;
   MMP_CUDA(launch_adjoint(p.d.precision, a, ctx->stream));
   ctx->other_launches += 1;
@@ -1141,16 +1157,20 @@ int mmp_normals(const mmp_problem_desc* desc, int tag, unsigned int j, unsigned 
 // hand the whole device pool to another allocator and forbid allocations in
 // their inner loop, and latency-bound loops where an allocation could stall.
 // They own their ensembles; what they cannot provide is the scratch that the
-// fine kernel's cross-CTA mean reduction needs (partial sums and arrival
-// counters).  This entry point takes that scratch from one fixed array
+// fine kernel's cross-CTA mean reduction needs (publication slots and
+// epoch flags).  This entry point takes that scratch from one fixed array
 // compiled into the library instead of a caller workspace.
 // ---------------------------------------------------------------------------
 
-// CTAs per slice the array serves: partials [2][MMP_STATIC_MAX_CTAS][kNV]
-// doubles, then an arrival counter, a status word and one restriction row.
+// CTAs per slice the array serves: publication slots
+// [MMP_STATIC_MAX_CTAS][kSlots][kNV] doubles, then the control block (the
+// tagged step words [kSlots][MMP_STATIC_MAX_CTAS], one epoch flag per CTA
+// and the status word) and one restriction row.
 static_assert(MMP_STATIC_MAX_CTAS == 1216, "keep the header and the array in step");
-constexpr size_t kStaticPartialDoubles = 2 * (size_t)MMP_STATIC_MAX_CTAS * (kNV + 1);
-constexpr size_t kStaticDoubles = kStaticPartialDoubles + 8 + kStat;
+constexpr size_t kStaticPartialDoubles = (size_t)MMP_STATIC_MAX_CTAS * kSeatDoubles;
+constexpr size_t kStaticTagDoubles = (size_t)kSlots * MMP_STATIC_MAX_CTAS;
+constexpr size_t kStaticCtlDoubles = kStaticTagDoubles + MMP_STATIC_MAX_CTAS / 2 + 8;
+constexpr size_t kStaticDoubles = kStaticPartialDoubles + kStaticCtlDoubles + kStat;
 static __device__ __align__(256) double mmp_static_scratch[kStaticDoubles];
 
 namespace {
@@ -1200,11 +1220,13 @@ extern "C" int mmp_fine_static(const mmp_problem_desc* desc, int n, const void* 
   double* base = nullptr;
   rc = static_scratch(&base);
   if (rc) return rc;
-  unsigned* ctl = (unsigned*)(base + kStaticPartialDoubles);  // [0] counter, [1] status
-  double* stats = stats_dev != nullptr ? stats_dev : base + kStaticPartialDoubles + 8;
+  unsigned long long* tags = (unsigned long long*)(base + kStaticPartialDoubles);
+  unsigned* flags = (unsigned*)(base + kStaticPartialDoubles + kStaticTagDoubles);
+  unsigned* status = flags + MMP_STATIC_MAX_CTAS;
+  double* stats = stats_dev != nullptr ? stats_dev : base + kStaticPartialDoubles + kStaticCtlDoubles;
   cudaStream_t s = (cudaStream_t)stream;
   // every call shares the array: clear what must start at zero
-  MMP_CUDA(cudaMemsetAsync(ctl, 0, 8 * sizeof(double), s));
+  MMP_CUDA(cudaMemsetAsync(tags, 0, kStaticCtlDoubles * sizeof(double), s));
   FineArgs a;
   const mmp_problem_desc& d = p.d;
   a.nc3 = -d.c3; a.c1 = d.c1; a.kappa = d.kappa; a.c0 = d.c0;
@@ -1219,11 +1241,11 @@ extern "C" int mmp_fine_static(const mmp_problem_desc* desc, int n, const void* 
   a.stats = stats; a.stats_fixed = 1;
   a.G = p.G;
   a.nq = p.nq;
-  a.partials = base; a.counters = ctl; a.status = ctl + 1;
+  a.partials = base; a.flags = flags; a.tags = tags; a.status = status;
   a.wait_limit_ns = wait_limit_ns();
   MMP_CUDA(launch_fine(d.precision, p.layout, p.nq, p.mult, p.G, a, s));
   if (stats_dev != nullptr) {
-    k_status_to_stats<<<1, 1, 0, s>>>(ctl + 1, stats_dev);
+    k_status_to_stats<<<1, 1, 0, s>>>(status, stats_dev);
     MMP_CUDA(cudaGetLastError());
   }
   return MMP_OK;

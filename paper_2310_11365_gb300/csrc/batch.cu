@@ -16,10 +16,17 @@
 
 namespace mmp {
 
+// Four CTAs per SM (64 registers a thread): a batch holds many small tasks
+// whose CTAs are far from filling shared memory.
+constexpr int kBatchOcc = 4;
+
 template <typename R, bool MULT>
-__global__ void __launch_bounds__(kTPB, (FineOccupancy<R, 0>::value)) k_fine_batch(const BatchArgs b) {
+__global__ void __launch_bounds__(kTPB, kBatchOcc) k_fine_batch(const BatchArgs b) {
   __shared__ GroupShared sh;
-  __shared__ FineArgs sa;  // the current task's arguments
+  // the current task's arguments (raw storage: FineArgs has member
+  // initialisers, which a __shared__ variable cannot run)
+  __shared__ __align__(16) unsigned char sa_raw[sizeof(FineArgs)];
+  FineArgs& sa = *reinterpret_cast<FineArgs*>(sa_raw);
   __shared__ int s_task, s_rank;
   const int tid = threadIdx.x;
   if (tid == 0) sh.abort = 0;
@@ -57,15 +64,16 @@ __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, 0>::value)) k_fine_bat
     }
     __syncthreads();
     Group grp;
-    grp.part = b.partials + (size_t)tk.seat0 * 2 * (kNV + 1);
-    grp.counter = b.counters + t;
+    grp.part = b.partials + (size_t)tk.seat0 * kSeatDoubles;
+    grp.flags = b.flags + tk.seat0;
+    grp.tags = b.tags + (size_t)tk.seat0 * kSlots;
     grp.status = sa.status;
     grp.limit_ns = sa.wait_limit_ns;
     grp.G = tk.G;
     grp.g = s_rank;
     grp.epoch = 0;
-    if (!fine_task<R, 0, MULT>(sa, tk.slice, s_rank, grp, sh, xs)) return;
-    __syncthreads();
+    if (!fine_task<R, 0, MULT, 2>(sa, tk.slice, s_rank, grp, sh, xs)) return;
+    __syncthreads();  // every thread is done with sa and s_task
   }
 }
 

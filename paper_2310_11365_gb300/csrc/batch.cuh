@@ -11,8 +11,9 @@ namespace mmp {
 
 // One (problem, slice) task of a batched sweep.  Tasks are listed in the
 // order seats are handed out; task t owns seats [seat0, seat0 + G) of the
-// sweep, its group counter is counters[t] and its reduction scratch starts
-// at partials + 2 (kNV + 1) seat0 doubles.
+// sweep, and its group's flags, tagged words and publication slots are
+// those of its seats (flags + seat0, tags + kSlots seat0, partials +
+// kSeatDoubles seat0).
 struct BatchTask {
   int prob;     // index into the problem records
   int slice;    // slice n
@@ -28,8 +29,9 @@ struct BatchArgs {
   const BatchTask* tasks;  // [n_tasks] by ascending seat0
   const int* header;       // [0] n_tasks, [1] total seats
   unsigned* seat_counter;  // zeroed per sweep
-  unsigned* counters;      // [n_tasks] group arrivals, zeroed per sweep
-  double* partials;        // [total seats] x 2 (kNV + 1) doubles
+  unsigned* flags;         // [total seats] epoch flags, zeroed per sweep
+  unsigned long long* tags;  // [total seats] x kSlots tagged step words, zeroed per sweep
+  double* partials;        // [total seats] x kSeatDoubles doubles
 };
 
 const void* fine_batch_kernel(int precision, bool mult);

@@ -30,12 +30,13 @@ struct FineArgs {
   int stats_fixed;
   int G;                       // CTAs per slice
   int nq;                      // quads per thread (shared-memory layout)
-  double* partials;            // [slot] x ([2][G][kNV] doubles + [2][G] float2) reduction scratch
-  unsigned* counters;          // [slot] group-barrier arrival counters (zeroed per launch)
+  double* partials;            // [slot][G][kSlots][kNV] doubles: group publication slots
+  unsigned* flags;             // [slot][G] epoch flags (zeroed per launch)
+  unsigned long long* tags;    // [slot][kSlots][G] tagged step words (zeroed per launch)
   unsigned* status;            // device status word
   unsigned long long wait_limit_ns;
   // optional recording for the adjoint (serial runs only, one task):
-  void* rec_uni = nullptr;     // [global step][3] (m_j, kappa m_j + c0, (BE m_j + B0) sqrt h), precision R
+  void* rec_uni = nullptr;     // [global step][3] (m_j, h (kappa m_j + c0), B0 sqrt h), precision R
   void* rec_ckpt = nullptr;    // particle rows at global steps 0, c, 2c, ... (row gstep / c)
   int ckpt_every = 1;          // c
   long long step_offset = 0;   // global index of this slice's first step

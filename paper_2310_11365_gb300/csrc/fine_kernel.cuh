@@ -12,8 +12,8 @@
 //   steps     x += h a(x, m_j) + b(x, m_j) sqrt(h) xi   (Eq. Euler_Maruyama)
 //             with xi from Philox(p/4, j, n, problem) and the mean
 //             m_{j+1} reduced over the whole group (warp shuffles, a shared
-//             memory stage, then a cross-CTA stage through L2 guarded by a
-//             bounded spin on an arrival counter)
+//             memory stage, then a cross-CTA stage through L2: per-CTA
+//             publication slots and epoch flags, read after a bounded spin)
 //   epilogue  store x, restriction per region (Eq. multimodal_R): counts,
 //             means, then centred sums, extremes (two passes, FP64)
 //
@@ -58,107 +58,138 @@ struct Quad<double> {
 
 // Per-CTA shared state of the group reductions.
 struct GroupShared {
-  double red[kWarps][kNV];  // per-warp partials
-  float2 redf[kWarps];      // per-warp double-float partials of the per-step sum
-  double tot[kNV];          // group totals, broadcast
-  double uni[4];            // per-step uniforms derived from the mean
-  float unif[4];            // the same, rounded once for float particles
-  float cf[12];             // float copies of the task's coefficients (see fine_task)
+  double red[kWarps][kNV];    // per-warp partials of the restriction reductions
+  float2 redf[2][kWarps];     // per-warp double-float partials of the per-step sum (by step parity)
+  double redd[2][kWarps];     // the same for double particles
+  float2 gsumf[2];            // group sum of a step, handed from warp 0 to the CTA (by parity)
+  double gsumd[2];
+  double tot[kNV];            // group totals, broadcast
+  float cf[16];               // float copies of the task's coefficients (see fine_task)
   int abort;
 };
 
-template <typename R>
-__device__ __forceinline__ R uniform_of(const GroupShared& sh, int k);
-template <>
-__device__ __forceinline__ float uniform_of<float>(const GroupShared& sh, int k) { return sh.unif[k]; }
-template <>
-__device__ __forceinline__ double uniform_of<double>(const GroupShared& sh, int k) { return sh.uni[k]; }
-
 // Group-reduction context of one CTA.
+//
+// Epochs number the group reductions of a CTA in program order; every CTA
+// of a group runs the same sequence.  Two publication channels, each a ring
+// of kSlots entries per CTA indexed by epoch:
+//
+// * records of up to kNV doubles: publishing epoch e writes slot e mod
+//   kSlots, then stores e + 1 to the CTA's flag with release semantics; a
+//   reader acquires the flag (>= e + 1) before it reads the slot;
+// * per-step sums of float particles: one 8-byte word (hi, lo) whose low 16
+//   bits of lo are replaced by a tag of the epoch, written and read with
+//   single-copy-atomic relaxed accesses, so the word is its own flag (one
+//   L2 round trip per read, no fence on the writer).  Dropping those bits
+//   of lo leaves the pair accurate to about 2^-32 relative.
+//
+// A CTA publishes epoch e only after it has seen epoch e - 2 complete, and
+// every CTA reads an epoch before it publishes the epoch after next, so no
+// entry is rewritten before every CTA has read it (kSlots = 4 leaves one
+// spare).
 struct Group {
-  double* part;         // [2][G][kNV] doubles, then [2][G] float2, for this slot
-  unsigned* counter;    // arrivals of this slot
+  double* part;             // [G][kSlots][kNV] record slots of this group
+  unsigned* flags;          // [G] 1 + last record epoch published (zeroed per launch)
+  unsigned long long* tags; // [kSlots][G] tagged step words (zeroed per launch)
   unsigned* status;
   unsigned long long limit_ns;
   int G, g;
-  unsigned epoch;
+  unsigned epoch;           // epochs published so far by this CTA
 };
 
-// Warp 0 finishes a group reduction of nv values whose per-warp partials
-// sit in sh.red.  min_mask / max_mask select values combined by min / max
-// (all others are summed).  Returns false if the cross-CTA wait gave up.
-__device__ __forceinline__ bool group_wait(Group& grp);
+__device__ __forceinline__ double* group_slot(const Group& grp, int c, unsigned e) {
+  return grp.part + ((size_t)c * kSlots + (e & (unsigned)(kSlots - 1))) * kNV;
+}
 
+// One thread: publish nv values as epoch e of this CTA.
+__device__ __forceinline__ void group_publish(const Group& grp, unsigned e, const double* v, int nv) {
+  double* s = group_slot(grp, grp.g, e);
+  for (int k = 0; k < nv; ++k) __stcg(s + k, v[k]);
+  st_release_gpu(grp.flags + grp.g, e + 1u);
+}
+
+// Whole warp: bounded wait until every CTA of the group has published
+// epoch e.  Lane l acquires the flags of CTAs l, l + 32, ... and is the lane
+// that reads those CTAs' slots afterwards.  On timeout the status word gets
+// the timeout bit (which also releases every other waiter) and the result
+// is false.
+__device__ __forceinline__ bool group_wait(const Group& grp, unsigned e) {
+  bool ok = true;
+  for (int c = threadIdx.x & 31; c < grp.G && ok; c += 32) {
+    unsigned long long t0 = 0;
+    int spins = 0;
+    while (ld_acquire_gpu(grp.flags + c) <= e) {
+      if (++spins >= 32) {
+        spins = 0;
+        const unsigned long long now = globaltimer_ns();
+        if (t0 == 0) {
+          t0 = now;
+        } else if (now - t0 > grp.limit_ns) {
+          atomicOr(grp.status, kStatusTimeout);
+          ok = false;
+          break;
+        }
+        if (*(volatile unsigned*)grp.status & kStatusTimeout) {
+          ok = false;
+          break;
+        }
+      }
+    }
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
+// Warp 0 finishes a group reduction of NV values whose per-warp partials
+// sit in sh.red: the CTA's values (warps in index order) are published as
+// epoch e and the group's totals (CTAs in index order) land in sh.tot.
+// min_mask / max_mask select values combined by min / max (all others are
+// summed).  Every thread of the CTA advances grp.epoch past e itself.
+// Returns false if the wait gave up.
 template <int NV>
-__device__ __forceinline__ bool group_finish(GroupShared& sh, Group& grp, unsigned min_mask,
+__device__ __forceinline__ bool group_finish(GroupShared& sh, const Group& grp, unsigned e, unsigned min_mask,
                                              unsigned max_mask) {
-  constexpr int nv = NV;
   const int lane = threadIdx.x & 31;
+  auto comb = [&](int k, double x, double o) {
+    return (min_mask >> k & 1) ? fmin(x, o) : ((max_mask >> k & 1) ? fmax(x, o) : x + o);
+  };
+  auto ident = [&](int k) {
+    return (min_mask >> k & 1) ? (double)INFINITY : ((max_mask >> k & 1) ? -(double)INFINITY : 0.0);
+  };
   double v[NV];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    const double ident = (min_mask >> k & 1) ? INFINITY : ((max_mask >> k & 1) ? -INFINITY : 0.0);
-    v[k] = (k < nv && lane < kWarps) ? sh.red[lane][k] : ident;
-  }
-  // butterfly over the kWarps lanes that hold values
+  for (int k = 0; k < NV; ++k) v[k] = lane < kWarps ? sh.red[lane][k] : ident(k);
 #pragma unroll
   for (int off = kWarps / 2; off > 0; off >>= 1) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      if (k < nv) {
-        const double o = __shfl_xor_sync(0xffffffffu, v[k], off);
-        v[k] = (min_mask >> k & 1) ? fmin(v[k], o) : ((max_mask >> k & 1) ? fmax(v[k], o) : v[k] + o);
-      }
-    }
+    for (int k = 0; k < NV; ++k) v[k] = comb(k, v[k], __shfl_xor_sync(0xffffffffu, v[k], off));
   }
   if (grp.G > 1) {
-    const unsigned parity = grp.epoch & 1u;
-    grp.epoch += 1;
-    double* mine = grp.part + ((size_t)parity * grp.G + grp.g) * kNV;
-    if (lane == 0) {
+    if (lane == 0) group_publish(grp, e, v, NV);
+    if (!group_wait(grp, e)) return false;
 #pragma unroll
-      for (int k = 0; k < NV; ++k)
-        if (k < nv) mine[k] = v[k];
-      red_release_gpu_add(grp.counter, 1u);
-    }
-    if (!group_wait(grp)) return false;
-    const double* all = grp.part + (size_t)parity * grp.G * kNV;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      const double ident = (min_mask >> k & 1) ? INFINITY : ((max_mask >> k & 1) ? -INFINITY : 0.0);
-      v[k] = ident;
-    }
+    for (int k = 0; k < NV; ++k) v[k] = ident(k);
     for (int c = lane; c < grp.G; c += 32) {
+      const double* s = group_slot(grp, c, e);
 #pragma unroll
-      for (int k = 0; k < NV; ++k) {
-        if (k < nv) {
-          const double o = __ldcg(all + (size_t)c * kNV + k);
-          v[k] = (min_mask >> k & 1) ? fmin(v[k], o) : ((max_mask >> k & 1) ? fmax(v[k], o) : v[k] + o);
-        }
-      }
+      for (int k = 0; k < NV; ++k) v[k] = comb(k, v[k], __ldcg(s + k));
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) {
-        if (k < nv) {
-          const double o = __shfl_xor_sync(0xffffffffu, v[k], off);
-          v[k] = (min_mask >> k & 1) ? fmin(v[k], o) : ((max_mask >> k & 1) ? fmax(v[k], o) : v[k] + o);
-        }
-      }
+      for (int k = 0; k < NV; ++k) v[k] = comb(k, v[k], __shfl_xor_sync(0xffffffffu, v[k], off));
     }
   }
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
-      if (k < nv) sh.tot[k] = v[k];
+    for (int k = 0; k < NV; ++k) sh.tot[k] = v[k];
   }
   return true;
 }
 
 // Double-float addition (hi, lo) + (b_hi, b_lo) with error-free two-sums;
 // exact to about 2^-48 relative and free of FP64 instructions, which on
-// this chip issue at a small fraction of the FP32 rate.
+// this chip issue at a small fraction of the FP32 rate.  Commutative bit for
+// bit, so every lane of a butterfly ends with the same pair.
 __device__ __forceinline__ float2 dd_add(float2 a, float2 b) {
   float s, e;
   two_sum(a.x, b.x, s, e);
@@ -205,113 +236,154 @@ struct Centre<double> {
   __device__ __forceinline__ double diff(double x) const { return x - m; }
 };
 
-// Per-warp stage of the per-step sum: float input is carried as a
-// double-float pair, double input as a double.
-__device__ __forceinline__ void warp_sum_to_shared(GroupShared& sh, float s) {
-  float2 v = make_float2(s, 0.0f);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v = dd_add(v, shfl_xor_dd(v, off));
-  if ((threadIdx.x & 31) == 0) sh.redf[threadIdx.x >> 5] = v;
-}
-__device__ __forceinline__ void warp_sum_to_shared(GroupShared& sh, double s) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5][0] = s;
+// Plain arithmetic in the particle precision with explicit rounding (no
+// contraction choices left to the compiler, so every kernel that inlines
+// these rounds identically).
+__device__ __forceinline__ float addR(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double addR(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mulR(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mulR(double a, double b) { return __dmul_rn(a, b); }
+
+// The part of one Euler-Maruyama step that does not depend on the mean:
+//   y = x + h (nc3 x^3 + c1 x) + amp xi = fma(amp, xi, fma(fma(hn3, x^2, hc1), x, x)),
+// with hn3 = h nc3 and hc1 = h c1.  The step is x_{j+1} = y + h (kappa m_j + c0),
+// a shift common to all particles (the fine kernel and the adjoint's replay
+// both evaluate it through this function).
+template <typename R>
+__device__ __forceinline__ R em_partial(R x, R xi, R hn3, R hc1, R amp) {
+  return fmaR(amp, xi, fmaR(fmaR(hn3, mulR(x, x), hc1), x, x));
 }
 
-// Bounded wait of warp 0 for all G arrivals of the current epoch.
-__device__ __forceinline__ bool group_wait(Group& grp) {
-  const unsigned target = grp.epoch * (unsigned)grp.G;
-  bool ok = true;
-  unsigned long long t0 = 0;
-  int spins = 0;
-  while (ld_acquire_gpu(grp.counter) < target) {
-    if (++spins >= 32) {
-      spins = 0;
-      const unsigned long long now = globaltimer_ns();
-      if (t0 == 0) {
-        t0 = now;
-      } else if (now - t0 > grp.limit_ns) {
-        ok = false;
+// The per-step sum of the particles: a double-float pair for float
+// particles (no FP64 instruction in the step loop), a double otherwise.
+// Stages: per-thread sum in the particle precision, warp butterfly, warps
+// in index order, CTAs of the group in index order.
+template <typename R>
+struct StepSum;
+template <>
+struct StepSum<float> {
+  using T = float2;
+  static __device__ __forceinline__ T zero() { return make_float2(0.0f, 0.0f); }
+  static __device__ __forceinline__ T of(float s) { return make_float2(s, 0.0f); }
+  static __device__ __forceinline__ T add(T a, T b) { return dd_add(a, b); }
+  static __device__ __forceinline__ T shfl_xor(T v, int off) { return shfl_xor_dd(v, off); }
+  static __device__ __forceinline__ T bcast0(T v) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, 0), __shfl_sync(0xffffffffu, v.y, 0));
+  }
+  static __device__ __forceinline__ T* warp_slots(GroupShared& sh, int parity) { return sh.redf[parity]; }
+  static __device__ __forceinline__ T& gsum(GroupShared& sh, int parity) { return sh.gsumf[parity]; }
+  static __device__ __forceinline__ uint32_t tag_of(unsigned e) { return 0x8000u | ((e + 1u) & 0x7FFFu); }
+  // one thread: the CTA's value of epoch e as a tagged word
+  static __device__ __forceinline__ void publish(const Group& grp, unsigned e, T v) {
+    const uint32_t lo = (__float_as_uint(v.y) & 0xFFFF0000u) | tag_of(e);
+    const unsigned long long w = ((unsigned long long)lo << 32) | __float_as_uint(v.x);
+    st_relaxed_gpu_b64(grp.tags + (size_t)(e & (unsigned)(kSlots - 1)) * grp.G + grp.g, w);
+  }
+  // whole warp: bounded wait for the tagged words of epoch e of every CTA
+  // (lane l reads CTAs l, l + 32, ...), their sum in CTA order
+  static __device__ __forceinline__ bool fetch(const Group& grp, unsigned e, T& sum) {
+    const uint32_t tag = tag_of(e);
+    const unsigned long long* row = grp.tags + (size_t)(e & (unsigned)(kSlots - 1)) * grp.G;
+    T v = zero();
+    bool ok = true;
+    for (int c = threadIdx.x & 31; c < grp.G; c += 32) {
+      unsigned long long w = ld_relaxed_gpu_b64(row + c);
+      unsigned long long t0 = 0;
+      int spins = 0;
+      while (ok && ((uint32_t)(w >> 32) & 0xFFFFu) != tag) {
+        if (++spins >= 32) {
+          spins = 0;
+          const unsigned long long now = globaltimer_ns();
+          if (t0 == 0) {
+            t0 = now;
+          } else if (now - t0 > grp.limit_ns) {
+            atomicOr(grp.status, kStatusTimeout);
+            ok = false;
+          }
+          if (*(volatile unsigned*)grp.status & kStatusTimeout) ok = false;
+        }
+        if (ok) w = ld_relaxed_gpu_b64(row + c);
       }
-      if (*(volatile unsigned*)grp.status & kStatusTimeout) ok = false;
       if (!ok) break;
+      v = add(v, make_float2(__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)(w >> 32) & 0xFFFF0000u)));
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = add(v, shfl_xor(v, off));
+    sum = v;
+    return __all_sync(0xffffffffu, ok);
   }
-  ok = __all_sync(0xffffffffu, ok);
-  if (!ok && (threadIdx.x & 31) == 0) atomicOr(grp.status, kStatusTimeout);
-  return ok;
+  // sum / P with inv_p = 1 / P rounded to float
+  static __device__ __forceinline__ float mean(T v, float inv_p, long long) {
+    return __fmaf_rn(v.x, inv_p, __fmul_rn(v.y, inv_p));
+  }
+};
+template <>
+struct StepSum<double> {
+  using T = double;
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ T of(double s) { return s; }
+  static __device__ __forceinline__ T add(T a, T b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ T shfl_xor(T v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+  static __device__ __forceinline__ T bcast0(T v) { return __shfl_sync(0xffffffffu, v, 0); }
+  static __device__ __forceinline__ T* warp_slots(GroupShared& sh, int parity) { return sh.redd[parity]; }
+  static __device__ __forceinline__ T& gsum(GroupShared& sh, int parity) { return sh.gsumd[parity]; }
+  // one thread: the CTA's value of epoch e in its record slot, then its flag
+  static __device__ __forceinline__ void publish(const Group& grp, unsigned e, T v) {
+    __stcg(group_slot(grp, grp.g, e), v);
+    st_release_gpu(grp.flags + grp.g, e + 1u);
+  }
+  // whole warp: bounded wait for epoch e of every CTA, the sum in CTA order
+  static __device__ __forceinline__ bool fetch(const Group& grp, unsigned e, T& sum) {
+    if (!group_wait(grp, e)) return false;
+    T v = zero();
+    for (int c = threadIdx.x & 31; c < grp.G; c += 32) v = add(v, __ldcg(group_slot(grp, c, e)));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = add(v, shfl_xor(v, off));
+    sum = v;
+    return true;
+  }
+  static __device__ __forceinline__ double mean(T v, float, long long P) { return __ddiv_rn(v, (double)P); }
+};
+
+// Per-warp stage: butterfly of the per-thread sums, lane 0 stores the warp's
+// partial into the slot array of the step's parity.
+template <typename R>
+__device__ __forceinline__ void step_sum_warp(GroupShared& sh, int parity, R s) {
+  using S = StepSum<R>;
+  typename S::T v = S::of(s);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = S::add(v, S::shfl_xor(v, off));
+  if ((threadIdx.x & 31) == 0) S::warp_slots(sh, parity)[threadIdx.x >> 5] = v;
 }
 
-// Warp 0 finishes the per-step sum of float particles entirely in FP32
-// double-float arithmetic (warps in index order, then CTAs in index order)
-// and publishes the per-step uniforms as floats.  Returns false on timeout.
-__device__ __forceinline__ bool step_sum_finish_f(GroupShared& sh, Group& grp, float inv_p, float kappa,
-                                                  float c0, float be, float b0, float sqrt_h) {
+// Every warp, after the CTA barrier that follows step_sum_warp: the CTA's
+// sum (warps in index order; the same value in every warp and lane).
+template <typename R>
+__device__ __forceinline__ typename StepSum<R>::T step_sum_cta(GroupShared& sh, int parity) {
+  using S = StepSum<R>;
   const int lane = threadIdx.x & 31;
-  float2 v = lane < kWarps ? sh.redf[lane] : make_float2(0.0f, 0.0f);
+  typename S::T v = lane < kWarps ? S::warp_slots(sh, parity)[lane] : S::zero();
 #pragma unroll
-  for (int off = kWarps / 2; off > 0; off >>= 1) v = dd_add(v, shfl_xor_dd(v, off));
-  if (grp.G > 1) {
-    const unsigned parity = grp.epoch & 1u;
-    grp.epoch += 1;
-    // dense per-step partials after the [2][G][kNV] double area
-    float2* part = reinterpret_cast<float2*>(grp.part + (size_t)2 * grp.G * kNV) + (size_t)parity * grp.G;
-    if (lane == 0) {
-      part[grp.g] = v;
-      red_release_gpu_add(grp.counter, 1u);
-    }
-    if (!group_wait(grp)) return false;
-    v = make_float2(0.0f, 0.0f);
-    for (int c = lane; c < grp.G; c += 32) {
-      const float2 o = __ldcg(part + c);
-      v = dd_add(v, o);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = dd_add(v, shfl_xor_dd(v, off));
-  }
-  if (lane == 0) {
-    const float m = __fmaf_rn(v.x, inv_p, v.y * inv_p);
-    sh.unif[0] = m;
-    sh.unif[1] = __fmaf_rn(kappa, m, c0);
-    sh.unif[2] = __fmaf_rn(be, m, b0) * sqrt_h;
-  }
-  return true;
+  for (int off = kWarps / 2; off > 0; off >>= 1) v = S::add(v, S::shfl_xor(v, off));
+  return S::bcast0(v);
 }
 
 // General per-warp stage of nv double values.
 template <int NV>
 __device__ __forceinline__ void warp_reduce_to_shared(GroupShared& sh, double v[NV], unsigned min_mask,
                                                       unsigned max_mask) {
-  constexpr int nv = NV;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      if (k < nv) {
-        const double o = __shfl_xor_sync(0xffffffffu, v[k], off);
-        v[k] = (min_mask >> k & 1) ? fmin(v[k], o) : ((max_mask >> k & 1) ? fmax(v[k], o) : v[k] + o);
-      }
+      const double o = __shfl_xor_sync(0xffffffffu, v[k], off);
+      v[k] = (min_mask >> k & 1) ? fmin(v[k], o) : ((max_mask >> k & 1) ? fmax(v[k], o) : v[k] + o);
     }
   }
   if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
-      if (k < nv) sh.red[threadIdx.x >> 5][k] = v[k];
+    for (int k = 0; k < NV; ++k) sh.red[threadIdx.x >> 5][k] = v[k];
   }
-}
-
-// After a reduction of the running sum: publish the per-step uniforms
-// (mean, kappa m + c0, diffusion offset) so that no thread does FP64 work
-// in the step loop.
-__device__ __forceinline__ void publish_uniforms(GroupShared& sh, const FineArgs& a) {
-  const double m = sh.tot[0] / (double)a.P;
-  sh.uni[0] = m;
-  sh.uni[1] = __fma_rn(a.kappa, m, a.c0);
-  sh.uni[2] = __dmul_rn(__fma_rn(a.BE, m, a.B0), a.sqrt_h);
-  sh.unif[0] = (float)sh.uni[0];
-  sh.unif[1] = (float)sh.uni[1];
-  sh.unif[2] = (float)sh.uni[2];
 }
 
 // Where a thread keeps its quads of particles between steps.
@@ -344,21 +416,49 @@ struct QuadStore<R, 0> {
 
 // Resident CTAs per SM the register budget is sized for.  Register layout:
 // the quads a thread holds dominate its registers, so fewer CTAs fit as NQ
-// grows.  Shared-memory layout (NQ == 0): registers hold one quad in flight.
+// grows.  Shared-memory layout (NQ == 0): a slice's particles fill the
+// shared memory of two CTAs per SM at the sizes that matter, so each thread
+// gets 128 registers and keeps kStepUnrollSmem quads (independent Philox
+// chains) in flight.
+constexpr int kStepUnrollSmem = 4;
 template <typename R, int NQ>
 struct FineOccupancy {
-  static constexpr int value = NQ == 0 ? (sizeof(R) == 4 ? 5 : 4)
+  static constexpr int value = NQ == 0 ? 2
                                        : (sizeof(R) == 4 ? (NQ <= 2 ? 5 : (NQ <= 4 ? 4 : 3)) : (NQ <= 2 ? 3 : 2));
 };
 
 // One slice ("task") n processed by rank g of its group of G CTAs:
-// prologue (load, match, first mean), the n_f Euler-Maruyama steps with
-// the group mean each step, and the restriction epilogue.  Returns false if
-// a group wait gave up; the CTA must then leave the kernel.
-template <typename R, int NQ, bool MULT>
+// prologue (load, match, sum), the n_f Euler-Maruyama steps with the group
+// mean each step, and the restriction epilogue.  Returns false if a group
+// wait gave up; the CTA must then leave the kernel.
+//
+// Two forms of the step loop:
+//
+// * mean-additive diffusion (MULT false: b = B0, and generally whenever the
+//   mean enters the step only through the drift term kappa m + c0): the
+//   step is x_{j+1} = y_j + d_j with y_j = em_partial(x_j) independent of
+//   the mean and d_j = h (kappa m_j + c0) common to all particles.  The
+//   stored state is y_j with the shift pending; since
+//   m_{j+1} = mean(y_j) + d_j, the sum over y_j published at the end of
+//   step j is first needed at the end of step j + 1.  Every CTA publishes
+//   its step sum and reads the group's sum of the previous step, which its
+//   peers published a whole step earlier: the cross-CTA exchange never
+//   stalls the step loop of a CTA that keeps pace with its group.
+//
+// * general (MULT true: b = B x + BE m + B0): the noise amplitude depends on
+//   the mean per particle, so step j + 1 waits for the group sum of step j.
+//
+// Either way one CTA barrier per step: every warp forms the CTA sum from
+// the per-warp partials and the group sum from the published slots itself,
+// in the same order, so all warps hold the same values.
+template <typename R, int NQ, bool MULT, int STEP_UNROLL>
 __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const int g, Group& grp,
                                           GroupShared& sh, QuadStore<R, NQ>& xs) {
-  constexpr int kUnroll = NQ > 0 ? NQ : 2;
+  using SS = StepSum<R>;
+  using ST = typename SS::T;
+  constexpr bool kLag = !MULT;
+  constexpr int kUnroll = NQ > 0 ? NQ : 2;             // prologue and epilogue
+  constexpr int kStepUnroll = NQ > 0 ? NQ : STEP_UNROLL;
   const int G = a.G;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -371,12 +471,14 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   const int qlast = a.Q - 1;
   const int plast = (int)(a.P - 4LL * qlast);  // valid lanes of the last quad, 1..4
   const int loop_n = NQ > 0 ? NQ : nq;        // quads this thread visits
+  const int nf = a.nf;
 
   // Coefficients in the particle precision.  For float particles they are
   // rounded once per task by one thread and read from shared memory: left
   // to the compiler, the double-to-float conversions get re-derived from the
   // double kernel arguments inside the step loop, and every such conversion
   // issues on the FP64 pipe, which runs at 2 lanes per clock per SM here.
+  __syncthreads();  // the previous task's readers of sh are done
   if (sizeof(R) == 4 && tid == 0) {
     sh.cf[0] = (float)a.h;
     sh.cf[1] = (float)a.nc3;
@@ -390,6 +492,8 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
     sh.cf[9] = (float)a.BE;
     sh.cf[10] = (float)a.B0;
     sh.cf[11] = (float)a.sqrt_h;
+    sh.cf[12] = (float)(a.h * a.nc3);
+    sh.cf[13] = (float)(a.h * a.c1);
   }
   __syncthreads();
   const bool fl = sizeof(R) == 4;
@@ -399,16 +503,21 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   const R bsq = fl ? (R)sh.cf[3] : (R)(a.B * a.sqrt_h);    // state-proportional part of b sqrt(h)
   const R b0sq = fl ? (R)sh.cf[4] : (R)(a.B0 * a.sqrt_h);  // additive noise amplitude
   const R thr = fl ? (R)sh.cf[5] : (R)a.thr;
+  const float inv_p = sh.cf[6];                             // float path only
+  const R kap = fl ? (R)sh.cf[7] : (R)a.kappa;
+  const R c0r = fl ? (R)sh.cf[8] : (R)a.c0;
+  const R ber = fl ? (R)sh.cf[9] : (R)a.BE;
+  const R b0r = fl ? (R)sh.cf[10] : (R)a.B0;
+  const R sqh = fl ? (R)sh.cf[11] : (R)a.sqrt_h;
+  const R hn3 = fl ? (R)sh.cf[12] : (R)(a.h * a.nc3);
+  const R hc1 = fl ? (R)sh.cf[13] : (R)(a.h * a.c1);
   const bool two = a.n_regions > 1;
-  // per-step uniforms of the float path are formed in FP32 by warp 0
-  const float inv_p = sh.cf[6];
-  const float kappa_f = sh.cf[7], c0_f = sh.cf[8], be_f = sh.cf[9], b0_f = sh.cf[10];
-  const float sqrt_h_f = sh.cf[11];
+  const unsigned E = grp.epoch;  // first epoch of this task
 
   {
   const R* src = (a.src == nullptr || n == 0) ? (const R*)a.src0
                                               : (const R*)a.src + (size_t)(n - 1) * a.pitch;
-  // ---------------- prologue: load, match, first mean ------------------
+  // ---------------- prologue: load, match, sum --------------------------
   int flips = 0;
   R s_in = (R)0;
   {
@@ -465,57 +574,51 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
           if (plast < 3) v[2] = (R)0;
           if (plast < 2) v[1] = (R)0;
         }
-        s_in += (v[0] + v[1]) + (v[2] + v[3]);
+        s_in = addR(s_in, addR(addR(v[0], v[1]), addR(v[2], v[3])));
       }
       xs.put(i, v);
     }
   }
-  {
-    double v[2];
-    v[0] = (double)s_in;
-    v[1] = (double)flips;
-    warp_reduce_to_shared<2>(sh, v, 0u, 0u);
-    __syncthreads();
+  // The sum of the inputs is epoch E.  The shift form reads it at the end
+  // of step 0 (or right here when there are no steps); the general form
+  // needs m_0 before step 0.  Warp 0 does all cross-CTA work: it publishes
+  // the CTA's sums and, before each CTA barrier, fetches the group sum the
+  // other warps need after it (through sh.gsum).
+  step_sum_warp<R>(sh, 1, s_in);
+  __syncthreads();
+  ST own = SS::zero();  // warp 0: this CTA's sum of the latest epoch it published
+  if (warp == 0) {
+    own = step_sum_cta<R>(sh, 1);
+    if (G > 1 && lane == 0) SS::publish(grp, E, own);
+  }
+  grp.epoch = E + 1u;
+  double m_in = 0.0;
+  R d = (R)0;                  // shift form: the pending shift d_{j-1}
+  R base = (R)0, boff = (R)0;  // general form: kappa m_j + c0, (BE m_j + B0) sqrt(h)
+  if (!kLag || nf == 0) {
     if (warp == 0) {
-      if (!group_finish<2>(sh, grp, 0u, 0u)) {
-        if (lane == 0) sh.abort = 1;
-      } else if (lane == 0) {
-        publish_uniforms(sh, a);
+      ST sum = own;
+      const bool ok = G == 1 || SS::fetch(grp, E, sum);
+      if (lane == 0) {
+        SS::gsum(sh, 1) = sum;
+        if (!ok) sh.abort = 1;
       }
     }
     __syncthreads();
     if (sh.abort) return false;
+    const R m = (R)SS::mean(SS::gsum(sh, 1), inv_p, a.P);
+    m_in = (double)m;
+    base = fmaR(kap, m, c0r);
+    boff = mulR(fmaR(ber, m, b0r), sqh);
   }
-  const double flips_tot = sh.tot[1];
-  const double m_in = sh.uni[0];
 
   // ---------------- Euler-Maruyama steps --------------------------------
-  for (int j = 0; j < a.nf; ++j) {
-    const R base = uniform_of<R>(sh, 1);  // kappa m_j + c0
-    const R boff = uniform_of<R>(sh, 2);  // (BE m_j + B0) sqrt(h)
-    if (a.rec_uni != nullptr) {
-      // the adjoint replays steps from exactly these values
-      const long long gs = a.step_offset + j;
-      if (g == 0 && tid == 0) {
-        R* u = (R*)a.rec_uni + 3 * gs;
-        u[0] = uniform_of<R>(sh, 0);
-        u[1] = base;
-        u[2] = MULT ? boff : b0sq;  // the noise amplitude this step used
-      }
-      if (gs % a.ckpt_every == 0) {
-        R* row = (R*)a.rec_ckpt + (size_t)(gs / a.ckpt_every) * a.pitch;
-#pragma unroll kUnroll
-        for (int i = 0; i < loop_n; ++i) {
-          if (i < nq) {
-            R v[4];
-            xs.get(i, v);
-            Quad<R>::store(row + 4 * (size_t)(qb + tid + i * kTPB), v);
-          }
-        }
-      }
-    }
+  for (int j = 0; j < nf; ++j) {
+    const long long gs = a.step_offset + j;
+    const bool ckpt = kLag && a.rec_ckpt != nullptr && gs % a.ckpt_every == 0;
+    R* ck_row = ckpt ? (R*)a.rec_ckpt + (size_t)(gs / a.ckpt_every) * a.pitch : nullptr;
     R s = (R)0;
-#pragma unroll kUnroll
+#pragma unroll kStepUnroll
     for (int i = 0; i < loop_n; ++i) {
       if (i < nq) {
         const uint32_t q = (uint32_t)(qb + tid + i * kTPB);
@@ -523,50 +626,101 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
         xs.get(i, v);
         R z[4];
         normals4<R>(philox4x32_10(rng_counter(q, (uint32_t)j, (uint32_t)n, 0u, a.ptag), a.key0, a.key1), z);
+        if constexpr (kLag) {
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const R xv = v[w];
-          const R drift = fmaR(fmaR(nc3, xv * xv, c1), xv, base);
-          const R amp = MULT ? fmaR(bsq, xv, boff) : b0sq;
-          v[w] = fmaR(amp, z[w], fmaR(h, drift, xv));
+          for (int w = 0; w < 4; ++w) v[w] = addR(v[w], d);  // x_j = y_{j-1} + d_{j-1}
+          if (ckpt) Quad<R>::store(ck_row + 4 * (size_t)q, v);
+#pragma unroll
+          for (int w = 0; w < 4; ++w) v[w] = em_partial(v[w], z[w], hn3, hc1, b0sq);
+        } else {
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const R xv = v[w];
+            const R drift = fmaR(fmaR(nc3, mulR(xv, xv), c1), xv, base);
+            const R amp = fmaR(bsq, xv, boff);
+            v[w] = fmaR(amp, z[w], fmaR(h, drift, xv));
+          }
         }
         if (q == (uint32_t)qlast) {
           if (plast < 4) v[3] = (R)0;
           if (plast < 3) v[2] = (R)0;
           if (plast < 2) v[1] = (R)0;
         }
-        s += (v[0] + v[1]) + (v[2] + v[3]);
+        s = addR(s, addR(addR(v[0], v[1]), addR(v[2], v[3])));
         xs.put(i, v);
       }
     }
-    warp_sum_to_shared(sh, s);
-    __syncthreads();
-    if (warp == 0) {
-      bool ok;
-      if constexpr (sizeof(R) == 4) {
-        ok = step_sum_finish_f(sh, grp, inv_p, kappa_f, c0_f, be_f, b0_f, sqrt_h_f);
-      } else {
-        ok = group_finish<1>(sh, grp, 0u, 0u);
-        if (ok && lane == 0) publish_uniforms(sh, a);
+    step_sum_warp<R>(sh, j & 1, s);
+    if constexpr (kLag) {
+      // Warp 0 fetches the group sum of the previous epoch (published by
+      // the peers a whole step ago) before the barrier:
+      //   m_j = mean(y_{j-1}) + d_{j-1},  d_j = h (kappa m_j + c0).
+      if (warp == 0) {
+        ST sum = own;
+        const bool ok = G == 1 || SS::fetch(grp, E + (unsigned)j, sum);
+        if (lane == 0) {
+          SS::gsum(sh, j & 1) = sum;
+          if (!ok) sh.abort = 1;
+        }
       }
-      if (!ok && lane == 0) sh.abort = 1;
+      __syncthreads();
+      if (sh.abort) return false;
+      const R m = addR((R)SS::mean(SS::gsum(sh, j & 1), inv_p, a.P), d);
+      if (j == 0) m_in = (double)m;
+      d = mulR(h, fmaR(kap, m, c0r));
+      if (a.rec_uni != nullptr && g == 0 && tid == 0) {
+        // the adjoint replays step j from exactly these values
+        R* u = (R*)a.rec_uni + 3 * gs;
+        u[0] = m;
+        u[1] = d;
+        u[2] = b0sq;
+      }
+      // this step's sum becomes epoch E + 1 + j (unless nothing reads it)
+      if (warp == 0) {
+        own = step_sum_cta<R>(sh, j & 1);
+        if (G > 1 && j + 1 < nf && lane == 0) SS::publish(grp, E + 1u + (unsigned)j, own);
+      }
+      if (j + 1 < nf) grp.epoch = E + 2u + (unsigned)j;
+    } else {
+      __syncthreads();
+      const unsigned e = E + 1u + (unsigned)j;
+      if (warp == 0) {
+        ST sum = step_sum_cta<R>(sh, j & 1);
+        if (G > 1 && lane == 0) SS::publish(grp, e, sum);
+        const bool ok = G == 1 || SS::fetch(grp, e, sum);
+        if (lane == 0) {
+          SS::gsum(sh, j & 1) = sum;
+          if (!ok) sh.abort = 1;
+        }
+      }
+      grp.epoch = e + 1u;
+      __syncthreads();
+      if (sh.abort) return false;
+      const R m = (R)SS::mean(SS::gsum(sh, j & 1), inv_p, a.P);
+      base = fmaR(kap, m, c0r);
+      boff = mulR(fmaR(ber, m, b0r), sqh);
     }
-    __syncthreads();
-    if (sh.abort) return false;
   }
+  __syncthreads();
 
   // ---------------- epilogue: store and restrict -----------------------
-  // pass 1 (with the store): counts and sums per region
+  // pass 1 (with the store): apply the pending shift, counts and sums per region
   {
     R* dst = a.dst != nullptr ? (R*)a.dst + (size_t)(a.dst_fixed ? 0 : n) * a.pitch : nullptr;
     int n0 = 0, n1 = 0;
     Acc<R> s0, s1;
+    const bool shift = kLag && nf > 0;
 #pragma unroll kUnroll
     for (int i = 0; i < loop_n; ++i) {
       if (i < nq) {
         const int q = qb + tid + i * kTPB;
         R x4[4];
         xs.get(i, x4);
+        if (shift) {
+#pragma unroll
+          for (int w = 0; w < 4; ++w) x4[w] = addR(x4[w], d);
+          xs.put(i, x4);
+        }
         if (dst != nullptr) {
           if (q != qlast || plast == 4) {
             Quad<R>::store(dst + 4 * (size_t)q, x4);
@@ -591,10 +745,11 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
         }
       }
     }
-    double v[4] = {(double)n0, s0.get(), (double)n1, s1.get()};
-    warp_reduce_to_shared<4>(sh, v, 0u, 0u);
+    double v[5] = {(double)n0, s0.get(), (double)n1, s1.get(), (double)flips};
+    warp_reduce_to_shared<5>(sh, v, 0u, 0u);
     __syncthreads();
-    if (warp == 0 && !group_finish<4>(sh, grp, 0u, 0u) && lane == 0) sh.abort = 1;
+    const unsigned e = grp.epoch++;
+    if (warp == 0 && !group_finish<5>(sh, grp, e, 0u, 0u) && lane == 0) sh.abort = 1;
     __syncthreads();
     if (sh.abort) return false;
   }
@@ -602,6 +757,7 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   const double mean0 = cnt0 > 0 ? sh.tot[1] / cnt0 : 0.0;
   const double mean1 = cnt1 > 0 ? sh.tot[3] / cnt1 : 0.0;
   const double gmean = (sh.tot[1] + sh.tot[3]) / (double)a.P;
+  const double flips_tot = sh.tot[4];
   __syncthreads();
   // pass 2: centred sums and extremes
   {
@@ -622,13 +778,13 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
             const R dg = cg.diff(xv);
             ssg.add(dg * dg);
             if (two && !(xv < thr)) {
-              const R d = c1c.diff(xv);
-              ss1.add(d * d);
+              const R dd = c1c.diff(xv);
+              ss1.add(dd * dd);
               lo1 = lo1 < xv ? lo1 : xv;
               hi1 = hi1 > xv ? hi1 : xv;
             } else {
-              const R d = c0c.diff(xv);
-              ss0.add(d * d);
+              const R dd = c0c.diff(xv);
+              ss0.add(dd * dd);
               lo0 = lo0 < xv ? lo0 : xv;
               hi0 = hi0 > xv ? hi0 : xv;
             }
@@ -640,7 +796,8 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
     const unsigned mn = (1u << 3) | (1u << 5), mx = (1u << 4) | (1u << 6);
     warp_reduce_to_shared<7>(sh, v, mn, mx);
     __syncthreads();
-    if (warp == 0 && !group_finish<7>(sh, grp, mn, mx) && lane == 0) sh.abort = 1;
+    const unsigned e = grp.epoch++;
+    if (warp == 0 && !group_finish<7>(sh, grp, e, mn, mx) && lane == 0) sh.abort = 1;
     __syncthreads();
     if (sh.abort) return false;
   }
@@ -665,7 +822,6 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
     if (!(fabs(gmean) < INFINITY) || !(st[11] < INFINITY)) atomicOr(a.status, kStatusNumeric);
     if (flips_tot > 0.0) atomicOr(a.status, kStatusRegionFlip);
   }
-    __syncthreads();
   }
   return true;
 }
@@ -679,8 +835,9 @@ __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, NQ>::value)) k_fine(co
   const int g = blockIdx.x - slot * G;
   if (slot >= n_slots) return;
   Group grp;
-  grp.part = a.partials + (size_t)slot * 2 * G * (kNV + 1);
-  grp.counter = a.counters + slot;
+  grp.part = a.partials + (size_t)slot * G * kSeatDoubles;
+  grp.flags = a.flags + (size_t)slot * G;
+  grp.tags = a.tags + (size_t)slot * kSlots * G;
   grp.status = a.status;
   grp.limit_ns = a.wait_limit_ns;
   grp.G = G;
@@ -690,7 +847,7 @@ __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, NQ>::value)) k_fine(co
   QuadStore<R, NQ> xs;
   xs.bind();
   for (int task = slot; task < a.n_tasks; task += n_slots) {
-    if (!fine_task<R, NQ, MULT>(a, a.slice_begin + task, g, grp, sh, xs)) return;
+    if (!fine_task<R, NQ, MULT, kStepUnrollSmem>(a, a.slice_begin + task, g, grp, sh, xs)) return;
   }
 }
 

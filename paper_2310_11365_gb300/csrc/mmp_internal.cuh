@@ -15,6 +15,8 @@ namespace mmp {
 constexpr int kTPB = 256;          // threads per block of the fine kernel
 constexpr int kWarps = kTPB / 32;
 constexpr int kNV = 8;             // values per group reduction slot
+constexpr int kSlots = 4;          // publication slots per CTA (a ring indexed by epoch)
+constexpr int kSeatDoubles = kSlots * kNV;  // reduction scratch per CTA of a group
 constexpr int kStat = MMP_STAT_STRIDE;
 constexpr int kMom = MMP_MOMENT_STRIDE;
 constexpr int kAff = 4;            // doubles per (slice, region) matching record
@@ -43,13 +45,22 @@ constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
 constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 
+// Both halves of the 64-bit product a * b from one wide multiply.
+__device__ __forceinline__ void mul_hilo(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
+  uint64_t p;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+  lo = (uint32_t)p;
+  hi = (uint32_t)(p >> 32);
+}
+
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint32_t rk0 = k0 + (uint32_t)r * kPhiloxW0;
     const uint32_t rk1 = k1 + (uint32_t)r * kPhiloxW1;
-    const uint32_t lo0 = kPhiloxM0 * c.x, hi0 = __umulhi(kPhiloxM0, c.x);
-    const uint32_t lo1 = kPhiloxM1 * c.z, hi1 = __umulhi(kPhiloxM1, c.z);
+    uint32_t hi0, lo0, hi1, lo1;
+    mul_hilo(kPhiloxM0, c.x, hi0, lo0);
+    mul_hilo(kPhiloxM1, c.z, hi1, lo1);
     c = make_uint4(hi1 ^ c.y ^ rk0, lo1, hi0 ^ c.w ^ rk1, lo0);
   }
   return c;
@@ -72,17 +83,20 @@ __device__ __forceinline__ double fmaR(double a, double b, double c) { return __
 // Box-Muller: z = sqrt(-2 ln ua) (cos 2 pi ub, sin 2 pi ub).
 // FP32 form on the special-function unit: ln ua from the hardware log2,
 // sqrt t as t * rsqrt(t), and sin/cos of theta = 2 pi (ub - 1/2), which lies
-// in (-pi, pi) where the hardware sin/cos are accurate; then
+// in [-pi, pi) where the hardware sin/cos are accurate; then
 // cos 2 pi ub = -cos theta and sin 2 pi ub = -sin theta.  The draws differ
 // from the FP64 definition by a few 1e-6 absolute (bounded in the tests).
-__device__ __forceinline__ void box_muller(float ua, float ub, float& z0, float& z1) {
+// ub enters as fb = 1 + (o >> 9) 2^-23 in [1, 2): ub - 1/2 = (fb - 3/2) + 2^-24,
+// where fb - 3/2 is exact, so theta takes one add and one fused multiply-add.
+__device__ __forceinline__ void box_muller_f(float ua, float fb, float& z0, float& z1) {
   const float t = -1.38629436f * __log2f(ua);  // -2 ln 2 log2(ua) > 0 for ua < 1
   const float r = t * rsqrtf(t);
   float s, c;
-  __sincosf(6.28318531f * (ub - 0.5f), &s, &c);
+  __sincosf(__fmaf_rn(__fsub_rn(fb, 1.5f), 6.28318531f, 3.74507028e-7f), &s, &c);  // 2 pi 2^-24
   z0 = -r * c;
   z1 = -r * s;
 }
+__device__ __forceinline__ float unit_f(uint32_t o) { return __uint_as_float(0x3F800000u | (o >> 9)); }
 __device__ __forceinline__ void box_muller(double ua, double ub, double& z0, double& z1) {
   const double r = sqrt(-2.0 * log(ua));
   double s, c;
@@ -95,8 +109,8 @@ template <typename R>
 __device__ __forceinline__ void normals4(uint4 o, R z[4]);
 template <>
 __device__ __forceinline__ void normals4<float>(uint4 o, float z[4]) {
-  box_muller(uniform_f(o.x), uniform_f(o.y), z[0], z[1]);
-  box_muller(uniform_f(o.z), uniform_f(o.w), z[2], z[3]);
+  box_muller_f(uniform_f(o.x), unit_f(o.y), z[0], z[1]);
+  box_muller_f(uniform_f(o.z), unit_f(o.w), z[2], z[3]);
 }
 template <>
 __device__ __forceinline__ void normals4<double>(uint4 o, double z[4]) {
@@ -132,8 +146,16 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_gpu_b64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu_b64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
