@@ -116,23 +116,19 @@ __device__ __forceinline__ void group_publish(const Group& grp, unsigned e, cons
 __device__ __forceinline__ bool group_wait(const Group& grp, unsigned e) {
   bool ok = true;
   for (int c = threadIdx.x & 31; c < grp.G && ok; c += 32) {
-    unsigned long long t0 = 0;
-    int spins = 0;
-    while (ld_acquire_gpu(grp.flags + c) <= e) {
-      if (++spins >= 32) {
-        spins = 0;
-        const unsigned long long now = globaltimer_ns();
-        if (t0 == 0) {
-          t0 = now;
-        } else if (now - t0 > grp.limit_ns) {
-          atomicOr(grp.status, kStatusTimeout);
-          ok = false;
-          break;
-        }
-        if (*(volatile unsigned*)grp.status & kStatusTimeout) {
-          ok = false;
-          break;
-        }
+    if (ld_acquire_gpu(grp.flags + c) > e) continue;
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+      __nanosleep(64);
+      if (ld_acquire_gpu(grp.flags + c) > e) break;
+      if (globaltimer_ns() - t0 > grp.limit_ns) {
+        atomicOr(grp.status, kStatusTimeout);
+        ok = false;
+        break;
+      }
+      if (*(volatile unsigned*)grp.status & kStatusTimeout) {
+        ok = false;
+        break;
       }
     }
   }
@@ -280,37 +276,54 @@ struct StepSum<float> {
     st_relaxed_gpu_b64(grp.tags + (size_t)(e & (unsigned)(kSlots - 1)) * grp.G + grp.g, w);
   }
   // whole warp: bounded wait for the tagged words of epoch e of every CTA
-  // (lane l reads CTAs l, l + 32, ...), their sum in CTA order
+  // (lane l reads CTAs l, l + 32, ...; a lane issues its loads of up to 128
+  // CTAs before examining any), their sum in CTA order
   static __device__ __forceinline__ bool fetch(const Group& grp, unsigned e, T& sum) {
     const uint32_t tag = tag_of(e);
     const unsigned long long* row = grp.tags + (size_t)(e & (unsigned)(kSlots - 1)) * grp.G;
+    const int lane = threadIdx.x & 31;
     T v = zero();
     bool ok = true;
-    for (int c = threadIdx.x & 31; c < grp.G; c += 32) {
-      unsigned long long w = ld_relaxed_gpu_b64(row + c);
-      unsigned long long t0 = 0;
-      int spins = 0;
-      while (ok && ((uint32_t)(w >> 32) & 0xFFFFu) != tag) {
-        if (++spins >= 32) {
-          spins = 0;
-          const unsigned long long now = globaltimer_ns();
-          if (t0 == 0) {
-            t0 = now;
-          } else if (now - t0 > grp.limit_ns) {
-            atomicOr(grp.status, kStatusTimeout);
-            ok = false;
-          }
-          if (*(volatile unsigned*)grp.status & kStatusTimeout) ok = false;
-        }
-        if (ok) w = ld_relaxed_gpu_b64(row + c);
-      }
-      if (!ok) break;
-      v = add(v, make_float2(__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)(w >> 32) & 0xFFFF0000u)));
-    }
+    for (int base = 0; base < grp.G; base += 128) {
+      unsigned long long w[4];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = add(v, shfl_xor(v, off));
+      for (int k = 0; k < 4; ++k) {
+        const int c = base + lane + 32 * k;
+        w[k] = c < grp.G ? ld_relaxed_gpu_b64(row + c) : 0ull;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int c = base + lane + 32 * k;
+        if (c < grp.G) {
+          if (ok && ((uint32_t)(w[k] >> 32) & 0xFFFFu) != tag) ok = wait_word(grp, row + c, tag, w[k]);
+          v = add(v, make_float2(__uint_as_float((uint32_t)w[k]),
+                                 __uint_as_float((uint32_t)(w[k] >> 32) & 0xFFFF0000u)));
+        }
+      }
+    }
+    if (grp.G == 1) {
+      v = bcast0(v);
+    } else {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v = add(v, shfl_xor(v, off));
+    }
     sum = v;
     return __all_sync(0xffffffffu, ok);
+  }
+  // bounded wait (with back-off) until the word at p carries the tag
+  static __device__ __noinline__ bool wait_word(const Group& grp, const unsigned long long* p, uint32_t tag,
+                                                unsigned long long& w) {
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+      __nanosleep(64);
+      w = ld_relaxed_gpu_b64(p);
+      if (((uint32_t)(w >> 32) & 0xFFFFu) == tag) return true;
+      if (globaltimer_ns() - t0 > grp.limit_ns) {
+        atomicOr(grp.status, kStatusTimeout);
+        return false;
+      }
+      if (*(volatile unsigned*)grp.status & kStatusTimeout) return false;
+    }
   }
   // sum / P with inv_p = 1 / P rounded to float
   static __device__ __forceinline__ float mean(T v, float inv_p, long long) {
@@ -581,15 +594,15 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   }
   // The sum of the inputs is epoch E.  The shift form reads it at the end
   // of step 0 (or right here when there are no steps); the general form
-  // needs m_0 before step 0.  Warp 0 does all cross-CTA work: it publishes
-  // the CTA's sums and, before each CTA barrier, fetches the group sum the
-  // other warps need after it (through sh.gsum).
+  // needs m_0 before step 0.  Warp 0 does all cross-CTA work: after each
+  // CTA barrier it publishes the CTA's sum of the step just finished, and
+  // before the next barrier it reads the group sum that the other warps need
+  // after it (through sh.gsum).
   step_sum_warp<R>(sh, 1, s_in);
   __syncthreads();
-  ST own = SS::zero();  // warp 0: this CTA's sum of the latest epoch it published
   if (warp == 0) {
-    own = step_sum_cta<R>(sh, 1);
-    if (G > 1 && lane == 0) SS::publish(grp, E, own);
+    const ST cta = step_sum_cta<R>(sh, 1);
+    if (lane == 0) SS::publish(grp, E, cta);
   }
   grp.epoch = E + 1u;
   double m_in = 0.0;
@@ -597,8 +610,8 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   R base = (R)0, boff = (R)0;  // general form: kappa m_j + c0, (BE m_j + B0) sqrt(h)
   if (!kLag || nf == 0) {
     if (warp == 0) {
-      ST sum = own;
-      const bool ok = G == 1 || SS::fetch(grp, E, sum);
+      ST sum;
+      const bool ok = SS::fetch(grp, E, sum);
       if (lane == 0) {
         SS::gsum(sh, 1) = sum;
         if (!ok) sh.abort = 1;
@@ -652,12 +665,12 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
     }
     step_sum_warp<R>(sh, j & 1, s);
     if constexpr (kLag) {
-      // Warp 0 fetches the group sum of the previous epoch (published by
-      // the peers a whole step ago) before the barrier:
-      //   m_j = mean(y_{j-1}) + d_{j-1},  d_j = h (kappa m_j + c0).
+      // m_j = mean(y_{j-1}) + d_{j-1},  d_j = h (kappa m_j + c0), from the
+      // group sum of epoch E + j, which the peers published when their
+      // step j - 1 ended
       if (warp == 0) {
-        ST sum = own;
-        const bool ok = G == 1 || SS::fetch(grp, E + (unsigned)j, sum);
+        ST sum;
+        const bool ok = SS::fetch(grp, E + (unsigned)j, sum);
         if (lane == 0) {
           SS::gsum(sh, j & 1) = sum;
           if (!ok) sh.abort = 1;
@@ -676,18 +689,20 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
         u[2] = b0sq;
       }
       // this step's sum becomes epoch E + 1 + j (unless nothing reads it)
-      if (warp == 0) {
-        own = step_sum_cta<R>(sh, j & 1);
-        if (G > 1 && j + 1 < nf && lane == 0) SS::publish(grp, E + 1u + (unsigned)j, own);
+      if (j + 1 < nf) {
+        if (warp == 0) {
+          const ST cta = step_sum_cta<R>(sh, j & 1);
+          if (lane == 0) SS::publish(grp, E + 1u + (unsigned)j, cta);
+        }
+        grp.epoch = E + 2u + (unsigned)j;
       }
-      if (j + 1 < nf) grp.epoch = E + 2u + (unsigned)j;
     } else {
       __syncthreads();
       const unsigned e = E + 1u + (unsigned)j;
       if (warp == 0) {
         ST sum = step_sum_cta<R>(sh, j & 1);
-        if (G > 1 && lane == 0) SS::publish(grp, e, sum);
-        const bool ok = G == 1 || SS::fetch(grp, e, sum);
+        if (lane == 0) SS::publish(grp, e, sum);
+        const bool ok = SS::fetch(grp, e, sum);
         if (lane == 0) {
           SS::gsum(sh, j & 1) = sum;
           if (!ok) sh.abort = 1;
