@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -28,11 +29,40 @@ WORKLOAD = "config2: cubic MV SDE dX=(-X^3+kappa(E[X]-X))dt+sigma dW, kappa=1, s
 # Algorithmic FP32/INT32 lane operations of one particle-step (mixed path):
 # Philox-4x32-10 shared by 4 particles (10 rounds x (2 wide multiplies +
 # 2 three-input xors) / 4 = 10), the uniform map (3), Box-Muller shared by 2
-# particles (log 2, sqrt 2, sin/cos 3, products 2 -> 4.5), the update x^2 and
-# four fused multiply-adds (5), the running sum (1).
+# particles (log 2, sqrt 2, sin/cos 3, products 2 -> 4.5), the update (the
+# pending shift, x^2 and three fused multiply-adds: 5), the running sum (1).
 ALG_OPS_PER_PARTICLE_STEP = 23.5
 SMS = 152
 LANES = 128
+
+
+# The committed ncu summary of the fine kernel records its DRAM bytes per
+# slice and a hash of the sources it was captured on; the bench reports
+# traffic only while those sources are unchanged.
+PROFILE = os.path.join(ROOT, "profiles", "k_fine_config2_N8_mixed.md")
+PROFILE_SOURCES = ("fine_kernel.cuh", "mmp_internal.cuh", "fine_f32.cu")
+
+
+def _profile_bytes_per_slice():
+    import hashlib
+
+    try:
+        fields = {}
+        with open(PROFILE) as f:
+            for line in f:
+                line = line.strip().lstrip("- ")
+                for key in ("source-sha256-16:", "dram-bytes-per-slice:"):
+                    if line.startswith(key):
+                        fields[key] = line[len(key):].split()[0]
+        h = hashlib.sha256()
+        for name in PROFILE_SOURCES:
+            with open(os.path.join(ROOT, "paper_2310_11365_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest()[:16] != fields.get("source-sha256-16:"):
+            return None
+        return float(fields["dram-bytes-per-slice:"])
+    except Exception:
+        return None
 
 
 def _peaks():
@@ -295,6 +325,11 @@ def main():
     peaks = _peaks()
     f_clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak = SMS * LANES * f_clk / 1e12
+    # DRAM bytes per launch: the captured bytes per slice x slices per launch
+    bps = _profile_bytes_per_slice()
+    nf = math.ceil(p.T / p.N / p.dt - 1e-9)
+    slices_per_launch = steps_done / (p.P * nf) / max(1, tm["fine_launches"])
+    traffic = None if bps is None else bps * slices_per_launch
 
     # end to end through the C-ABI with host buffers: u0 from pinned host
     # memory in, all moments back to host, every step
@@ -355,7 +390,8 @@ def main():
                        "plan": plan},
             "time_to_tol_s": ms / 1e3 / args.steps, "sweeps_to_tol": sweeps[-1],
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
+                         "traffic_unit": "DRAM bytes per launch (ncu capture scaled by slices per launch)",
                          "kernel": "k_fine<float>", "ops_per_particle_step": ALG_OPS_PER_PARTICLE_STEP,
                          "fine_launches": tm["fine_launches"],
                          "fine_ms_per_launch": tm["fine_ms"] / max(1, tm["fine_launches"]),

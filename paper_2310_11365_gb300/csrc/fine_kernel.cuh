@@ -295,7 +295,10 @@ struct StepSum<float> {
       for (int k = 0; k < 4; ++k) {
         const int c = base + lane + 32 * k;
         if (c < grp.G) {
-          if (ok && ((uint32_t)(w[k] >> 32) & 0xFFFFu) != tag) ok = wait_word(grp, row + c, tag, w[k]);
+          if (ok && ((uint32_t)(w[k] >> 32) & 0xFFFFu) != tag) {
+            w[k] = wait_word(grp, row + c, tag);
+            ok = ((uint32_t)(w[k] >> 32) & 0xFFFFu) == tag;
+          }
           v = add(v, make_float2(__uint_as_float((uint32_t)w[k]),
                                  __uint_as_float((uint32_t)(w[k] >> 32) & 0xFFFF0000u)));
         }
@@ -310,19 +313,20 @@ struct StepSum<float> {
     sum = v;
     return __all_sync(0xffffffffu, ok);
   }
-  // bounded wait (with back-off) until the word at p carries the tag
-  static __device__ __noinline__ bool wait_word(const Group& grp, const unsigned long long* p, uint32_t tag,
-                                                unsigned long long& w) {
+  // bounded wait (with back-off) until the word at p carries the tag; on
+  // timeout the result is 0, whose tag (no bit 15) never matches
+  static __device__ __noinline__ unsigned long long wait_word(const Group& grp, const unsigned long long* p,
+                                                              uint32_t tag) {
     const unsigned long long t0 = globaltimer_ns();
     for (;;) {
       __nanosleep(64);
-      w = ld_relaxed_gpu_b64(p);
-      if (((uint32_t)(w >> 32) & 0xFFFFu) == tag) return true;
+      const unsigned long long w = ld_relaxed_gpu_b64(p);
+      if (((uint32_t)(w >> 32) & 0xFFFFu) == tag) return w;
       if (globaltimer_ns() - t0 > grp.limit_ns) {
         atomicOr(grp.status, kStatusTimeout);
-        return false;
+        return 0ull;
       }
-      if (*(volatile unsigned*)grp.status & kStatusTimeout) return false;
+      if (*(volatile unsigned*)grp.status & kStatusTimeout) return 0ull;
     }
   }
   // sum / P with inv_p = 1 / P rounded to float
