@@ -185,10 +185,12 @@ def cpu_baseline(seconds: float = 12.0) -> dict:
             "sample": f"FP64 oracle fine propagator on the config-2 model, P=2000, {slices} slices x {nf} steps ({steps:.3g} particle-steps, {dt:.1f} s)"}
 
 
-def batched_run(n_problems: int, sweeps: int, rank: int) -> dict:
+def batched_run(n_problems: int, sweeps: int, rank: int, to_tol: bool = False) -> dict:
     """Config 5 (batched): n problems of the linear / double-well forms with
     P log-uniform in [1e4, 2e6] and N in 16..128, one cooperative launch per
-    sweep; the first `sweeps` fine sweeps are timed (device time)."""
+    sweep, sweeps built on the device and replayed from a CUDA graph; the
+    sweeps after a warm-up sweep are timed (device time), and with to_tol a
+    second run from lifting to every problem's tolerance."""
     import torch
 
     from paper_2310_11365_gb300 import mmp
@@ -208,10 +210,25 @@ def batched_run(n_problems: int, sweeps: int, rank: int) -> dict:
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     tm = mmp.mmp_timing(s.ctx, reset=True)
-    out = {"problems": n_problems, "sweeps_timed": sweeps, "ms": ms,
+    info = mmp.mmp_batch_info(s.ctx)
+    out = {"problems": n_problems, "sweeps_timed": sweeps, "ms": ms, "batched": info["batched"],
+           "cuda_graph": info["graph"],
            "particle_steps": tm["fine_particle_steps"], "value": tm["fine_particle_steps"] / (ms / 1e3),
            "unit": UNIT, "fine_launches_per_sweep": tm["fine_launches"] / max(1, sweeps),
            "sum_P": int(sum(p.P for p in probs)), "max_P": int(max(p.P for p in probs))}
+    if to_tol:
+        mmp.mmp_timing(s.ctx, reset=True)
+        ev0.record()
+        s.run()
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        tm = mmp.mmp_timing(s.ctx, reset=True)
+        sw = [s.status(i)["sweeps"] for i in range(len(probs))]
+        out["to_tol"] = {"ms": ms, "particle_steps": tm["fine_particle_steps"],
+                         "value": tm["fine_particle_steps"] / (ms / 1e3),
+                         "sweeps_max": max(sw), "sweeps_mean": sum(sw) / len(sw),
+                         "converged": sum(1 for i in range(len(probs)) if s.status(i)["converged"])}
     s.close()
     return out
 
@@ -260,8 +277,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--N", type=int, default=None, help="override the slice count (profiling runs)")
     ap.add_argument("--P", type=int, default=None, help="override the particle count (profiling runs)")
-    ap.add_argument("--batch", type=int, default=0,
-                    help="also time config 5 (batched problems): number of problems (0: skip)")
+    ap.add_argument("--batch", type=int, default=512,
+                    help="problems of the batched config-5 workload (0: skip)")
+    ap.add_argument("--batch-tol", action="store_true",
+                    help="also time the batched workload from lifting to tolerance")
     ap.add_argument("--batch-sweeps", type=int, default=2, help="fine sweeps timed for the batched workload")
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -372,7 +391,7 @@ def main():
 
     batch = None
     if args.batch > 0:
-        batch = batched_run(args.batch, args.batch_sweeps, rank)
+        batch = batched_run(args.batch, args.batch_sweeps, rank, args.batch_tol)
 
     cpu = None
     if rank == 0 and not args.no_cpu:

@@ -209,6 +209,15 @@ int mmp_set_timing(mmp_ctx* ctx, int on);
 int mmp_timing(mmp_ctx* ctx, int reset, double* fine_ms, long long* fine_launches,
                double* fine_particle_steps, long long* other_launches);
 
+/* Batched sweeps of a context with several problems (one cooperative
+ * launch per sweep over every unconverged problem's slices; the task list
+ * is built on the device, so sweeps run back to back).  batched (may be
+ * NULL) = 1 if the context batches its problems; graph (may be NULL) = 1
+ * if its sweeps replay from a captured CUDA graph (known after the first
+ * mmp_iterate; 0 when MMP_BATCH_GRAPH=0 or the runtime refused the
+ * capture, in which case the same work is enqueued directly). */
+int mmp_batch_info(mmp_ctx* ctx, int* batched, int* graph);
+
 /* One fine propagation F_n of an explicit ensemble (no matching):
  * reads P values at u_in (device), writes F_n(u_in) to u_out (device,
  * may not alias u_in) and its restriction record to stats_out (host,

@@ -3,6 +3,7 @@
 // (Eq. mM_parareal_other_k_NEW) on one stream.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -49,14 +50,20 @@ namespace {
 
 int g_last_cuda_error = 0;
 
-int cuda_fail(cudaError_t e) {
+// Records a failed CUDA call; MMP_DEBUG=1 also names it on stderr.
+int cuda_fail(cudaError_t e, const char* what, int line) {
   g_last_cuda_error = (int)e;
+  static const bool debug = [] {
+    const char* v = std::getenv("MMP_DEBUG");
+    return v != nullptr && v[0] == '1';
+  }();
+  if (debug) std::fprintf(stderr, "libmmp: %s (api.cu:%d): %s\n", what, line, cudaGetErrorString(e));
   return MMP_ERR_CUDA;
 }
 #define MMP_CUDA(call)                         \
   do {                                         \
     cudaError_t e_ = (call);                   \
-    if (e_ != cudaSuccess) return cuda_fail(e_); \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call, __LINE__); \
   } while (0)
 
 constexpr size_t kAlign = 256;
@@ -176,6 +183,16 @@ int plan(Prob& p, const Device& dev, int batch_nq = 0) {
     p.nq = (int)std::min<long long>(batch_nq, std::max<long long>(1, ((long long)p.Q + kTPB - 1) / kTPB));
     p.G = (int)(((long long)p.Q + (long long)p.nq * kTPB - 1) / ((long long)p.nq * kTPB));
     p.slots_max = 1;
+    // the per-problem kernel still serves lifting and serial runs
+    const void* fn = fine_kernel(p.d.precision, kLayoutSmem, p.nq, p.mult);
+    size_t limit = 0;
+    const int rc = allow_dynamic_smem(fn, dev.dev, &limit);
+    if (rc) return rc;
+    if (fine_smem_bytes(p.d.precision, kLayoutSmem, p.nq) > limit) return MMP_ERR_UNSUPPORTED;
+    int occ = 0;
+    MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB,
+                                                           fine_smem_bytes(p.d.precision, kLayoutSmem, p.nq)));
+    if ((long long)occ * dev.sms < p.G) return MMP_ERR_UNSUPPORTED;
     return MMP_OK;
   }
   const char* env = std::getenv("MMP_FINE_LAYOUT");
@@ -311,10 +328,22 @@ struct mmp_ctx {
   DriverArgs* b_dargs = nullptr;
   int* b_sweep = nullptr;
   double* b_summary = nullptr;
-  std::vector<BatchTask> h_tasks;
-  std::vector<int> h_sweep;
+  const double** b_ctlp = nullptr;  // device-side task builder inputs
+  int* b_order = nullptr;
+  int* b_N = nullptr;
+  int* b_G = nullptr;
+  int* b_remaining = nullptr;
+  size_t b_seats_cap = 0;
   std::vector<double> h_summary;
+  // a CUDA graph of kGraphSweeps batched sweeps (built on first use on a
+  // private stream: the context stream may be the legacy default stream,
+  // which cannot be captured)
+  cudaGraphExec_t b_graph = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  bool b_graph_failed = false;
   ~mmp_ctx() {
+    if (b_graph != nullptr) cudaGraphExecDestroy(b_graph);
+    if (cap_stream != nullptr) cudaStreamDestroy(cap_stream);
     for (auto& pr : pending) {
       cudaEventDestroy(pr.first);
       cudaEventDestroy(pr.second);
@@ -445,6 +474,11 @@ size_t batch_layout(const std::vector<Prob>& probs, const BatchLayout& B, char* 
   char* dargs_p = ptr(sizeof(DriverArgs) * n);
   char* sweep_p = ptr(sizeof(int) * n);
   char* summary_p = ptr(sizeof(double) * 5 * n);
+  char* ctlp_p = ptr(sizeof(double*) * n);
+  char* order_p = ptr(sizeof(int) * n);
+  char* N_p = ptr(sizeof(int) * n);
+  char* G_p = ptr(sizeof(int) * n);
+  char* remaining_p = ptr(sizeof(int) * 4);
   if (c != nullptr) {
     c->b_probs = (FineArgs*)probs_p;
     c->b_bufs = (void**)bufs_p;
@@ -457,6 +491,12 @@ size_t batch_layout(const std::vector<Prob>& probs, const BatchLayout& B, char* 
     c->b_dargs = (DriverArgs*)dargs_p;
     c->b_sweep = (int*)sweep_p;
     c->b_summary = (double*)summary_p;
+    c->b_ctlp = (const double**)ctlp_p;
+    c->b_order = (int*)order_p;
+    c->b_N = (int*)N_p;
+    c->b_G = (int*)G_p;
+    c->b_remaining = (int*)remaining_p;
+    c->b_seats_cap = B.seats_cap;
   }
   return cv.off;
 }
@@ -526,55 +566,57 @@ int batch_setup(mmp_ctx* c) {
   std::vector<FineArgs> fa(n);
   std::vector<void*> bufs(2 * n);
   std::vector<DriverArgs> da(n);
+  std::vector<const double*> ctlp(n);
+  std::vector<int> order(n), Ns(n), Gs(n);
   for (int i = 0; i < n; ++i) {
     fa[i] = make_fine_args(c, c->probs[i]);
     bufs[2 * i] = c->probs[i].B[0];
     bufs[2 * i + 1] = c->probs[i].B[1];
     da[i] = make_driver_args(c->probs[i], 0);
+    ctlp[i] = c->probs[i].ctl;
+    order[i] = i;
+    Ns[i] = c->probs[i].d.N;
+    Gs[i] = c->probs[i].G;
   }
+  // tasks largest first: problems by P n_f, descending, ties by index
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const Prob& px = c->probs[x];
+    const Prob& py = c->probs[y];
+    return (double)px.d.P * px.nf > (double)py.d.P * py.nf;
+  });
   MMP_CUDA(cudaMemcpyAsync(c->b_probs, fa.data(), sizeof(FineArgs) * n, cudaMemcpyHostToDevice, c->stream));
   MMP_CUDA(cudaMemcpyAsync(c->b_bufs, bufs.data(), sizeof(void*) * 2 * n, cudaMemcpyHostToDevice, c->stream));
   MMP_CUDA(cudaMemcpyAsync(c->b_dargs, da.data(), sizeof(DriverArgs) * n, cudaMemcpyHostToDevice, c->stream));
+  MMP_CUDA(cudaMemcpyAsync(c->b_ctlp, ctlp.data(), sizeof(double*) * n, cudaMemcpyHostToDevice, c->stream));
+  MMP_CUDA(cudaMemcpyAsync(c->b_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
+  MMP_CUDA(cudaMemcpyAsync(c->b_N, Ns.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
+  MMP_CUDA(cudaMemcpyAsync(c->b_G, Gs.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
   MMP_CUDA(cudaStreamSynchronize(c->stream));
   return MMP_OK;
 }
 
-// One batched sweep: every unconverged problem's slices k-1..N-1 in one
-// cooperative launch (largest tasks first), then every driver in one launch.
-int batch_sweep(mmp_ctx* c) {
+// Enqueues one batched sweep, all on the device: clear the exchange words
+// and flags of every seat, build the task list from the problems' control
+// blocks, one cooperative launch over every unconverged problem's slices
+// k-1..N-1 (largest tasks first), then every driver in one launch.  No host
+// work depends on the sweep, so sweeps can be enqueued back to back and
+// captured in a graph.
+int batch_enqueue_sweep(mmp_ctx* c, cudaStream_t stream) {
   const int n = (int)c->probs.size();
-  std::vector<BatchTask>& tasks = c->h_tasks;
-  std::vector<int>& sweep = c->h_sweep;
-  tasks.clear();
-  sweep.assign(n, -1);
-  for (int i = 0; i < n; ++i) {
-    Prob& p = c->probs[i];
-    if (p.done) continue;
-    const int k = p.sweeps + 1;
-    sweep[i] = k;
-    for (int sl = k - 1; sl < p.d.N; ++sl) tasks.push_back({i, sl, k == 1 ? -1 : ((k - 1) & 1), k & 1, 0, p.G});
-  }
-  if (tasks.empty()) return MMP_OK;
-  std::stable_sort(tasks.begin(), tasks.end(), [&](const BatchTask& x, const BatchTask& y) {
-    const Prob& px = c->probs[x.prob];
-    const Prob& py = c->probs[y.prob];
-    return (double)px.d.P * px.nf > (double)py.d.P * py.nf;
-  });
-  int seats = 0;
-  double steps = 0.0;
-  for (BatchTask& t : tasks) {
-    t.seat0 = seats;
-    seats += t.G;
-    steps += (double)c->probs[t.prob].d.P * c->probs[t.prob].nf;
-  }
-  const int nt = (int)tasks.size();
-  int header[4] = {nt, seats, 0, 0};
-  MMP_CUDA(cudaMemcpyAsync(c->b_tasks, tasks.data(), sizeof(BatchTask) * nt, cudaMemcpyHostToDevice, c->stream));
-  MMP_CUDA(cudaMemcpyAsync(c->b_header, header, sizeof(header), cudaMemcpyHostToDevice, c->stream));
-  MMP_CUDA(cudaMemcpyAsync(c->b_sweep, sweep.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
-  MMP_CUDA(cudaMemsetAsync(c->b_seat, 0, sizeof(unsigned) * 4, c->stream));
-  MMP_CUDA(cudaMemsetAsync(c->b_flags, 0, sizeof(unsigned) * seats, c->stream));
-  MMP_CUDA(cudaMemsetAsync(c->b_tags, 0, sizeof(unsigned long long) * kSlots * seats, c->stream));
+  MMP_CUDA(cudaMemsetAsync(c->b_flags, 0, sizeof(unsigned) * c->b_seats_cap, stream));
+  MMP_CUDA(cudaMemsetAsync(c->b_tags, 0, sizeof(unsigned long long) * kSlots * c->b_seats_cap, stream));
+  BatchPlanArgs pa;
+  pa.ctl = c->b_ctlp;
+  pa.order = c->b_order;
+  pa.N = c->b_N;
+  pa.G = c->b_G;
+  pa.n = n;
+  pa.tasks = c->b_tasks;
+  pa.header = c->b_header;
+  pa.sweep = c->b_sweep;
+  pa.seat_counter = c->b_seat;
+  pa.remaining = c->b_remaining;
+  MMP_CUDA(launch_batch_plan(pa, stream));
   BatchArgs b;
   b.probs = c->b_probs;
   b.bufs = c->b_bufs;
@@ -584,21 +626,63 @@ int batch_sweep(mmp_ctx* c) {
   b.flags = c->b_flags;
   b.tags = c->b_tags;
   b.partials = c->b_partials;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c->timing) {
-    MMP_CUDA(cudaEventCreate(&e0));
-    MMP_CUDA(cudaEventCreate(&e1));
-    MMP_CUDA(cudaEventRecord(e0, c->stream));
+  MMP_CUDA(launch_fine_batch(c->probs[0].d.precision, c->probs[0].mult, c->batch_grid, c->batch_smem, b, stream));
+  MMP_CUDA(launch_driver_batch(c->b_dargs, c->b_sweep, c->b_summary, n, stream));
+  return MMP_OK;
+}
+
+// Batched sweeps per graph launch.  A graph runs this many sweeps whatever
+// the problems do; sweeps after the last problem finished (or after the
+// requested count) build no task and cost a few microseconds.
+constexpr int kGraphSweeps = 4;
+
+// Enqueues kGraphSweeps batched sweeps: one launch of a graph captured on
+// first use (MMP_BATCH_GRAPH=0, or a capture the runtime refuses, enqueues
+// the same work directly).
+int batch_enqueue_sweeps(mmp_ctx* c) {
+  const char* e = std::getenv("MMP_BATCH_GRAPH");
+  const bool want = !(e != nullptr && std::strcmp(e, "0") == 0);
+  if (want && c->b_graph == nullptr && !c->b_graph_failed) {
+    cudaGraph_t g = nullptr;
+    int rc = MMP_OK;
+    cudaError_t ce = cudaSuccess;
+    if (c->cap_stream == nullptr) ce = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+      for (int s = 0; s < kGraphSweeps && rc == MMP_OK; ++s) rc = batch_enqueue_sweep(c, c->cap_stream);
+      ce = cudaStreamEndCapture(c->cap_stream, &g);
+    }
+    if (ce == cudaSuccess && rc == MMP_OK) ce = cudaGraphInstantiate(&c->b_graph, g, 0);
+    if (g != nullptr) cudaGraphDestroy(g);
+    if (ce != cudaSuccess || rc != MMP_OK) {
+      // a refused capture is not an error of the run: enqueue directly
+      if (ce != cudaSuccess) cuda_fail(ce, "batched sweep capture (falling back to direct enqueue)", __LINE__);
+      cudaGetLastError();
+      if (c->b_graph != nullptr) cudaGraphExecDestroy(c->b_graph);
+      c->b_graph = nullptr;
+      c->b_graph_failed = true;
+    }
   }
-  MMP_CUDA(launch_fine_batch(c->probs[0].d.precision, c->probs[0].mult, c->batch_grid, c->batch_smem, b, c->stream));
-  if (c->timing) {
-    MMP_CUDA(cudaEventRecord(e1, c->stream));
-    c->pending.emplace_back(e0, e1);
+  bool launched = false;
+  if (want && c->b_graph != nullptr) {
+    const cudaError_t ce = cudaGraphLaunch(c->b_graph, c->stream);
+    if (ce == cudaSuccess) {
+      launched = true;
+    } else {
+      cuda_fail(ce, "batched sweep graph launch (falling back to direct enqueue)", __LINE__);
+      cudaGetLastError();
+      cudaGraphExecDestroy(c->b_graph);
+      c->b_graph = nullptr;
+      c->b_graph_failed = true;
+    }
   }
-  c->fine_launches += 1;
-  c->fine_steps += steps;
-  MMP_CUDA(launch_driver_batch(c->b_dargs, c->b_sweep, c->b_summary, n, c->stream));
-  c->other_launches += 1;
+  if (!launched) {
+    for (int s = 0; s < kGraphSweeps; ++s) {
+      int rc = batch_enqueue_sweep(c, c->stream);
+      if (rc) return rc;
+    }
+  }
+  c->other_launches += 2 * kGraphSweeps;
   return MMP_OK;
 }
 
@@ -746,7 +830,7 @@ int mmp_create(mmp_ctx** out, const mmp_problem_desc* descs, int n_problems, voi
     c->other_launches += 1;
     if (e != cudaSuccess) {
       delete c;
-      return cuda_fail(e);
+      return cuda_fail(e, "launch", __LINE__);
     }
   }
   if (c->batch) {
@@ -794,6 +878,8 @@ int mmp_lift(mmp_ctx* ctx) {
     p.last_change = 0.0;
     std::fill(p.out_buf.begin(), p.out_buf.end(), -1);
   }
+  if (ctx->batch)
+    MMP_CUDA(cudaMemsetAsync(ctx->b_summary, 0, sizeof(double) * 5 * ctx->probs.size(), ctx->stream));
   return MMP_OK;
 }
 
@@ -802,34 +888,66 @@ int mmp_iterate(mmp_ctx* ctx, int n_iter, int* all_converged) {
   for (Prob& p : ctx->probs)
     if (!p.lifted) return MMP_ERR_STATE;
   if (ctx->batch) {
+    // sweeps are built and run on the device, kGraphSweeps per graph launch;
+    // the host reads the problems' summaries once per launch
     const int n = (int)ctx->probs.size();
-    ctx->h_summary.assign((size_t)5 * n, 0.0);
-    for (int it = 0; it < n_iter; ++it) {
-      bool any = false;
-      for (Prob& p : ctx->probs) any = any || !p.done;
-      if (!any) break;
-      int rc = batch_sweep(ctx);
-      if (rc) return rc;
-      MMP_CUDA(cudaMemcpyAsync(ctx->h_summary.data(), ctx->b_summary, sizeof(double) * 5 * n, cudaMemcpyDeviceToHost,
-                               ctx->stream));
-      MMP_CUDA(cudaStreamSynchronize(ctx->stream));
-      rc = collect_timing(ctx);
-      if (rc) return rc;
-      int err = MMP_OK;
-      for (int i = 0; i < n; ++i) {
-        Prob& p = ctx->probs[i];
-        if (ctx->h_sweep[i] < 0) continue;
-        const double* sm = &ctx->h_summary[(size_t)5 * i];
-        const int k = ctx->h_sweep[i];
-        for (int sl = k - 1; sl < p.d.N; ++sl) p.out_buf[sl] = k & 1;
-        p.sweeps = k;
-        p.last_change = sm[0];
-        p.converged = sm[1] != 0.0 || k == p.d.N;
-        p.done = sm[3] != 0.0;
-        const int e = status_to_error((unsigned)sm[4]);
-        if (e && !err) err = e;
+    bool any = false;
+    for (Prob& p : ctx->probs) any = any || !p.done;
+    if (any && n_iter > 0) {
+      MMP_CUDA(cudaMemcpyAsync(ctx->b_remaining, &n_iter, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+      ctx->h_summary.assign((size_t)5 * n, 0.0);
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      for (int done_sweeps = 0; done_sweeps < n_iter;) {
+        if (ctx->timing) {
+          for (cudaEvent_t* ev : {&e0, &e1}) {
+            if (!ctx->ev_pool.empty()) {
+              *ev = ctx->ev_pool.back();
+              ctx->ev_pool.pop_back();
+            } else {
+              MMP_CUDA(cudaEventCreate(ev));
+            }
+          }
+          MMP_CUDA(cudaEventRecord(e0, ctx->stream));
+        }
+        int rc = batch_enqueue_sweeps(ctx);
+        if (rc) return rc;
+        if (ctx->timing) {
+          MMP_CUDA(cudaEventRecord(e1, ctx->stream));
+          ctx->pending.emplace_back(e0, e1);
+        }
+        done_sweeps += kGraphSweeps;
+        MMP_CUDA(cudaMemcpyAsync(ctx->h_summary.data(), ctx->b_summary, sizeof(double) * 5 * n,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+        rc = collect_timing(ctx);
+        if (rc) return rc;
+        int err = MMP_OK;
+        bool all = true;
+        int max_new = 0;
+        for (int i = 0; i < n; ++i) {
+          Prob& p = ctx->probs[i];
+          const double* sm = &ctx->h_summary[(size_t)5 * i];
+          const int K = (int)sm[2];
+          if (K <= p.sweeps) {  // not swept since the last look
+            all = all && p.done;
+            continue;
+          }
+          for (int k = p.sweeps + 1; k <= K; ++k)
+            ctx->fine_steps += (double)(p.d.N - k + 1) * (double)p.d.P * (double)p.nf;
+          max_new = std::max(max_new, K - p.sweeps);
+          p.sweeps = K;
+          for (int sl = 0; sl < p.d.N; ++sl) p.out_buf[sl] = std::min(K, sl + 1) & 1;
+          p.last_change = sm[0];
+          p.converged = sm[1] != 0.0 || K == p.d.N;
+          p.done = sm[3] != 0.0;
+          all = all && p.done;
+          const int e = status_to_error((unsigned)sm[4]);
+          if (e && !err) err = e;
+        }
+        ctx->fine_launches += max_new;
+        if (err) return err;
+        if (all) break;
       }
-      if (err) return err;
     }
     if (all_converged) {
       bool all = true;
@@ -885,8 +1003,10 @@ int mmp_run(mmp_ctx* ctx, int* sweeps_out) {
   int rc = mmp_lift(ctx);
   if (rc) return rc;
   int all = 0;
+  int most = 0;
+  for (Prob& p : ctx->probs) most = std::max(most, p.d.N);
   while (!all) {
-    rc = mmp_iterate(ctx, 1, &all);
+    rc = mmp_iterate(ctx, most, &all);
     if (rc) return rc;
   }
   if (sweeps_out) {
@@ -1096,6 +1216,13 @@ int mmp_timing(mmp_ctx* ctx, int reset, double* fine_ms, long long* fine_launche
     ctx->fine_launches = 0;
     ctx->other_launches = 0;
   }
+  return MMP_OK;
+}
+
+int mmp_batch_info(mmp_ctx* ctx, int* batched, int* graph) {
+  if (ctx == nullptr) return MMP_ERR_INVALID_ARG;
+  if (batched) *batched = ctx->batch ? 1 : 0;
+  if (graph) *graph = ctx->b_graph != nullptr ? 1 : 0;
   return MMP_OK;
 }
 

@@ -77,18 +77,95 @@ __global__ void __launch_bounds__(kTPB, kBatchOcc) k_fine_batch(const BatchArgs 
   }
 }
 
+// One CTA: per-problem task and seat counts, a block-wide scan over the
+// problems in order, then each thread writes the tasks of its problems.
+constexpr int kPlanThreads = 1024;
+
+__global__ void __launch_bounds__(kPlanThreads) k_batch_plan(const BatchPlanArgs a) {
+  __shared__ int s_t[kPlanThreads], s_s[kPlanThreads];
+  __shared__ int s_active;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_active = 0;
+  const bool go = *(volatile int*)a.remaining > 0;
+  const int per = (a.n + kPlanThreads - 1) / kPlanThreads;
+  const int r0 = min(a.n, tid * per), r1 = min(a.n, r0 + per);
+  auto next_sweep = [&](int i) -> int {  // k of problem i, or 0 if it does not sweep
+    const double* ctl = a.ctl[i];
+    return (go && ctl[3] == 0.0) ? (int)ctl[2] + 1 : 0;
+  };
+  int nt = 0, ns = 0, na = 0;
+  for (int r = r0; r < r1; ++r) {
+    const int i = a.order[r];
+    const int k = next_sweep(i);
+    if (k > 0) {
+      const int cnt = a.N[i] - k + 1;
+      nt += cnt;
+      ns += cnt * a.G[i];
+      na += 1;
+    }
+  }
+  s_t[tid] = nt;
+  s_s[tid] = ns;
+  __syncthreads();
+  if (na > 0) atomicAdd(&s_active, na);
+  for (int off = 1; off < kPlanThreads; off <<= 1) {  // inclusive scan
+    const int vt = tid >= off ? s_t[tid - off] : 0;
+    const int vs = tid >= off ? s_s[tid - off] : 0;
+    __syncthreads();
+    s_t[tid] += vt;
+    s_s[tid] += vs;
+    __syncthreads();
+  }
+  int t = s_t[tid] - nt, seat = s_s[tid] - ns;
+  for (int r = r0; r < r1; ++r) {
+    const int i = a.order[r];
+    const int k = next_sweep(i);
+    a.sweep[i] = k > 0 ? k : -1;
+    if (k == 0) continue;
+    for (int sl = k - 1; sl < a.N[i]; ++sl) {
+      a.tasks[t++] = BatchTask{i, sl, k == 1 ? -1 : ((k - 1) & 1), k & 1, seat, a.G[i]};
+      seat += a.G[i];
+    }
+  }
+  __syncthreads();
+  if (tid == kPlanThreads - 1) {
+    a.header[0] = s_t[tid];
+    a.header[1] = s_s[tid];
+    a.header[2] = s_active;
+    *a.seat_counter = 0u;
+    if (go) *a.remaining -= 1;
+  }
+}
+
+cudaError_t launch_batch_plan(const BatchPlanArgs& args, cudaStream_t stream) {
+  k_batch_plan<<<1, kPlanThreads, 0, stream>>>(args);
+  return cudaGetLastError();
+}
+
 const void* fine_batch_kernel(int precision, bool mult) {
   if (precision == MMP_MIXED)
     return mult ? (const void*)k_fine_batch<float, true> : (const void*)k_fine_batch<float, false>;
   return mult ? (const void*)k_fine_batch<double, true> : (const void*)k_fine_batch<double, false>;
 }
 
+// Cooperative launch through cudaLaunchKernelEx with the cooperative
+// attribute: the form stream capture records as a cooperative kernel node
+// (cudaLaunchCooperativeKernel itself cannot be captured).
 cudaError_t launch_fine_batch(int precision, bool mult, int grid, size_t smem, const BatchArgs& args,
                               cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kTPB);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   BatchArgs copy = args;
   void* params[] = {&copy};
-  return cudaLaunchCooperativeKernel(fine_batch_kernel(precision, mult), dim3(grid), dim3(kTPB), params, smem,
-                                     stream);
+  return cudaLaunchKernelExC(&cfg, fine_batch_kernel(precision, mult), params);
 }
 
 }  // namespace mmp

@@ -34,6 +34,26 @@ struct BatchArgs {
   double* partials;        // [total seats] x kSeatDoubles doubles
 };
 
+// Device-side builder of a batched sweep's task list, so that sweeps can be
+// enqueued back to back (and captured in a CUDA graph) without the host:
+// every problem whose control block says "not done" contributes its slices
+// k-1 .. N-1 (k = sweeps done + 1), problems in `order` (largest P n_f
+// first), seats handed out in task order.  A sweep budget (`remaining`)
+// stops the sweeps after the requested number.
+struct BatchPlanArgs {
+  const double* const* ctl;  // [n] control blocks: ctl[2] sweeps done, ctl[3] done
+  const int* order;          // [n] problem indices, largest P n_f first (stable)
+  const int* N;              // [n] slices
+  const int* G;              // [n] CTAs per slice
+  int n;
+  BatchTask* tasks;          // out: task list
+  int* header;               // out: [0] tasks, [1] seats, [2] problems swept
+  int* sweep;                // out: [n] sweep index k of each problem, -1 if idle
+  unsigned* seat_counter;    // zeroed
+  int* remaining;            // sweeps still allowed (decremented when > 0)
+};
+cudaError_t launch_batch_plan(const BatchPlanArgs& args, cudaStream_t stream);
+
 const void* fine_batch_kernel(int precision, bool mult);
 cudaError_t launch_fine_batch(int precision, bool mult, int grid, size_t smem, const BatchArgs& args,
                               cudaStream_t stream);

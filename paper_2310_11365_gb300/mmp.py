@@ -34,6 +34,7 @@ EXPORTED = [
     "mmp_get_moments", "mmp_get_particles", "mmp_fine_serial", "mmp_fine", "mmp_philox",
     "mmp_normals", "mmp_get_plan", "mmp_set_timing", "mmp_timing", "mmp_fine_static",
     "mmp_set_params", "mmp_adjoint_workspace_size", "mmp_adjoint_forward", "mmp_adjoint_backward",
+    "mmp_batch_info",
 ]
 
 
@@ -99,6 +100,7 @@ def load():
         "mmp_adjoint_workspace_size": ([vp, i, i, C.POINTER(C.c_size_t)], i),
         "mmp_adjoint_forward": ([vp, i, i, vp, C.c_size_t, d], i),
         "mmp_adjoint_backward": ([vp, i, d, d, vp, C.c_size_t, d], i),
+        "mmp_batch_info": ([vp, C.POINTER(i), C.POINTER(i)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -232,6 +234,12 @@ def mmp_timing(ctx, reset: bool = False) -> dict:
            "mmp_timing")
     return {"fine_ms": ms.value, "fine_launches": fl.value, "fine_particle_steps": steps.value,
             "other_launches": ol.value}
+
+
+def mmp_batch_info(ctx) -> dict:
+    b, g = C.c_int(), C.c_int()
+    _check(load().mmp_batch_info(ctx, C.byref(b), C.byref(g)), "mmp_batch_info")
+    return {"batched": bool(b.value), "graph": bool(g.value)}
 
 
 def mmp_fine_static(p: workloads.Problem, n: int, u_in_ptr: int, u_out_ptr: int, stats_ptr: int | None,

@@ -114,8 +114,9 @@ ADJOINT_CKPT = 64
 
 
 def config5(n_problems: int = 512, p_max: float = 2e6, **kw) -> list[Problem]:
-    """Batch of seeded problems of the linear / double-well forms:
-    theta ~ U[0.5, 2], kappa ~ U[0, 1], sigma ~ U[0.3, 1],
+    """Batch of seeded problems of the config-1 form (linear, unimodal) and
+    the config-3 form (double well, two regions split at 0, learning
+    variant): theta ~ U[0.5, 2], kappa ~ U[0, 1], sigma ~ U[0.3, 1],
     P log-uniform in [1e4, p_max], N uniform in 16..128, T=8, dt=1e-3."""
     rng = np.random.default_rng(SEED_BASE + 5)
     out = []
@@ -130,6 +131,7 @@ def config5(n_problems: int = 512, p_max: float = 2e6, **kw) -> list[Problem]:
         if i % 2 == 0:
             p = linear(theta, kappa, sigma, m0=1.0, s0=0.1, **common)
         else:
-            p = double_well(0.25, 0.5, kappa, sigma, m0=0.0, s0=0.3, **common)
+            p = double_well(0.25, 0.5, kappa, sigma, m0=0.0, s0=0.3, n_regions=2, threshold=0.0,
+                            variant=LEARNING, **common)
         out.append(p.scaled(**kw) if kw else p)
     return out

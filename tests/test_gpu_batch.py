@@ -88,3 +88,57 @@ def test_batched_exactness_invariant(mmplib):
         for n in range(3):
             assert mom[n, 1] == ser[n, 1] and mom[n, 2] == ser[n, 2], (i, n)
     s.close()
+
+
+def test_batched_graph_equals_direct_enqueue(mmplib):
+    """Sweeps replayed from the captured CUDA graph equal the same sweeps
+    enqueued directly, bit for bit, and both stop where the problems do."""
+    probs = _batch_problems(n=10, seed=5)
+    old = os.environ.get("MMP_BATCH_GRAPH")
+    try:
+        os.environ["MMP_BATCH_GRAPH"] = "0"
+        sd, md, std_, _ = _solve(probs, True)
+    finally:
+        if old is None:
+            del os.environ["MMP_BATCH_GRAPH"]
+        else:
+            os.environ["MMP_BATCH_GRAPH"] = old
+    sg, mg, stg, _ = _solve(probs, True)
+    for i in range(len(probs)):
+        assert stg[i]["sweeps"] == std_[i]["sweeps"]
+        assert np.array_equal(mg[i], md[i]), i
+    sd.close()
+    sg.close()
+
+
+def test_batched_iterate_budget(mmplib):
+    """iterate(k) runs exactly k batched sweeps (a graph launch runs more
+    sweep slots, the device budget stops them), and 2 + 3 sweeps equal 5."""
+    from paper_2310_11365_gb300.mmp import Solver
+
+    probs = [p.scaled(tol=0.0, max_iter=12) for p in _batch_problems(n=6, seed=9)]
+    a = Solver(probs)
+    a.lift()
+    a.iterate(2)
+    assert [a.status(i)["sweeps"] for i in range(len(probs))] == [min(2, p.N) for p in probs]
+    a.iterate(3)
+    b = Solver(probs)
+    b.lift()
+    b.iterate(5)
+    for i, p in enumerate(probs):
+        assert a.status(i)["sweeps"] == b.status(i)["sweeps"] == min(5, p.N)
+        assert np.array_equal(a.moments(i), b.moments(i)), i
+    a.close()
+    b.close()
+
+
+def test_batched_sweeps_replay_a_graph(mmplib):
+    """A batched context captures its sweeps once and replays the graph
+    (the cooperative launch is accepted inside stream capture)."""
+    from paper_2310_11365_gb300.mmp import Solver, mmp_batch_info
+
+    s = Solver(_batch_problems(n=4, seed=13))
+    s.run()
+    info = mmp_batch_info(s.ctx)
+    s.close()
+    assert info["batched"] and info["graph"]
