@@ -196,7 +196,10 @@ def batched_run(n_problems: int, sweeps: int, rank: int, to_tol: bool = False) -
     from paper_2310_11365_gb300 import mmp
     from paper_2310_11365_gb300 import workloads as W
 
+    from paper_2310_11365_gb300 import tune
+
     probs = W.config5(n_problems)
+    tuned = tune.tune_batch(probs)  # measured cap on quads per thread (batched sweeps of a sample)
     s = mmp.Solver(probs)
     mmp.mmp_set_timing(s.ctx, True)
     s.lift()
@@ -213,6 +216,7 @@ def batched_run(n_problems: int, sweeps: int, rank: int, to_tol: bool = False) -
     info = mmp.mmp_batch_info(s.ctx)
     out = {"problems": n_problems, "sweeps_timed": sweeps, "ms": ms, "batched": info["batched"],
            "cuda_graph": info["graph"],
+           "autotuned_cap": tuned,
            "particle_steps": tm["fine_particle_steps"], "value": tm["fine_particle_steps"] / (ms / 1e3),
            "unit": UNIT, "fine_launches_per_sweep": tm["fine_launches"] / max(1, sweeps),
            "sum_P": int(sum(p.P for p in probs)), "max_P": int(max(p.P for p in probs))}
@@ -305,6 +309,11 @@ def main():
     if "N" in overrides:
         overrides["T"] = 8.0 * overrides["N"] / 64  # keep the slice length (n_f = 125)
     p = W.config2(problem_tag=rank, **overrides)
+    # measured launch shapes (mmp_autotune) for the mixed and FP64 config-2
+    # problems, registered before any context is planned
+    from paper_2310_11365_gb300 import tune
+
+    tuned = tune.tune([p, p.scaled(precision="fp64")], probe_steps=32)
     solver = mmp.Solver(p)
     mmp.mmp_set_timing(solver.ctx, True)
     plan = solver.plan()
@@ -406,7 +415,12 @@ def main():
             "config": {"workload": WORKLOAD if not overrides else f"{WORKLOAD} with overrides {overrides}",
                        "parallelism": f"replicas x{world}",
                        "precision": "mixed", "l2": "inputs larger than L2 (2 x 256 MB particle buffers)",
-                       "plan": plan},
+                       "plan": plan,
+                       "autotune": {k: {"quads_per_thread": v["nq"],
+                                        "best_rate": max(v["rates"].values()),
+                                        "rate_at": {q: v["rates"][q] for q in ("8", "13", "17", "26", "32")
+                                                    if q in v["rates"]}}
+                                    for k, v in tuned.items()}},
             "time_to_tol_s": ms / 1e3 / args.steps, "sweeps_to_tol": sweeps[-1],
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": traffic,

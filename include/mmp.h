@@ -218,6 +218,44 @@ int mmp_timing(mmp_ctx* ctx, int reset, double* fine_ms, long long* fine_launche
  * capture, in which case the same work is enqueued directly). */
 int mmp_batch_info(mmp_ctx* ctx, int* batched, int* graph);
 
+/* Measured launch shapes.  The planner chooses the fine kernel's quads
+ * per thread (4 particles each; this fixes the CTAs per slice G =
+ * ceil(ceil(P/4) / (256 nq)) and the slices resident at once) from a cost
+ * model; mmp_autotune measures instead.  For each candidate count
+ * (`candidates`, n_candidates entries; NULL: every count 1..32 for mixed,
+ * 1..16 for FP64) it times, with CUDA events after one warm-up launch, a
+ * fine launch of *desc's model and P with probe_steps Euler-Maruyama steps
+ * per slice (0: min(n_f, 64)) from the problem's seeded initial ensemble,
+ * over max(N, two full waves of resident slices) slices, i.e. the
+ * throughput with the GPU full, on `stream` (synchronising).  best_nq receives the fastest candidate;
+ * rates (may be NULL; n_candidates entries, or 32 / 16 for NULL
+ * candidates) the particle-steps per second of each (0 for a candidate that
+ * does not fit).  `workspace` (device, mmp_autotune_workspace_size bytes,
+ * caller-owned) holds the ensemble and the exchange scratch.  Errors:
+ * MMP_ERR_INVALID_ARG, MMP_ERR_WORKSPACE, MMP_ERR_UNSUPPORTED (no
+ * candidate fits), MMP_ERR_TIMEOUT, MMP_ERR_CUDA.
+ *
+ * mmp_set_tuning adds a process-wide entry: problems of `precision` with
+ * p_lo <= P <= p_hi are planned with the largest reachable count of at most
+ * quads_per_thread (later entries win; MMP_FINE_NQ still overrides).
+ * quads_per_thread = 0 removes every entry of that precision.  Contexts
+ * created afterwards use the table for single problems whose N slices fill
+ * the resident CTAs at that count (otherwise the cost model, which favours
+ * more CTAs per slice, decides).
+ *
+ * mmp_set_batch_nq sets the cap on quads per thread of batched contexts of
+ * `precision` created afterwards (each problem takes the most quads per
+ * thread up to the cap; 0 restores the default 26 mixed / 13 FP64;
+ * MMP_BATCH_NQ still overrides).  The batched kernel sizes its shared
+ * memory for the largest count in the batch, so the cap also fixes its
+ * occupancy; the Python helper tune.tune_batch measures it on a sample of
+ * the batch.  The paper has no counterpart (a property of this library). */
+int mmp_autotune_workspace_size(const mmp_problem_desc* desc, size_t* bytes);
+int mmp_autotune(const mmp_problem_desc* desc, const int* candidates, int n_candidates, int probe_steps,
+                 void* workspace, size_t bytes, void* stream, int* best_nq, double* rates);
+int mmp_set_tuning(int precision, long long p_lo, long long p_hi, int quads_per_thread);
+int mmp_set_batch_nq(int precision, int quads_per_thread);
+
 /* One fine propagation F_n of an explicit ensemble (no matching):
  * reads P values at u_in (device), writes F_n(u_in) to u_out (device,
  * may not alias u_in) and its restriction record to stats_out (host,

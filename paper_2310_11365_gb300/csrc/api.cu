@@ -165,6 +165,23 @@ void derive(Prob& p) {
   p.out_buf.assign(d.N, -1);
 }
 
+// Measured launch shapes (mmp_set_tuning, usually filled by mmp_autotune):
+// quads per thread for a precision and a range of P.  Later entries win.
+struct TuneEntry {
+  int precision;
+  long long p_lo, p_hi;
+  int nq;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+
+int tuned_nq(int precision, long long P) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (auto it = g_tune.rbegin(); it != g_tune.rend(); ++it)
+    if (it->precision == precision && it->p_lo <= P && P <= it->p_hi) return it->nq;
+  return 0;
+}
+
 // Launch plan of the fine kernel: particle layout (registers or shared
 // memory), quads per thread (nq) and CTAs per slice (G).  The group size is
 // fixed per problem so that every launch reduces in the same order (the
@@ -173,9 +190,11 @@ void derive(Prob& p) {
 // time: waves of concurrent slices times the per-step time, with the per-SM
 // load in quad-steps and a fixed per-step latency for the group barrier.
 // The layout is the shared-memory one unless MMP_FINE_LAYOUT=regs;
-// MMP_FINE_NQ=<k> restricts the choice to k quads per thread (launch-shape
-// sweeps).
+// MMP_FINE_NQ=<k>, else a tuning entry (mmp_set_tuning) for the problem's
+// precision and P, selects the largest reachable count of at most k quads
+// per thread.
 int plan(Prob& p, const Device& dev, int batch_nq = 0) {
+  int tuned = batch_nq > 0 ? 0 : tuned_nq(p.d.precision, p.d.P);
   if (batch_nq > 0) {
     // many problems share one launch: the most particles per thread (the
     // fewest CTAs, hence group barriers, per slice) within the cap
@@ -198,7 +217,22 @@ int plan(Prob& p, const Device& dev, int batch_nq = 0) {
   const char* env = std::getenv("MMP_FINE_LAYOUT");
   const int layout = (env != nullptr && std::strcmp(env, "regs") == 0) ? kLayoutRegs : kLayoutSmem;
   const char* env_nq = std::getenv("MMP_FINE_NQ");
-  const int force_nq = env_nq != nullptr ? std::atoi(env_nq) : 0;
+  const int max_nq_l = layout == kLayoutSmem ? (p.esz == 4 ? 32 : 16) : (p.esz == 4 ? 8 : 4);
+  if (tuned > 0 && (layout != kLayoutSmem || tuned > max_nq_l)) tuned = 0;
+  if (tuned > 0) {
+    // a measured shape is a saturated-throughput optimum: use it only if the
+    // problem's slices fill the resident CTAs at that shape
+    const void* fn = fine_kernel(p.d.precision, layout, tuned, p.mult);
+    size_t limit = 0;
+    int occ = 0;
+    const size_t smem = fine_smem_bytes(p.d.precision, layout, tuned);
+    const int rc = allow_dynamic_smem(fn, dev.dev, &limit);
+    if (rc) return rc;
+    if (smem <= limit) MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, smem));
+    const long long G = ((long long)p.Q + (long long)tuned * kTPB - 1) / ((long long)tuned * kTPB);
+    if (occ < 1 || (long long)p.d.N * G < (long long)occ * dev.sms) tuned = 0;
+  }
+  const int force_nq = env_nq != nullptr ? std::atoi(env_nq) : tuned;
   const int max_nq = layout == kLayoutSmem ? (p.esz == 4 ? 32 : 16) : (p.esz == 4 ? 8 : 4);
   int occ_of[33] = {0};
   for (int nq = 1; nq <= max_nq; ++nq) {
@@ -224,7 +258,7 @@ int plan(Prob& p, const Device& dev, int batch_nq = 0) {
     const long long qpc = (p.Q + G - 1) / G;
     const int nq = (int)std::max<long long>(1, (qpc + kTPB - 1) / kTPB);
     if (nq > max_nq || occ_of[nq] < 1) continue;
-    if (force_nq > 0 && nq != force_nq) continue;
+    if (force_nq > 0 && nq > force_nq) continue;
     const int S = dev.sms * occ_of[nq];
     if (G > S) continue;
     const int slots = std::min(N, S / G);
@@ -232,7 +266,11 @@ int plan(Prob& p, const Device& dev, int batch_nq = 0) {
     const int per_sm = (slots * G + dev.sms - 1) / dev.sms;
     const double step = per_sm * (double)kTPB * nq / quad_rate + (G > 1 ? 2500.0 : 400.0);
     const double cost = waves * step;
-    if (cost < best * (1 - 1e-12)) {
+    // forced (MMP_FINE_NQ or a tuning entry): the largest reachable count
+    // not above the forced one, else the cheapest by the cost model
+    const bool better = force_nq > 0 ? (nq > best_nq || (nq == best_nq && cost < best * (1 - 1e-12)))
+                                     : cost < best * (1 - 1e-12);
+    if (better) {
       best = cost;
       best_nq = nq;
       best_G = G;
@@ -356,9 +394,16 @@ namespace {
 
 // Quads per thread of every problem when several problems are batched:
 // MMP_BATCH_NQ overrides (launch-shape sweeps).
+int g_batch_nq[2] = {0, 0};  // mmp_set_batch_nq, by precision (0: default)
+
 int batch_nq_cap(int precision) {
   const char* e = std::getenv("MMP_BATCH_NQ");
   if (e != nullptr && std::atoi(e) > 0) return std::atoi(e);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const int set = g_batch_nq[precision == MMP_MIXED ? 1 : 0];
+    if (set > 0) return set;
+  }
   return precision == MMP_MIXED ? 26 : 13;
 }
 
@@ -382,7 +427,7 @@ int prepare(const mmp_problem_desc* descs, int n, std::vector<Prob>& probs, Devi
 }
 
 // The problem-constant part of the fine kernel's arguments.
-FineArgs make_fine_args(mmp_ctx* c, const Prob& p) {
+FineArgs fine_args_of(const Prob& p, unsigned long long limit_ns) {
   FineArgs a;
   const mmp_problem_desc& d = p.d;
   a.nc3 = -d.c3; a.c1 = d.c1; a.kappa = d.kappa; a.c0 = d.c0;
@@ -398,9 +443,11 @@ FineArgs make_fine_args(mmp_ctx* c, const Prob& p) {
   a.G = p.G;
   a.nq = p.nq;
   a.partials = p.partials; a.flags = p.flags; a.tags = p.tags; a.status = p.status;
-  a.wait_limit_ns = c->limit_ns;
+  a.wait_limit_ns = limit_ns;
   return a;
 }
+
+FineArgs make_fine_args(mmp_ctx* c, const Prob& p) { return fine_args_of(p, c->limit_ns); }
 
 DriverArgs make_driver_args(const Prob& p, int sweep) {
   DriverArgs a;
@@ -1375,5 +1422,191 @@ extern "C" int mmp_fine_static(const mmp_problem_desc* desc, int n, const void* 
     k_status_to_stats<<<1, 1, 0, s>>>(status, stats_dev);
     MMP_CUDA(cudaGetLastError());
   }
+  return MMP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Measured launch shapes (mmp_autotune, mmp_set_tuning).
+//
+// The planner's cost model ranks launch shapes by modelled time.  The
+// autotuner measures instead: for each candidate count of quads per thread
+// (shared-memory layout; it fixes the CTAs per slice G = ceil(Q / (256 nq))
+// and the slices resident at once), one fine launch over all N slices of the
+// problem, n_probe steps each, from the problem's own initial ensemble,
+// timed with CUDA events after a warm-up launch.  Rates are particle-steps
+// per second of that launch; the fastest candidate is returned, and
+// mmp_set_tuning makes the planner use it for a range of P.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct TuneLayout {
+  size_t bytes = 0;
+  int seats = 0;
+  char* u0 = nullptr;
+  double* stats = nullptr;
+  double* partials = nullptr;
+  unsigned long long* tags = nullptr;  // followed by flags
+  unsigned* flags = nullptr;
+  unsigned* status = nullptr;
+};
+
+size_t tune_layout(const Prob& p, const Device& dev, char* base, TuneLayout& L) {
+  Carver c{base, 0};
+  auto ptr = [&](size_t b) -> char* {
+    const size_t at = c.take(b);
+    return base ? base + at : nullptr;
+  };
+  L.seats = 8 * dev.sms;  // at most 8 resident CTAs of 256 threads per SM
+  L.u0 = ptr((size_t)p.pitch * p.esz);
+  L.stats = (double*)ptr(sizeof(double) * kStat * (size_t)std::max(p.d.N, 2 * L.seats));
+  L.partials = (double*)ptr(sizeof(double) * kSeatDoubles * (size_t)L.seats);
+  L.tags = (unsigned long long*)ptr((sizeof(unsigned long long) * kSlots + sizeof(unsigned)) * (size_t)L.seats);
+  L.flags = base ? (unsigned*)(L.tags + (size_t)kSlots * L.seats) : nullptr;
+  L.status = (unsigned*)ptr(sizeof(unsigned) * 4);
+  L.bytes = (c.off + kAlign - 1) / kAlign * kAlign;
+  return L.bytes;
+}
+
+}  // namespace
+
+extern "C" int mmp_autotune_workspace_size(const mmp_problem_desc* desc, size_t* bytes) {
+  if (desc == nullptr || bytes == nullptr) return MMP_ERR_INVALID_ARG;
+  int rc = validate(*desc);
+  if (rc) return rc;
+  Prob p;
+  p.d = *desc;
+  derive(p);
+  Device dev;
+  rc = query_device(dev);
+  if (rc) return rc;
+  TuneLayout L;
+  *bytes = tune_layout(p, dev, nullptr, L);
+  return MMP_OK;
+}
+
+extern "C" int mmp_autotune(const mmp_problem_desc* desc, const int* candidates, int n_candidates, int probe_steps,
+                            void* workspace, size_t bytes, void* stream, int* best_nq, double* rates) {
+  if (desc == nullptr || workspace == nullptr || best_nq == nullptr) return MMP_ERR_INVALID_ARG;
+  if (candidates != nullptr && n_candidates < 1) return MMP_ERR_INVALID_ARG;
+  int rc = validate(*desc);
+  if (rc) return rc;
+  Prob p;
+  p.d = *desc;
+  derive(p);
+  Device dev;
+  rc = query_device(dev);
+  if (rc) return rc;
+  TuneLayout L;
+  if (tune_layout(p, dev, (char*)workspace, L) > bytes) return MMP_ERR_WORKSPACE;
+  const int max_nq = p.esz == 4 ? 32 : 16;
+  std::vector<int> cand;
+  if (candidates != nullptr) {
+    cand.assign(candidates, candidates + n_candidates);
+  } else {
+    for (int k = 1; k <= max_nq; ++k) cand.push_back(k);
+  }
+  const int nf = probe_steps > 0 ? std::min(probe_steps, p.nf) : std::min(p.nf, 64);
+  cudaStream_t s = (cudaStream_t)stream;
+  MMP_CUDA(cudaMemsetAsync(L.status, 0, sizeof(unsigned) * 4, s));
+  MMP_CUDA(launch_init_u0(p.d.precision, L.u0, p.d.P, p.Q, p.d.m0, p.d.s0, p.key0, p.key1, p.d.problem_tag, s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  MMP_CUDA(cudaEventCreate(&e0));
+  MMP_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  double best_rate = -1.0;
+  int err = MMP_OK;
+  for (size_t ci = 0; ci < cand.size() && err == MMP_OK; ++ci) {
+    double rate = 0.0;
+    const int nq = cand[ci];
+    const void* fn = nq >= 1 && nq <= max_nq ? fine_kernel(p.d.precision, kLayoutSmem, nq, p.mult) : nullptr;
+    size_t limit = 0;
+    const size_t smem = fine_smem_bytes(p.d.precision, kLayoutSmem, nq);
+    if (fn != nullptr && (err = allow_dynamic_smem(fn, dev.dev, &limit)) == MMP_OK && smem <= limit) {
+      int occ = 0;
+      cudaError_t ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, smem);
+      if (ce != cudaSuccess) {
+        err = cuda_fail(ce, "occupancy", __LINE__);
+        break;
+      }
+      const long long G = ((long long)p.Q + (long long)nq * kTPB - 1) / ((long long)nq * kTPB);
+      if (occ >= 1 && G <= (long long)occ * dev.sms && G <= L.seats) {
+        Prob t = p;
+        t.layout = kLayoutSmem;
+        t.nq = nq;
+        t.G = (int)G;
+        t.slots_max = (int)(std::min<long long>((long long)occ * dev.sms, L.seats) / G);
+        t.u0 = L.u0;
+        t.stats = L.stats;
+        t.partials = L.partials;
+        t.tags = L.tags;
+        t.flags = L.flags;
+        t.status = L.status;
+        FineArgs a = fine_args_of(t, wait_limit_ns());
+        // saturated: at least two full waves of resident slices (slice
+        // indices past N only select other draws)
+        const int n_tasks = std::max(p.d.N, 2 * t.slots_max);
+        a.nf = nf;
+        a.slice_begin = 0;
+        a.n_tasks = n_tasks;
+        a.aff = nullptr;
+        const size_t sync = (sizeof(unsigned long long) * kSlots + sizeof(unsigned)) * (size_t)L.seats;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && err == MMP_OK; ++rep) {  // warm-up, then timed
+          ce = cudaMemsetAsync(L.tags, 0, sync, s);
+          if (ce == cudaSuccess && rep == 1) ce = cudaEventRecord(e0, s);
+          if (ce == cudaSuccess) ce = launch_fine(p.d.precision, kLayoutSmem, nq, p.mult, t.slots_max * t.G, a, s);
+          if (ce == cudaSuccess && rep == 1) ce = cudaEventRecord(e1, s);
+          if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+          if (ce != cudaSuccess) err = cuda_fail(ce, "autotune launch", __LINE__);
+        }
+        if (err == MMP_OK) {
+          cudaError_t ce2 = cudaEventElapsedTime(&ms, e0, e1);
+          unsigned stw = 0;
+          if (ce2 == cudaSuccess) ce2 = cudaMemcpy(&stw, L.status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+          if (ce2 != cudaSuccess) {
+            err = cuda_fail(ce2, "autotune timing", __LINE__);
+          } else if (stw & kStatusTimeout) {
+            err = MMP_ERR_TIMEOUT;
+          } else if (ms > 0.0f) {
+            rate = (double)n_tasks * (double)p.d.P * (double)nf / (ms * 1e-3);
+          }
+        }
+      }
+    }
+    if (rates != nullptr) rates[ci] = rate;
+    if (rate > best_rate) {
+      best_rate = rate;
+      best = nq;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err) return err;
+  if (best_rate <= 0.0) return MMP_ERR_UNSUPPORTED;
+  *best_nq = best;
+  return MMP_OK;
+}
+
+extern "C" int mmp_set_tuning(int precision, long long p_lo, long long p_hi, int quads_per_thread) {
+  if (precision != MMP_FP64 && precision != MMP_MIXED) return MMP_ERR_INVALID_ARG;
+  if (quads_per_thread < 0 || quads_per_thread > (precision == MMP_MIXED ? 32 : 16)) return MMP_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (quads_per_thread == 0) {
+    g_tune.erase(std::remove_if(g_tune.begin(), g_tune.end(),
+                                [&](const TuneEntry& e) { return e.precision == precision; }),
+                 g_tune.end());
+    return MMP_OK;
+  }
+  if (p_lo < 1 || p_hi < p_lo) return MMP_ERR_INVALID_ARG;
+  g_tune.push_back({precision, p_lo, p_hi, quads_per_thread});
+  return MMP_OK;
+}
+
+extern "C" int mmp_set_batch_nq(int precision, int quads_per_thread) {
+  if (precision != MMP_FP64 && precision != MMP_MIXED) return MMP_ERR_INVALID_ARG;
+  if (quads_per_thread < 0 || quads_per_thread > (precision == MMP_MIXED ? 32 : 16)) return MMP_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_batch_nq[precision == MMP_MIXED ? 1 : 0] = quads_per_thread;
   return MMP_OK;
 }

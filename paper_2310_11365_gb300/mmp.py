@@ -34,7 +34,7 @@ EXPORTED = [
     "mmp_get_moments", "mmp_get_particles", "mmp_fine_serial", "mmp_fine", "mmp_philox",
     "mmp_normals", "mmp_get_plan", "mmp_set_timing", "mmp_timing", "mmp_fine_static",
     "mmp_set_params", "mmp_adjoint_workspace_size", "mmp_adjoint_forward", "mmp_adjoint_backward",
-    "mmp_batch_info",
+    "mmp_batch_info", "mmp_autotune_workspace_size", "mmp_autotune", "mmp_set_tuning", "mmp_set_batch_nq",
 ]
 
 
@@ -101,6 +101,10 @@ def load():
         "mmp_adjoint_forward": ([vp, i, i, vp, C.c_size_t, d], i),
         "mmp_adjoint_backward": ([vp, i, d, d, vp, C.c_size_t, d], i),
         "mmp_batch_info": ([vp, C.POINTER(i), C.POINTER(i)], i),
+        "mmp_autotune_workspace_size": ([pd, C.POINTER(C.c_size_t)], i),
+        "mmp_autotune": ([pd, C.POINTER(i), i, i, vp, C.c_size_t, vp, C.POINTER(i), d], i),
+        "mmp_set_tuning": ([i, ll, ll, i], i),
+        "mmp_set_batch_nq": ([i, i], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -240,6 +244,37 @@ def mmp_batch_info(ctx) -> dict:
     b, g = C.c_int(), C.c_int()
     _check(load().mmp_batch_info(ctx, C.byref(b), C.byref(g)), "mmp_batch_info")
     return {"batched": bool(b.value), "graph": bool(g.value)}
+
+
+def mmp_autotune(p: workloads.Problem, candidates=None, probe_steps: int = 0, stream=None) -> dict:
+    """Time one fine launch per candidate quads-per-thread count (see the
+    C header); returns the fastest count and the rate of each candidate."""
+    import torch
+
+    dsc = desc(p)
+    nb = C.c_size_t()
+    _check(load().mmp_autotune_workspace_size(C.byref(dsc), C.byref(nb)), "mmp_autotune_workspace_size")
+    ws = torch.empty(max(1, nb.value), dtype=torch.uint8, device="cuda")
+    prec = dsc.precision
+    cands = list(candidates) if candidates is not None else list(range(1, (32 if prec == MMP_MIXED else 16) + 1))
+    carr = (C.c_int * len(cands))(*cands)
+    rates = np.zeros(len(cands))
+    best = C.c_int()
+    _check(load().mmp_autotune(C.byref(dsc), carr, len(cands), int(probe_steps), C.c_void_p(ws.data_ptr()),
+                               nb.value, C.c_void_p(_stream_handle(stream)), C.byref(best),
+                               rates.ctypes.data_as(C.POINTER(C.c_double))), "mmp_autotune")
+    del ws
+    return {"best_nq": best.value, "rates": dict(zip(cands, rates.tolist()))}
+
+
+def mmp_set_tuning(precision: str, p_lo: int, p_hi: int, quads_per_thread: int) -> None:
+    prec = MMP_MIXED if precision == "mixed" else MMP_FP64
+    _check(load().mmp_set_tuning(prec, int(p_lo), int(p_hi), int(quads_per_thread)), "mmp_set_tuning")
+
+
+def mmp_set_batch_nq(precision: str, quads_per_thread: int) -> None:
+    prec = MMP_MIXED if precision == "mixed" else MMP_FP64
+    _check(load().mmp_set_batch_nq(prec, int(quads_per_thread)), "mmp_set_batch_nq")
 
 
 def mmp_fine_static(p: workloads.Problem, n: int, u_in_ptr: int, u_out_ptr: int, stats_ptr: int | None,
