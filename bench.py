@@ -237,6 +237,81 @@ def batched_run(n_problems: int, sweeps: int, rank: int, to_tol: bool = False) -
     return out
 
 
+def config3_run() -> dict:
+    """Config 3 at full size (double well, two regions split at 0, learning
+    variant, P = 4e6, N = 128, n_f = 313): one Parareal solve from lifting to
+    tolerance, device time with CUDA events."""
+    import torch
+
+    from paper_2310_11365_gb300 import mmp, tune
+    from paper_2310_11365_gb300 import workloads as W
+
+    p = W.config3()
+    tuned = tune.tune(p, probe_steps=32)
+    s = mmp.Solver(p)
+    mmp.mmp_set_timing(s.ctx, True)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    k = s.run()
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    tm = mmp.mmp_timing(s.ctx, reset=True)
+    st = s.status(0)
+    out = {"workload": "config3: double well V=x^4/4-x^2/2, kappa=0.1, sigma=0.7, X0~N(0,0.3^2), two regions "
+                       "(x<0, x>=0), learning variant, T=20, N=128, dt=5e-4 (n_f=313), P=4e6, tol 1e-6",
+           "time_to_tol_s": ms / 1e3, "sweeps": k, "converged": st["converged"],
+           "particle_steps": tm["fine_particle_steps"], "value": tm["fine_particle_steps"] / (ms / 1e3),
+           "unit": UNIT, "plan": s.plan(0), "autotune": {kk: v["nq"] for kk, v in tuned.items()}}
+    s.close()
+    return out
+
+
+def config4_run() -> dict:
+    """Config 4 at full size (the adjoint): the double-well model, P = 1e6,
+    N = 64, T = 20, n_f = 313 (20032 steps), checkpoints every 64 steps; the
+    recording forward and the reverse sweep timed separately (device time),
+    loss L = sum_n (M_n - m*_n)^2 + (V_n - v*_n)^2 with targets from a run at
+    the target parameters on the same draws."""
+    import numpy as np
+    import torch
+
+    from paper_2310_11365_gb300 import mmp
+    from paper_2310_11365_gb300 import workloads as W
+
+    p = W.config4()
+    s = mmp.Solver(p)
+    adj = mmp.Adjoint(s, 0, W.ADJOINT_CKPT)
+
+    def theta(kappa, sigma, a, b):
+        return np.array([4.0 * a, 2.0 * b - kappa, kappa, 0.0, sigma])
+
+    tgt = adj.forward(theta(*W.ADJOINT_TARGET_PARAMS))  # also warms up
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    mom = adj.forward(theta(*W.ADJOINT_EVAL_PARAMS))
+    ev[1].record()
+    gm = 2.0 * (mom[1:, 0] - tgt[1:, 0])
+    gv = 2.0 * (mom[1:, 1] - tgt[1:, 1])
+    ev[2].record()
+    grad = adj.backward(gm, gv)
+    ev[3].record()
+    torch.cuda.synchronize()
+    f_ms, b_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    J = p.N * math.ceil(p.T / p.N / p.dt - 1e-9)
+    out = {"workload": "config4: adjoint of the serial fine run, double well (kappa, sigma, a, b) = "
+                       "(0.1, 0.7, 0.25, 0.5), targets at (0.15, 0.65, 0.25, 0.5), P=1e6, N=64, T=20, "
+                       "dt=1e-3 (n_f=313), checkpoint every 64 steps",
+           "steps": J, "P": p.P, "forward_ms": f_ms, "backward_ms": b_ms,
+           "forward_particle_steps_per_s": J * p.P / (f_ms / 1e3),
+           "backward_particle_steps_per_s": J * p.P / (b_ms / 1e3),
+           "loss": float(np.sum(gm ** 2 + gv ** 2) / 4.0),
+           "grad_c3_c1_kappa_c0_B0": [float(x) for x in grad]}
+    s.close()
+    return out
+
+
 def reference_arm(args, world, rank):
     """The oracle timed as it stands on the host cores: one step = one
     Parareal iteration (fine propagator on all 64 slices + coarse/iterator
@@ -286,6 +361,8 @@ def main():
     ap.add_argument("--batch-tol", action="store_true",
                     help="also time the batched workload from lifting to tolerance")
     ap.add_argument("--batch-sweeps", type=int, default=2, help="fine sweeps timed for the batched workload")
+    ap.add_argument("--no-cfg3", action="store_true", help="skip the config-3 (learning variant) solve")
+    ap.add_argument("--no-cfg4", action="store_true", help="skip the config-4 adjoint timing")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -401,6 +478,8 @@ def main():
     batch = None
     if args.batch > 0:
         batch = batched_run(args.batch, args.batch_sweeps, rank, args.batch_tol)
+    cfg3 = None if args.no_cfg3 or overrides else config3_run()
+    cfg4 = None if args.no_cfg4 or overrides else config4_run()
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -432,6 +511,8 @@ def main():
             "e2e": e2e,
             "fp64_plain": fp64,
             "batched_config5": batch,
+            "config3": cfg3,
+            "config4_adjoint": cfg4,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": tm["fine_launches"] + tm["other_launches"],

@@ -17,9 +17,10 @@
 // the common shift d_j = h (kappa m_j + c0) and the noise amplitude).  Per segment,
 // in reverse: each thread recomputes its own particles over the c steps from
 // the checkpoint (no reduction is needed: the means are recorded), storing
-// states and draws, then sweeps backward with one group sum of lambda per
-// step.  The replay evaluates the step exactly as the forward kernel did,
-// so it reproduces the forward states bit for bit.
+// states and draws, then sweeps backward with one group sum per step, in
+// the shift form that lets that sum run one step behind the sweep (below).
+// The replay evaluates the step exactly as the forward kernel did, so it
+// reproduces the forward states.
 #include <cmath>
 
 #include "adjoint.cuh"
@@ -28,7 +29,7 @@
 namespace mmp {
 
 template <typename R>
-__global__ void __launch_bounds__(kTPB, 4) k_adjoint(const AdjointArgs a) {
+__global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
   __shared__ GroupShared sh;
   const int G = a.G;
   const int g = blockIdx.x;
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(kTPB, 4) k_adjoint(const AdjointArgs a) {
 
   Acc<R> acc3, acc1, accb;         // -h x^3, h x, sqrt(h) xi terms
   double acc_k = 0.0, acc_c0 = 0.0;  // h m_j S_j, h S_j (thread 0 of CTA 0)
+  R s_next = (R)0;                   // pending shift s_{j+1} of lambda_{j+1}
 
   auto zero_tail = [&](int q, R v[4]) {
     if (q == qlast) {
@@ -131,98 +133,95 @@ __global__ void __launch_bounds__(kTPB, 4) k_adjoint(const AdjointArgs a) {
       Quad<R>::store(segx + (size_t)L * a.pitch + 4 * (size_t)q, x);
     }
     // ---- backward through the segment ----------------------------------
-    R S_part = (R)0, p3 = (R)0, p1 = (R)0, pb = (R)0;
-    for (int i = 0; i < nq; ++i) {
-      const int q = qb + tid + i * kTPB;
-      R l[4], x[4], z[4];
-      lam.get(i, l);
-      // the last slice end enters here; every earlier slice end j1 < J was
-      // injected when the later segment's sweep reached its first step
-      if (j1 == a.J) {
+    // Shift form of the reverse recursion: lambda_j = mu_j + s_j with
+    //   mu_j = lambda_{j+1} (1 + h a_x(x_j)) [+ slice-end injection at x_j],
+    //   s_j  = (h kappa / P) S_j,  S_j = sum lambda_{j+1} = sum mu_{j+1} + P s_{j+1},
+    // so the group sum of mu_j published at the end of reverse step j is
+    // first needed at the end of step j - 1 (the exchange is one step
+    // behind, as in the forward).  `lam` holds mu, `s_next` the pending shift.
+    if (j1 == a.J) {
+      // lambda_J: the last slice end's injection alone (s_J = 0); its sum is epoch 0
+      R part = (R)0;
+      for (int i = 0; i < nq; ++i) {
+        const int q = qb + tid + i * kTPB;
+        R x[4], l[4] = {0, 0, 0, 0};
         Quad<R>::load(segx + (size_t)L * a.pitch + 4 * (size_t)q, x);
-        inject(j1, q, x, l);
+        inject(a.J, q, x, l);
         lam.put(i, l);
+        part = addR(part, addR(addR(l[0], l[1]), addR(l[2], l[3])));
       }
-      Quad<R>::load(segx + (size_t)(L - 1) * a.pitch + 4 * (size_t)q, x);
-      Quad<R>::load(segz + (size_t)(L - 1) * a.pitch + 4 * (size_t)q, z);
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        p3 -= l[w] * x[w] * x[w] * x[w];
-        p1 += l[w] * x[w];
-        pb += l[w] * z[w];
-        S_part += l[w];
+      step_sum_warp<R>(sh, 1, part);
+      __syncthreads();
+      if (warp == 0) {
+        const typename StepSum<R>::T cta = step_sum_cta<R>(sh, 1);
+        if (lane == 0) StepSum<R>::publish(grp, 0u, cta);
       }
+      grp.epoch = 1u;
     }
     for (int jj = L - 1; jj >= 0; --jj) {
       const long long j = j0 + jj;
+      const unsigned ej = (unsigned)(a.J - j);  // epoch of sum mu_j
+      const bool end_j = j > 0 && j % a.nf == 0;
+      R part = (R)0, p3 = (R)0, p1 = (R)0, pb = (R)0;
+      for (int i = 0; i < nq; ++i) {
+        const int q = qb + tid + i * kTPB;
+        R l[4], x[4], z[4];
+        lam.get(i, l);
+        Quad<R>::load(segx + (size_t)jj * a.pitch + 4 * (size_t)q, x);
+        Quad<R>::load(segz + (size_t)jj * a.pitch + 4 * (size_t)q, z);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) l[w] = addR(l[w], s_next);  // lambda_{j+1}
+        zero_tail(q, l);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          // step j's parameter partials, then mu_j
+          p3 -= l[w] * x[w] * x[w] * x[w];
+          p1 += l[w] * x[w];
+          pb += l[w] * z[w];
+          const R ax = fmaR((R)3 * nc3, x[w] * x[w], c1);  // -3 c3 x^2 + c1
+          l[w] = mulR(l[w], fmaR(h, ax, (R)1));
+        }
+        if (end_j) inject(j, q, x, l);
+        zero_tail(q, l);
+        lam.put(i, l);
+        part = addR(part, addR(addR(l[0], l[1]), addR(l[2], l[3])));
+      }
       acc3.add(h * p3);
       acc1.add(h * p1);
       accb.add(sqh * pb);
-      // S_j = sum_p lambda_{j+1,p} over the whole ensemble (warp 0 does the
-      // cross-CTA exchange; the other warps wait at the second barrier)
-      step_sum_warp<R>(sh, jj & 1, S_part);
-      __syncthreads();
-      {
-        const unsigned e = grp.epoch++;
-        if (warp == 0) {
-          typename StepSum<R>::T sum = step_sum_cta<R>(sh, jj & 1);
-          if (G > 1 && lane == 0) StepSum<R>::publish(grp, e, sum);
-          const bool ok = G == 1 || StepSum<R>::fetch(grp, e, sum);
-          if (lane == 0) {
-            StepSum<R>::gsum(sh, jj & 1) = sum;
-            if (!ok) sh.abort = 1;
-          }
+      // warp 0 reads sum mu_{j+1} (epoch ej - 1, published a step ago) before
+      // the barrier and publishes sum mu_j (epoch ej) after it
+      step_sum_warp<R>(sh, jj & 1, part);
+      if (warp == 0) {
+        typename StepSum<R>::T sum;
+        const bool ok = StepSum<R>::fetch(grp, ej - 1u, sum);
+        if (lane == 0) {
+          StepSum<R>::gsum(sh, jj & 1) = sum;
+          if (!ok) sh.abort = 1;
         }
       }
       __syncthreads();
       if (sh.abort) return;
-      const typename StepSum<R>::T Ssum = StepSum<R>::gsum(sh, jj & 1);
+      const typename StepSum<R>::T sm = StepSum<R>::gsum(sh, jj & 1);
       double S_d;
       R S;
       if constexpr (sizeof(R) == 4) {
-        S = Ssum.x + Ssum.y;
-        S_d = (double)Ssum.x + (double)Ssum.y;
+        S = addR(addR(sm.x, sm.y), mulR((R)a.P, s_next));
+        S_d = (double)sm.x + (double)sm.y + (double)a.P * (double)s_next;
       } else {
-        S = (R)Ssum;
-        S_d = Ssum;
+        S = addR(sm, mulR((R)a.P, s_next));
+        S_d = S;
       }
       if (g == 0 && tid == 0) {
         acc_k += a.h * (double)uni[3 * j] * S_d;
         acc_c0 += a.h * S_d;
       }
-      // lambda_j, then the partials of step j - 1
-      S_part = (R)0;
-      p3 = (R)0;
-      p1 = (R)0;
-      pb = (R)0;
-      const R shift = kh_p * S;
-      const bool end_j = j > 0 && j % a.nf == 0;
-      for (int i = 0; i < nq; ++i) {
-        const int q = qb + tid + i * kTPB;
-        R l[4], x[4];
-        lam.get(i, l);
-        Quad<R>::load(segx + (size_t)jj * a.pitch + 4 * (size_t)q, x);
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const R ax = fmaR((R)3 * nc3, x[w] * x[w], c1);  // -3 c3 x^2 + c1
-          l[w] = fmaR(l[w], fmaR(h, ax, (R)1), shift);
-        }
-        zero_tail(q, l);
-        if (end_j) inject(j, q, x, l);
-        lam.put(i, l);
-        if (jj > 0) {
-          R xp[4], zp[4];
-          Quad<R>::load(segx + (size_t)(jj - 1) * a.pitch + 4 * (size_t)q, xp);
-          Quad<R>::load(segz + (size_t)(jj - 1) * a.pitch + 4 * (size_t)q, zp);
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            p3 -= l[w] * xp[w] * xp[w] * xp[w];
-            p1 += l[w] * xp[w];
-            pb += l[w] * zp[w];
-            S_part += l[w];
-          }
-        }
+      s_next = mulR(kh_p, S);  // s_j, pending on lambda_j
+      if (warp == 0) {
+        const typename StepSum<R>::T cta = step_sum_cta<R>(sh, jj & 1);
+        if (lane == 0) StepSum<R>::publish(grp, ej, cta);
       }
+      grp.epoch = ej + 1u;
     }
   }
   // ---- reduce the parameter partials over the group (FP64) -------------

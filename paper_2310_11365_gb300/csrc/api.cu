@@ -746,6 +746,9 @@ int status_to_error(unsigned s) {
 struct AdjLayout {
   size_t bytes = 0;
   int n_seg = 0, G = 1, nq = 1;
+  int fG = 1, fnq = 1;  // the recording forward: one slice over the whole GPU
+  double* fpartials = nullptr;
+  unsigned long long* ftags = nullptr;  // followed by flags
   void *ckpt = nullptr, *uni = nullptr, *segx = nullptr, *segz = nullptr;
   double *gm = nullptr, *gv = nullptr, *grad = nullptr, *partials = nullptr;
   unsigned* flags = nullptr;
@@ -767,13 +770,35 @@ int adjoint_layout(mmp_ctx* c, Prob& p, int ckpt_every, char* base, AdjLayout& L
     if (smem > limit) break;
     MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, smem));
     const long long G = ((long long)p.Q + (long long)nq * kTPB - 1) / ((long long)nq * kTPB);
-    if (occ >= 1 && G <= (long long)occ * c->dev.sms) {
+    if (occ >= 1 && G <= (long long)c->dev.sms) {  // about one CTA per SM (see the forward below)
       L.nq = nq;
       L.G = (int)G;
       break;
     }
   }
   if (L.G == 0) return MMP_ERR_UNSUPPORTED;
+  // The recording forward runs the slices one after another, so it takes
+  // its own shape rather than the Parareal plan's: about one CTA per SM
+  // (the fewest quads per thread with G <= SMs).  More CTAs leave each with
+  // too little work per step for the cross-CTA exchange they add.
+  L.fG = 0;
+  for (int nq = 1; nq <= max_nq; ++nq) {
+    const void* ff = fine_kernel(p.d.precision, kLayoutSmem, nq, p.mult);
+    size_t flimit = 0;
+    const int frc = allow_dynamic_smem(ff, c->dev.dev, &flimit);
+    if (frc) return frc;
+    const size_t smem = fine_smem_bytes(p.d.precision, kLayoutSmem, nq);
+    if (smem > flimit) break;
+    int occ = 0;
+    MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ff, kTPB, smem));
+    const long long G = ((long long)p.Q + (long long)nq * kTPB - 1) / ((long long)nq * kTPB);
+    if (occ >= 1 && G <= (long long)c->dev.sms) {
+      L.fnq = nq;
+      L.fG = (int)G;
+      break;
+    }
+  }
+  if (L.fG == 0) return MMP_ERR_UNSUPPORTED;
   Carver cv{base, 0};
   const size_t row = (size_t)p.pitch * p.esz;
   auto ptr = [&](size_t b) -> char* {
@@ -790,6 +815,8 @@ int adjoint_layout(mmp_ctx* c, Prob& p, int ckpt_every, char* base, AdjLayout& L
   L.partials = (double*)ptr(sizeof(double) * kSeatDoubles * (size_t)L.G);
   L.tags = (unsigned long long*)ptr((sizeof(unsigned long long) * kSlots + sizeof(unsigned)) * (size_t)L.G);
   L.flags = base ? (unsigned*)(L.tags + (size_t)kSlots * L.G) : nullptr;
+  L.fpartials = (double*)ptr(sizeof(double) * kSeatDoubles * (size_t)L.fG);
+  L.ftags = (unsigned long long*)ptr((sizeof(unsigned long long) * kSlots + sizeof(unsigned)) * (size_t)L.fG);
   L.bytes = (cv.off + kAlign - 1) / kAlign * kAlign;
   return MMP_OK;
 }
@@ -1175,12 +1202,21 @@ int mmp_adjoint_forward(mmp_ctx* ctx, int prob, int ckpt_every, void* ws, size_t
   if (rc) return rc;
   if (L.bytes > ws_bytes) return MMP_ERR_WORKSPACE;
   const int N = p.d.N;
-  // the serial fine run with recording; slice ends restricted into ser_stats
-  rc = run_fine(ctx, p, 0, 1, 0, p.u0, nullptr, nullptr, 0, nullptr, 0, p.ser_stats, 1);
+  // the serial fine run with recording, in the forward's own launch shape;
+  // slice ends restricted into ser_stats
+  Prob q = p;
+  q.layout = kLayoutSmem;
+  q.nq = L.fnq;
+  q.G = L.fG;
+  q.slots_max = 1;
+  q.partials = L.fpartials;
+  q.tags = L.ftags;
+  q.flags = (unsigned*)(L.ftags + (size_t)kSlots * L.fG);
+  rc = run_fine(ctx, q, 0, 1, 0, p.u0, nullptr, nullptr, 0, nullptr, 0, p.ser_stats, 1);
   if (rc) return rc;
   for (int n = 0; n < N; ++n) {
     const void* in = n == 0 ? (const void*)p.u0 : (const void*)p.S[(n - 1) & 1];
-    rc = run_fine(ctx, p, n, 1, p.nf, in, nullptr, p.S[n & 1], 1, nullptr, 0,
+    rc = run_fine(ctx, q, n, 1, p.nf, in, nullptr, p.S[n & 1], 1, nullptr, 0,
                   p.ser_stats + (size_t)(n + 1) * kStat, 1, L.uni, L.ckpt, ckpt_every, (long long)n * p.nf);
     if (rc) return rc;
   }

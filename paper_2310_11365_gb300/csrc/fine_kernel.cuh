@@ -97,6 +97,10 @@ struct Group {
   unsigned epoch;           // epochs published so far by this CTA
 };
 
+// Polls of a bounded wait before it backs off with nanosleep (a word that is
+// about to land is then picked up at L2 latency, not at sleep granularity).
+constexpr int kTightPolls = 256;
+
 __device__ __forceinline__ double* group_slot(const Group& grp, int c, unsigned e) {
   return grp.part + ((size_t)c * kSlots + (e & (unsigned)(kSlots - 1))) * kNV;
 }
@@ -118,8 +122,8 @@ __device__ __forceinline__ bool group_wait(const Group& grp, unsigned e) {
   for (int c = threadIdx.x & 31; c < grp.G && ok; c += 32) {
     if (ld_acquire_gpu(grp.flags + c) > e) continue;
     const unsigned long long t0 = globaltimer_ns();
-    for (;;) {
-      __nanosleep(64);
+    for (int spin = 0;; ++spin) {
+      if (spin >= kTightPolls) __nanosleep(64);
       if (ld_acquire_gpu(grp.flags + c) > e) break;
       if (globaltimer_ns() - t0 > grp.limit_ns) {
         atomicOr(grp.status, kStatusTimeout);
@@ -276,7 +280,7 @@ struct StepSum<float> {
     st_relaxed_gpu_b64(grp.tags + (size_t)(e & (unsigned)(kSlots - 1)) * grp.G + grp.g, w);
   }
   // whole warp: bounded wait for the tagged words of epoch e of every CTA
-  // (lane l reads CTAs l, l + 32, ...; a lane issues its loads of up to 128
+  // (lane l reads CTAs l, l + 32, ...; a lane issues its loads of up to 256
   // CTAs before examining any), their sum in CTA order
   static __device__ __forceinline__ bool fetch(const Group& grp, unsigned e, T& sum) {
     const uint32_t tag = tag_of(e);
@@ -284,15 +288,15 @@ struct StepSum<float> {
     const int lane = threadIdx.x & 31;
     T v = zero();
     bool ok = true;
-    for (int base = 0; base < grp.G; base += 128) {
-      unsigned long long w[4];
+    for (int base = 0; base < grp.G; base += 256) {
+      unsigned long long w[8];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 8; ++k) {
         const int c = base + lane + 32 * k;
         w[k] = c < grp.G ? ld_relaxed_gpu_b64(row + c) : 0ull;
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 8; ++k) {
         const int c = base + lane + 32 * k;
         if (c < grp.G) {
           if (ok && ((uint32_t)(w[k] >> 32) & 0xFFFFu) != tag) {
@@ -318,8 +322,8 @@ struct StepSum<float> {
   static __device__ __noinline__ unsigned long long wait_word(const Group& grp, const unsigned long long* p,
                                                               uint32_t tag) {
     const unsigned long long t0 = globaltimer_ns();
-    for (;;) {
-      __nanosleep(64);
+    for (int spin = 0;; ++spin) {
+      if (spin >= kTightPolls) __nanosleep(64);
       const unsigned long long w = ld_relaxed_gpu_b64(p);
       if (((uint32_t)(w >> 32) & 0xFFFFu) == tag) return w;
       if (globaltimer_ns() - t0 > grp.limit_ns) {
