@@ -363,6 +363,8 @@ def main():
     ap.add_argument("--batch-sweeps", type=int, default=2, help="fine sweeps timed for the batched workload")
     ap.add_argument("--no-cfg3", action="store_true", help="skip the config-3 (learning variant) solve")
     ap.add_argument("--no-cfg4", action="store_true", help="skip the config-4 adjoint timing")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="plan config 2 with the cost model instead of measured shapes (profiling runs)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -390,7 +392,7 @@ def main():
     # problems, registered before any context is planned
     from paper_2310_11365_gb300 import tune
 
-    tuned = tune.tune([p, p.scaled(precision="fp64")], probe_steps=32)
+    tuned = {} if args.no_tune else tune.tune([p, p.scaled(precision="fp64")], probe_steps=32)
     solver = mmp.Solver(p)
     mmp.mmp_set_timing(solver.ctx, True)
     plan = solver.plan()

@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
   grp.G = G;
   grp.g = g;
   grp.epoch = 0;
+  grp.tight_polls = G <= a.sms ? kTightPolls : 0;
   if (tid == 0) sh.abort = 0;
 
   QuadStore<R, 0> lam;  // lambda of this thread's quads, in shared memory

@@ -31,6 +31,7 @@ struct AdjointArgs {
   unsigned long long* tags;          // [kSlots][G] tagged step words (zeroed per launch)
   unsigned* status;
   unsigned long long wait_limit_ns;
+  int sms;                           // SMs of the device
 };
 
 const void* adjoint_kernel(int precision);

@@ -565,6 +565,7 @@ int run_fine(mmp_ctx* c, Prob& p, int slice_begin, int n_tasks, int nf, const vo
   a.ckpt_every = ckpt_every;
   a.step_offset = step_offset;
   const int slots = std::min(n_tasks, p.slots_max);
+  a.tight_polls = slots * p.G <= c->dev.sms ? kTightPolls : 0;
   MMP_CUDA(cudaMemsetAsync(p.tags, 0, sync_bytes(p), c->stream));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
@@ -1268,6 +1269,7 @@ int mmp_adjoint_backward(mmp_ctx* ctx, int prob, const double* gm, const double*
   a.mom = p.ser_stats; a.gm = L.gm; a.gv = L.gv; a.grad = L.grad;
   a.partials = L.partials; a.flags = L.flags; a.tags = L.tags; a.status = p.status;
   a.wait_limit_ns = ctx->limit_ns;
+  a.sms = ctx->dev.sms;
   MMP_CUDA(launch_adjoint(p.d.precision, a, ctx->stream));
   ctx->other_launches += 1;
   MMP_CUDA(cudaMemcpyAsync(grad_out, L.grad, sizeof(double) * 5, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1453,6 +1455,7 @@ extern "C" int mmp_fine_static(const mmp_problem_desc* desc, int n, const void* 
   a.nq = p.nq;
   a.partials = base; a.flags = flags; a.tags = tags; a.status = status;
   a.wait_limit_ns = wait_limit_ns();
+  a.tight_polls = p.G <= dev.sms ? kTightPolls : 0;
   MMP_CUDA(launch_fine(d.precision, p.layout, p.nq, p.mult, p.G, a, s));
   if (stats_dev != nullptr) {
     k_status_to_stats<<<1, 1, 0, s>>>(status, stats_dev);

@@ -35,6 +35,7 @@ struct FineArgs {
   unsigned long long* tags;    // [slot][kSlots][G] tagged step words (zeroed per launch)
   unsigned* status;            // device status word
   unsigned long long wait_limit_ns;
+  int tight_polls = 0;         // polls before a group wait backs off (launches of <= 1 CTA per SM)
   // optional recording for the adjoint (serial runs only, one task):
   void* rec_uni = nullptr;     // [global step][3] (m_j, h (kappa m_j + c0), B0 sqrt h), precision R
   void* rec_ckpt = nullptr;    // particle rows at global steps 0, c, 2c, ... (row gstep / c)

@@ -95,11 +95,9 @@ struct Group {
   unsigned long long limit_ns;
   int G, g;
   unsigned epoch;           // epochs published so far by this CTA
+  int tight_polls = 0;      // polls before a wait backs off (kTightPolls or 0)
 };
 
-// Polls of a bounded wait before it backs off with nanosleep (a word that is
-// about to land is then picked up at L2 latency, not at sleep granularity).
-constexpr int kTightPolls = 256;
 
 __device__ __forceinline__ double* group_slot(const Group& grp, int c, unsigned e) {
   return grp.part + ((size_t)c * kSlots + (e & (unsigned)(kSlots - 1))) * kNV;
@@ -123,7 +121,7 @@ __device__ __forceinline__ bool group_wait(const Group& grp, unsigned e) {
     if (ld_acquire_gpu(grp.flags + c) > e) continue;
     const unsigned long long t0 = globaltimer_ns();
     for (int spin = 0;; ++spin) {
-      if (spin >= kTightPolls) __nanosleep(64);
+      if (spin >= grp.tight_polls) __nanosleep(64);
       if (ld_acquire_gpu(grp.flags + c) > e) break;
       if (globaltimer_ns() - t0 > grp.limit_ns) {
         atomicOr(grp.status, kStatusTimeout);
@@ -323,7 +321,7 @@ struct StepSum<float> {
                                                               uint32_t tag) {
     const unsigned long long t0 = globaltimer_ns();
     for (int spin = 0;; ++spin) {
-      if (spin >= kTightPolls) __nanosleep(64);
+      if (spin >= grp.tight_polls) __nanosleep(64);
       const unsigned long long w = ld_relaxed_gpu_b64(p);
       if (((uint32_t)(w >> 32) & 0xFFFFu) == tag) return w;
       if (globaltimer_ns() - t0 > grp.limit_ns) {
@@ -866,6 +864,7 @@ __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, NQ>::value)) k_fine(co
   grp.G = G;
   grp.g = g;
   grp.epoch = 0;
+  grp.tight_polls = a.tight_polls;
   if (threadIdx.x == 0) sh.abort = 0;
   QuadStore<R, NQ> xs;
   xs.bind();

@@ -22,6 +22,13 @@ constexpr int kMom = MMP_MOMENT_STRIDE;
 constexpr int kAff = 4;            // doubles per (slice, region) matching record
 constexpr int kMaxNQ = 8;          // largest quads-per-thread template
 
+// Polls of a bounded group wait before it backs off with nanosleep, for
+// launches with at most one CTA per SM: a word about to land is then picked
+// up at L2 latency rather than at sleep granularity, and no co-resident CTA
+// loses issue slots to the spinning warp.  With co-resident CTAs a wait
+// sleeps from the first miss.
+constexpr int kTightPolls = 256;
+
 // Device status bits (or-ed into the status word).
 constexpr unsigned kStatusTimeout = 1u;
 constexpr unsigned kStatusNumeric = 2u;
@@ -82,7 +89,7 @@ __device__ __forceinline__ double fmaR(double a, double b, double c) { return __
 
 // Box-Muller: z = sqrt(-2 ln ua) (cos 2 pi ub, sin 2 pi ub).
 // FP32 form on the special-function unit: ln ua from the hardware log2,
-// sqrt t as t * rsqrt(t), and sin/cos of theta = 2 pi (ub - 1/2), which lies
+// the hardware square root, and sin/cos of theta = 2 pi (ub - 1/2), which lies
 // in [-pi, pi) where the hardware sin/cos are accurate; then
 // cos 2 pi ub = -cos theta and sin 2 pi ub = -sin theta.  The draws differ
 // from the FP64 definition by a few 1e-6 absolute (bounded in the tests).
@@ -90,7 +97,8 @@ __device__ __forceinline__ double fmaR(double a, double b, double c) { return __
 // where fb - 3/2 is exact, so theta takes one add and one fused multiply-add.
 __device__ __forceinline__ void box_muller_f(float ua, float fb, float& z0, float& z1) {
   const float t = -1.38629436f * __log2f(ua);  // -2 ln 2 log2(ua) > 0 for ua < 1
-  const float r = t * rsqrtf(t);
+  float r;  // sqrt t on the special-function unit (one instruction)
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
   float s, c;
   __sincosf(__fmaf_rn(__fsub_rn(fb, 1.5f), 6.28318531f, 3.74507028e-7f), &s, &c);  // 2 pi 2^-24
   z0 = -r * c;
