@@ -166,28 +166,49 @@ def replica_value(units: float, seconds: float, world: int) -> float:
     return sum_over_ranks(units, world) / max_over_ranks(seconds, world)
 
 
-def cpu_baseline(seconds: float = 12.0) -> dict:
-    """The FP64 oracle as it stands, on this host's cores (it is
-    single-threaded): fine particle-steps/s of the config-2 model on a
-    bounded sample (P = 2000 particles, whole slices, until ~`seconds`)."""
+def _oracle_worker(args):
+    """One host core: the oracle's fine propagator on the config-2 model
+    (P = 2000), whole slices, from slice `first`, until `seconds` pass."""
+    first, seconds = args
     import oracle
     from paper_2310_11365_gb300 import workloads as W
 
-    oracle.build()
     p = W.config2(P=2000, precision="fp64")
     u = oracle.initial(p)
     nf = oracle.fine_steps(p)
     t0 = time.perf_counter()
     slices = 0
     while True:
-        u = oracle.fine(p, slices % p.N, u)
+        u = oracle.fine(p, (first + slices) % p.N, u)
         slices += 1
         if time.perf_counter() - t0 > seconds:
             break
-    dt = time.perf_counter() - t0
-    steps = slices * p.P * nf
-    return {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle fine propagator on the config-2 model, P=2000, {slices} slices x {nf} steps ({steps:.3g} particle-steps, {dt:.1f} s)"}
+    return slices * p.P * nf, time.perf_counter() - t0
+
+
+def cpu_baseline(seconds: float = 12.0) -> dict:
+    """The FP64 oracle as it stands (single-threaded C) on this host's cores:
+    one process per core (spawned, so no CUDA state is inherited), each
+    running the fine propagator of the config-2 model on a bounded sample
+    (P = 2000 particles, whole slices, ~`seconds`); value = all processes'
+    particle-steps over the longest process time.  The same sample on one
+    core is reported beside it."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    cores = max(1, os.cpu_count() or 1)
+    one_steps, one_dt = _oracle_worker((0, seconds / 3))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(i * 7, seconds) for i in range(cores)])
+    steps = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    return {"value": steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core_value": one_steps / one_dt,
+            "sample": f"FP64 oracle fine propagator on the config-2 model, P=2000, whole slices of 125 steps; "
+                      f"{cores} processes x {dt:.1f} s ({steps:.3g} particle-steps); one core "
+                      f"{one_dt:.1f} s ({one_steps:.3g} particle-steps)"}
 
 
 def batched_run(n_problems: int, sweeps: int, rank: int, to_tol: bool = False) -> dict:
