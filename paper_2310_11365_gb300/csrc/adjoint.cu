@@ -121,14 +121,17 @@ __global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
       for (int jj = 0; jj < L; ++jj) {
         const long long j = j0 + jj;
         Quad<R>::store(segx + (size_t)jj * a.pitch + 4 * (size_t)q, x);
-        R z[4];
-        normals4<R>(philox4x32_10(rng_counter((uint32_t)q, (uint32_t)(j % a.nf), (uint32_t)(j / a.nf), 0u,
-                                              a.ptag), a.key0, a.key1), z);
+        R nr[2], c[2], sn[2];
+        normals4_polar<R>(philox4x32_10(rng_counter((uint32_t)q, (uint32_t)(j % a.nf), (uint32_t)(j / a.nf), 0u,
+                                                    a.ptag), a.key0, a.key1), nr, c, sn);
+        const R z[4] = {mulR(nr[0], c[0]), mulR(nr[0], sn[0]), mulR(nr[1], c[1]), mulR(nr[1], sn[1])};
         Quad<R>::store(segz + (size_t)jj * a.pitch + 4 * (size_t)q, z);
         const R d = uni[3 * j + 1];    // h (kappa m_j + c0) as the forward used it
         const R amp = uni[3 * j + 2];  // B0 sqrt(h) as the forward used it
+        em_partial_pair(x[0], x[1], nr[0], c[0], sn[0], hn3, hc1, amp);
+        em_partial_pair(x[2], x[3], nr[1], c[1], sn[1], hn3, hc1, amp);
 #pragma unroll
-        for (int w = 0; w < 4; ++w) x[w] = addR(em_partial(x[w], z[w], hn3, hc1, amp), d);
+        for (int w = 0; w < 4; ++w) x[w] = addR(x[w], d);
         zero_tail(q, x);
       }
       Quad<R>::store(segx + (size_t)L * a.pitch + 4 * (size_t)q, x);

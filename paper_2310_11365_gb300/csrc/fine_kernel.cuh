@@ -242,14 +242,18 @@ __device__ __forceinline__ double addR(double a, double b) { return __dadd_rn(a,
 __device__ __forceinline__ float mulR(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mulR(double a, double b) { return __dmul_rn(a, b); }
 
-// The part of one Euler-Maruyama step that does not depend on the mean:
-//   y = x + h (nc3 x^3 + c1 x) + amp xi = fma(amp, xi, fma(fma(hn3, x^2, hc1), x, x)),
-// with hn3 = h nc3 and hc1 = h c1.  The step is x_{j+1} = y + h (kappa m_j + c0),
-// a shift common to all particles (the fine kernel and the adjoint's replay
-// both evaluate it through this function).
+// The part of one Euler-Maruyama step that does not depend on the mean, for
+// the two particles that share a Box-Muller pair (normals nr (c | s)):
+//   y = x + h (nc3 x^3 + c1 x) + amp xi = fma(amp nr, c | s, fma(fma(hn3, x^2, hc1), x, x)),
+// with hn3 = h nc3 and hc1 = h c1 and the amplitude folded into the radius
+// once per pair.  The step is x_{j+1} = y + h (kappa m_j + c0), a shift
+// common to all particles (the fine kernel and the adjoint's replay both
+// evaluate it through this function).
 template <typename R>
-__device__ __forceinline__ R em_partial(R x, R xi, R hn3, R hc1, R amp) {
-  return fmaR(amp, xi, fmaR(fmaR(hn3, mulR(x, x), hc1), x, x));
+__device__ __forceinline__ void em_partial_pair(R& x0, R& x1, R nr, R c, R s, R hn3, R hc1, R amp) {
+  const R ar = mulR(amp, nr);
+  x0 = fmaR(ar, c, fmaR(fmaR(hn3, mulR(x0, x0), hc1), x0, x0));
+  x1 = fmaR(ar, s, fmaR(fmaR(hn3, mulR(x1, x1), hc1), x1, x1));
 }
 
 // The per-step sum of the particles: a double-float pair for float
@@ -455,7 +459,7 @@ struct FineOccupancy {
 //
 // * mean-additive diffusion (MULT false: b = B0, and generally whenever the
 //   mean enters the step only through the drift term kappa m + c0): the
-//   step is x_{j+1} = y_j + d_j with y_j = em_partial(x_j) independent of
+//   step is x_{j+1} = y_j + d_j with y_j = em_partial_pair(x_j) independent of
 //   the mean and d_j = h (kappa m_j + c0) common to all particles.  The
 //   stored state is y_j with the shift pending; since
 //   m_{j+1} = mean(y_j) + d_j, the sum over y_j published at the end of
@@ -491,6 +495,10 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   const int plast = (int)(a.P - 4LL * qlast);  // valid lanes of the last quad, 1..4
   const int loop_n = NQ > 0 ? NQ : nq;        // quads this thread visits
   const int nf = a.nf;
+  // this thread's index of the ragged last quad (lanes past P), or -1
+  const int tail_off = qlast - qb - tid;
+  const int tail_i = (plast < 4 && tail_off >= 0 && tail_off % kTPB == 0 && tail_off / kTPB < nq)
+                         ? tail_off / kTPB : -1;
 
   // Coefficients in the particle precision.  For float particles they are
   // rounded once per task by one thread and read from shared memory: left
@@ -643,15 +651,18 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
         const uint32_t q = (uint32_t)(qb + tid + i * kTPB);
         R v[4];
         xs.get(i, v);
-        R z[4];
-        normals4<R>(philox4x32_10(rng_counter(q, (uint32_t)j, (uint32_t)n, 0u, a.ptag), a.key0, a.key1), z);
+        const uint4 o = philox4x32_10(rng_counter(q, (uint32_t)j, (uint32_t)n, 0u, a.ptag), a.key0, a.key1);
         if constexpr (kLag) {
+          R nr[2], c[2], sn[2];
+          normals4_polar<R>(o, nr, c, sn);
 #pragma unroll
           for (int w = 0; w < 4; ++w) v[w] = addR(v[w], d);  // x_j = y_{j-1} + d_{j-1}
           if (ckpt) Quad<R>::store(ck_row + 4 * (size_t)q, v);
-#pragma unroll
-          for (int w = 0; w < 4; ++w) v[w] = em_partial(v[w], z[w], hn3, hc1, b0sq);
+          em_partial_pair(v[0], v[1], nr[0], c[0], sn[0], hn3, hc1, b0sq);
+          em_partial_pair(v[2], v[3], nr[1], c[1], sn[1], hn3, hc1, b0sq);
         } else {
+          R z[4];
+          normals4<R>(o, z);
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
             const R xv = v[w];
@@ -660,14 +671,34 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
             v[w] = fmaR(amp, z[w], fmaR(h, drift, xv));
           }
         }
-        if (q == (uint32_t)qlast) {
-          if (plast < 4) v[3] = (R)0;
-          if (plast < 3) v[2] = (R)0;
-          if (plast < 2) v[1] = (R)0;
-        }
+        // lanes past P evolve like particles; their values leave the sum below
         s = addR(s, addR(addR(v[0], v[1]), addR(v[2], v[3])));
         xs.put(i, v);
       }
+    }
+    if (tail_i >= 0) {
+      // the lanes past P of the ragged last quad (this thread's, if any)
+      // leave the sum: they evolve like particles but are none
+      R pad = (R)0;
+      if constexpr (NQ > 0) {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+          if (i == tail_i) {
+            R v[4];
+            xs.get(i, v);
+#pragma unroll
+            for (int w = 3; w >= 1; --w)
+              if (w >= plast) pad = addR(pad, v[w]);
+          }
+        }
+      } else {
+        R v[4];
+        xs.get(tail_i, v);
+#pragma unroll
+        for (int w = 3; w >= 1; --w)
+          if (w >= plast) pad = addR(pad, v[w]);
+      }
+      s = addR(s, -pad);
     }
     step_sum_warp<R>(sh, j & 1, s);
     if constexpr (kLag) {

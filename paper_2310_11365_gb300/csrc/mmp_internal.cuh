@@ -95,22 +95,32 @@ __device__ __forceinline__ double fmaR(double a, double b, double c) { return __
 // from the FP64 definition by a few 1e-6 absolute (bounded in the tests).
 // ub enters as fb = 1 + (o >> 9) 2^-23 in [1, 2): ub - 1/2 = (fb - 3/2) + 2^-24,
 // where fb - 3/2 is exact, so theta takes one add and one fused multiply-add.
-__device__ __forceinline__ void box_muller_f(float ua, float fb, float& z0, float& z1) {
+// Polar form: the pair is (nr c, nr s) with nr = -sqrt(t), c = cos theta,
+// s = sin theta, so a caller that scales both normals by one amplitude can
+// scale nr once.
+__device__ __forceinline__ void polar_f(float ua, float fb, float& nr, float& c, float& s) {
   const float t = -1.38629436f * __log2f(ua);  // -2 ln 2 log2(ua) > 0 for ua < 1
   float r;  // sqrt t on the special-function unit (one instruction)
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
-  float s, c;
   __sincosf(__fmaf_rn(__fsub_rn(fb, 1.5f), 6.28318531f, 3.74507028e-7f), &s, &c);  // 2 pi 2^-24
-  z0 = -r * c;
-  z1 = -r * s;
+  nr = -r;
+}
+__device__ __forceinline__ void box_muller_f(float ua, float fb, float& z0, float& z1) {
+  float nr, c, s;
+  polar_f(ua, fb, nr, c, s);
+  z0 = __fmul_rn(nr, c);
+  z1 = __fmul_rn(nr, s);
 }
 __device__ __forceinline__ float unit_f(uint32_t o) { return __uint_as_float(0x3F800000u | (o >> 9)); }
-__device__ __forceinline__ void box_muller(double ua, double ub, double& z0, double& z1) {
-  const double r = sqrt(-2.0 * log(ua));
-  double s, c;
+__device__ __forceinline__ void polar_d(double ua, double ub, double& nr, double& c, double& s) {
+  nr = sqrt(-2.0 * log(ua));
   sincospi(2.0 * ub, &s, &c);
-  z0 = r * c;
-  z1 = r * s;
+}
+__device__ __forceinline__ void box_muller(double ua, double ub, double& z0, double& z1) {
+  double nr, c, s;
+  polar_d(ua, ub, nr, c, s);
+  z0 = nr * c;
+  z1 = nr * s;
 }
 
 template <typename R>
@@ -124,6 +134,20 @@ template <>
 __device__ __forceinline__ void normals4<double>(uint4 o, double z[4]) {
   box_muller(uniform_d(o.x), uniform_d(o.y), z[0], z[1]);
   box_muller(uniform_d(o.z), uniform_d(o.w), z[2], z[3]);
+}
+
+// The same four normals in polar form: normal 2k + i is nr[k] (c[k] | s[k]).
+template <typename R>
+__device__ __forceinline__ void normals4_polar(uint4 o, R nr[2], R c[2], R s[2]);
+template <>
+__device__ __forceinline__ void normals4_polar<float>(uint4 o, float nr[2], float c[2], float s[2]) {
+  polar_f(uniform_f(o.x), unit_f(o.y), nr[0], c[0], s[0]);
+  polar_f(uniform_f(o.z), unit_f(o.w), nr[1], c[1], s[1]);
+}
+template <>
+__device__ __forceinline__ void normals4_polar<double>(uint4 o, double nr[2], double c[2], double s[2]) {
+  polar_d(uniform_d(o.x), uniform_d(o.y), nr[0], c[0], s[0]);
+  polar_d(uniform_d(o.z), uniform_d(o.w), nr[1], c[1], s[1]);
 }
 
 // Counter of the draw for particle quad q under (tag, step j, slice n).
