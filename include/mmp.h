@@ -209,6 +209,23 @@ int mmp_set_timing(mmp_ctx* ctx, int on);
 int mmp_timing(mmp_ctx* ctx, int reset, double* fine_ms, long long* fine_launches,
                double* fine_particle_steps, long long* other_launches);
 
+/* Checkpoint and resume of a run (for instance across a process restart).
+ * The state is the contents of the context's workspace (particle buffers,
+ * macro states, matching records, control blocks) and each problem's host
+ * view of the iteration (sweeps done, finished, last change, which buffer
+ * holds each slice's latest output).  mmp_state_size gives its bytes;
+ * mmp_get_state writes it to host memory `dst` (caller-owned, that many
+ * bytes); mmp_set_state restores it into a context created with the same
+ * problem descriptions and the same launch plans, at any workspace address:
+ * the next mmp_iterate continues exactly as the saved context would have,
+ * bit for bit.  Adjoint recordings are not part of the state.  Both
+ * synchronise.  Errors: MMP_ERR_INVALID_ARG (NULL), MMP_ERR_STATE (the blob
+ * belongs to other problems, plans or library version), MMP_ERR_CUDA.  The
+ * paper has no counterpart (a property of this library). */
+int mmp_state_size(mmp_ctx* ctx, size_t* bytes);
+int mmp_get_state(mmp_ctx* ctx, void* dst);
+int mmp_set_state(mmp_ctx* ctx, const void* src);
+
 /* Batched sweeps of a context with several problems (one cooperative
  * launch per sweep over every unconverged problem's slices; the task list
  * is built on the device, so sweeps run back to back).  batched (may be

@@ -341,6 +341,8 @@ unsigned long long wait_limit_ns() {
 
 struct mmp_ctx {
   std::vector<Prob> probs;
+  char* ws = nullptr;   // the caller's workspace and the bytes the layout uses
+  size_t ws_used = 0;
   cudaStream_t stream = nullptr;
   Device dev;
   unsigned long long limit_ns = 0;
@@ -886,6 +888,8 @@ int mmp_create(mmp_ctx** out, const mmp_problem_desc* descs, int n_problems, voi
     return rc;
   }
   off = batch_layout(c->probs, B, (char*)workspace, off, c);
+  c->ws = (char*)workspace;
+  c->ws_used = off;
   c->batch = B.on;
   c->batch_grid = B.grid;
   c->batch_smem = B.smem;
@@ -1647,5 +1651,123 @@ extern "C" int mmp_set_batch_nq(int precision, int quads_per_thread) {
   if (quads_per_thread < 0 || quads_per_thread > (precision == MMP_MIXED ? 32 : 16)) return MMP_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_batch_nq[precision == MMP_MIXED ? 1 : 0] = quads_per_thread;
+  return MMP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint and resume (mmp_state_size, mmp_get_state, mmp_set_state).
+//
+// The state of a run is the contents of the workspace the layout uses (every
+// particle buffer, macro state, matching record and control block lives
+// there) plus each problem's host view of the iteration.  A blob starts with
+// a header (library version, a hash of the problem descriptions and of each
+// launch plan), so it is only restored into a context whose problems and
+// plans are the same: the plan fixes the workspace layout and the order of
+// every sum, so the resumed run continues bit for bit.  Restoring into a
+// workspace at another address rewrites the batched records, which hold
+// device pointers.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr unsigned long long kStateMagic = 0x6d6d702d73746174ull;  // "mmp-stat"
+
+struct StateHeader {
+  unsigned long long magic;
+  int version, n;
+  unsigned long long digest;
+  unsigned long long ws_used;
+};
+
+struct ProbState {
+  int sweeps, lifted, done, converged;
+  double last_change;
+};
+
+unsigned long long fnv(unsigned long long h, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// Digest of the problem descriptions (field by field: the struct's padding
+// bytes carry no value) and of the launch plans.
+unsigned long long state_digest(const mmp_ctx* c) {
+  unsigned long long h = 1469598103934665603ull;
+  for (const Prob& p : c->probs) {
+    const mmp_problem_desc& d = p.d;
+    const double dv[] = {d.c3, d.c1, d.kappa, d.c0, d.B, d.BE, d.B0, d.m0, d.s0, d.T, d.dt, d.coarse_h,
+                         d.threshold, d.tol};
+    const long long iv[] = {d.N, d.P, d.n_regions, d.variant, d.precision, (long long)d.seed,
+                            (long long)d.problem_tag, d.max_iter, p.layout, p.nq, p.G, p.slots_max};
+    h = fnv(h, dv, sizeof(dv));
+    h = fnv(h, iv, sizeof(iv));
+  }
+  return fnv(h, &c->ws_used, sizeof(c->ws_used));
+}
+
+size_t state_bytes(const mmp_ctx* c) {
+  size_t b = sizeof(StateHeader);
+  for (const Prob& p : c->probs) b += sizeof(ProbState) + sizeof(int) * (size_t)p.d.N;
+  return b + c->ws_used;
+}
+
+}  // namespace
+
+extern "C" int mmp_state_size(mmp_ctx* ctx, size_t* bytes) {
+  if (ctx == nullptr || bytes == nullptr) return MMP_ERR_INVALID_ARG;
+  *bytes = state_bytes(ctx);
+  return MMP_OK;
+}
+
+extern "C" int mmp_get_state(mmp_ctx* ctx, void* dst) {
+  if (ctx == nullptr || dst == nullptr) return MMP_ERR_INVALID_ARG;
+  char* o = (char*)dst;
+  StateHeader hd{kStateMagic, mmp_version(), (int)ctx->probs.size(), state_digest(ctx), ctx->ws_used};
+  std::memcpy(o, &hd, sizeof(hd));
+  o += sizeof(hd);
+  for (const Prob& p : ctx->probs) {
+    ProbState ps{p.sweeps, p.lifted ? 1 : 0, p.done ? 1 : 0, p.converged ? 1 : 0, p.last_change};
+    std::memcpy(o, &ps, sizeof(ps));
+    o += sizeof(ps);
+    std::memcpy(o, p.out_buf.data(), sizeof(int) * (size_t)p.d.N);
+    o += sizeof(int) * (size_t)p.d.N;
+  }
+  MMP_CUDA(cudaMemcpyAsync(o, ctx->ws, ctx->ws_used, cudaMemcpyDeviceToHost, ctx->stream));
+  MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return MMP_OK;
+}
+
+extern "C" int mmp_set_state(mmp_ctx* ctx, const void* src) {
+  if (ctx == nullptr || src == nullptr) return MMP_ERR_INVALID_ARG;
+  const char* i = (const char*)src;
+  StateHeader hd;
+  std::memcpy(&hd, i, sizeof(hd));
+  i += sizeof(hd);
+  if (hd.magic != kStateMagic || hd.version != mmp_version() || hd.n != (int)ctx->probs.size() ||
+      hd.digest != state_digest(ctx) || hd.ws_used != ctx->ws_used)
+    return MMP_ERR_STATE;
+  for (Prob& p : ctx->probs) {
+    ProbState ps;
+    std::memcpy(&ps, i, sizeof(ps));
+    i += sizeof(ps);
+    p.sweeps = ps.sweeps;
+    p.lifted = ps.lifted != 0;
+    p.done = ps.done != 0;
+    p.converged = ps.converged != 0;
+    p.last_change = ps.last_change;
+    std::memcpy(p.out_buf.data(), i, sizeof(int) * (size_t)p.d.N);
+    i += sizeof(int) * (size_t)p.d.N;
+    p.adj_ready = false;
+  }
+  MMP_CUDA(cudaMemcpyAsync(ctx->ws, i, ctx->ws_used, cudaMemcpyHostToDevice, ctx->stream));
+  MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (ctx->batch) {
+    const int rc = batch_setup(ctx);  // the batched records hold device pointers
+    if (rc) return rc;
+  }
   return MMP_OK;
 }

@@ -35,6 +35,7 @@ EXPORTED = [
     "mmp_normals", "mmp_get_plan", "mmp_set_timing", "mmp_timing", "mmp_fine_static",
     "mmp_set_params", "mmp_adjoint_workspace_size", "mmp_adjoint_forward", "mmp_adjoint_backward",
     "mmp_batch_info", "mmp_autotune_workspace_size", "mmp_autotune", "mmp_set_tuning", "mmp_set_batch_nq",
+    "mmp_state_size", "mmp_get_state", "mmp_set_state",
 ]
 
 
@@ -105,6 +106,9 @@ def load():
         "mmp_autotune": ([pd, C.POINTER(i), i, i, vp, C.c_size_t, vp, C.POINTER(i), d], i),
         "mmp_set_tuning": ([i, ll, ll, i], i),
         "mmp_set_batch_nq": ([i, i], i),
+        "mmp_state_size": ([vp, C.POINTER(C.c_size_t)], i),
+        "mmp_get_state": ([vp, vp], i),
+        "mmp_set_state": ([vp, vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -277,6 +281,20 @@ def mmp_set_batch_nq(precision: str, quads_per_thread: int) -> None:
     _check(load().mmp_set_batch_nq(prec, int(quads_per_thread)), "mmp_set_batch_nq")
 
 
+def mmp_get_state(ctx) -> bytes:
+    """The context's checkpoint (see the C header) as bytes."""
+    n = C.c_size_t()
+    _check(load().mmp_state_size(ctx, C.byref(n)), "mmp_state_size")
+    buf = (C.c_char * n.value)()
+    _check(load().mmp_get_state(ctx, buf), "mmp_get_state")
+    return bytes(buf)
+
+
+def mmp_set_state(ctx, blob: bytes) -> None:
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(load().mmp_set_state(ctx, buf), "mmp_set_state")
+
+
 def mmp_fine_static(p: workloads.Problem, n: int, u_in_ptr: int, u_out_ptr: int, stats_ptr: int | None,
                     stream=None) -> None:
     """One fine propagation with no device allocation (scratch from the
@@ -388,6 +406,14 @@ class Solver:
         else:
             arr = np.ascontiguousarray(u0, dtype=np.float32 if self.problems[prob].precision == "mixed" else np.float64)
             mmp_set_initial(self.ctx, prob, arr.ctypes.data, True)
+
+    def state(self) -> bytes:
+        """Checkpoint of the run (workspace contents and iteration state)."""
+        return mmp_get_state(self.ctx)
+
+    def restore(self, blob: bytes) -> None:
+        """Resume from a checkpoint of a Solver with the same problems."""
+        mmp_set_state(self.ctx, blob)
 
     def close(self) -> None:
         if self.ctx is not None:
