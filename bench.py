@@ -263,6 +263,31 @@ def batched_run(n_problems: int, sweeps: int, rank: int, to_tol: bool = False) -
     return out
 
 
+def coarse_models_run() -> dict:
+    """Config 2 (mixed) to tolerance with each coarse moment model: the sweeps
+    and device time the choice of coarse propagator costs (the fine sweeps are
+    the same kernel; only how fast the iteration converges differs)."""
+    import torch
+
+    from paper_2310_11365_gb300 import mmp
+    from paper_2310_11365_gb300 import workloads as W
+
+    out = {}
+    for name, model in (("closure", W.CLOSURE), ("taylor", W.TAYLOR), ("sigma2", W.SIGMA2),
+                        ("sigma3", W.SIGMA3)):
+        s = mmp.Solver(W.config2(coarse_model=model))
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        k = s.run()
+        ev1.record()
+        torch.cuda.synchronize()
+        out[name] = {"sweeps": k, "time_to_tol_s": ev0.elapsed_time(ev1) / 1e3,
+                     "converged_before_N": bool(s.status(0)["converged"] and k < s.problems[0].N)}
+        s.close()
+    return out
+
+
 def config3_run() -> dict:
     """Config 3 at full size (double well, two regions split at 0, learning
     variant, P = 4e6, N = 128, n_f = 313): one Parareal solve from lifting to
@@ -505,6 +530,7 @@ def main():
     batch = None
     if args.batch > 0:
         batch = batched_run(args.batch, args.batch_sweeps, rank, args.batch_tol)
+    coarse = None if overrides else coarse_models_run()
     cfg3 = None if args.no_cfg3 or overrides else config3_run()
     cfg4 = None if args.no_cfg4 or overrides else config4_run()
 
@@ -538,6 +564,7 @@ def main():
             "e2e": e2e,
             "fp64_plain": fp64,
             "batched_config5": batch,
+            "coarse_models_config2": coarse,
             "config3": cfg3,
             "config4_adjoint": cfg4,
             "cpu_baseline": cpu,

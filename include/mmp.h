@@ -83,7 +83,21 @@ typedef struct {
   unsigned int problem_tag;
   double tol;                /* stop when max_n max(|dM|,|dV|) < tol          */
   int max_iter;              /* at most this many fine sweeps; <= 0 means N   */
+  int coarse_model;          /* MMP_COARSE_CLOSURE (0) / _TAYLOR / _SIGMA2 / _SIGMA3 */
 } mmp_problem_desc;
+
+/* Coarse moment models (Sec. 2), each integrated by forward Euler per
+ * region with the fractions frozen:
+ *   CLOSURE: Gaussian-assumed density with the expectations of the
+ *            polynomial drift and diffusion in closed form;
+ *   TAYLOR:  the Taylor-expansion model, Eq. moment_model_class_1
+ *            (dM = a(M) + a_XX(M) Sigma / 2, dSigma = (2 a_X + b_X^2) Sigma + b^2);
+ *   SIGMA2 / SIGMA3: Gaussian-assumed density, Eq. Gaussian_model_McK_V_SDE,
+ *            with a 2- or 3-point sigma-point rule. */
+#define MMP_COARSE_CLOSURE 0
+#define MMP_COARSE_TAYLOR 1
+#define MMP_COARSE_SIGMA2 2
+#define MMP_COARSE_SIGMA3 3
 
 typedef struct mmp_ctx mmp_ctx;
 

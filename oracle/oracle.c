@@ -247,6 +247,17 @@ int orc_coarse_steps(const orc_problem* pr) {
   return nc < 1 ? 1 : nc;
 }
 
+/* Right-hand side of the coarse moment ODE of each region i, the mean field
+ * M being the mixture mean (the region's own mean when I = 1).
+ *   closure: dm = E[a], dv = 2 Cov(X, a) + E[b^2] under N(m, v), in closed
+ *            form for the cubic drift (E X^3 = m^3 + 3 m v,
+ *            Cov(X, X^3) = 3 v (m^2 + v));
+ *   Taylor:  dm = a(m) + a_XX(m) v / 2, dv = (2 a_X(m) + b_X^2) v + b(m)^2
+ *            (Eq. moment_model_class_1; the same model without its Sigma^2
+ *            term for this drift);
+ *   sigma-point: the expectations of Eq. Gaussian_model_McK_V_SDE by a
+ *            k-point rule on N(m, v): k = 2: m -+ sqrt(v), weights 1/2;
+ *            k = 3: m, m -+ sqrt(3 v), weights 2/3, 1/6, 1/6. */
 void orc_coarse_rhs(const orc_problem* pr, const orc_macro* r, double* dm, double* dv) {
   const int I = pr->n_regions < 2 ? 1 : pr->n_regions;
   double M = 0.0;
@@ -257,14 +268,45 @@ void orc_coarse_rhs(const orc_problem* pr, const orc_macro* r, double* dm, doubl
   }
   for (int i = 0; i < I; ++i) {
     double m = r->mean[i], v = r->var[i];
-    double ex3 = m * m * m + 3.0 * m * v;
-    double cov3 = 3.0 * v * (m * m + v);
-    double eb = pr->B * m + pr->BE * M + pr->B0;
-    dm[i] = -pr->c3 * ex3 + pr->c1 * m + pr->kappa * M + pr->c0;
-    dv[i] = 2.0 * (-pr->c3 * cov3 + pr->c1 * v) + pr->B * pr->B * v + eb * eb;
+    if (pr->coarse_model == ORC_COARSE_TAYLOR) {
+      double ax = -3.0 * pr->c3 * m * m + pr->c1;
+      double axx = -6.0 * pr->c3 * m;
+      double b = diffusion(pr, m, M);
+      dm[i] = drift(pr, m, M) + 0.5 * axx * v;
+      dv[i] = (2.0 * ax + pr->B * pr->B) * v + b * b;
+    } else if (pr->coarse_model == ORC_COARSE_SIGMA2 || pr->coarse_model == ORC_COARSE_SIGMA3) {
+      double xs[3], ws[3];
+      int k;
+      if (pr->coarse_model == ORC_COARSE_SIGMA2) {
+        double d = sqrt(v > 0.0 ? v : 0.0);
+        xs[0] = m - d; xs[1] = m + d;
+        ws[0] = 0.5; ws[1] = 0.5;
+        k = 2;
+      } else {
+        double d = sqrt(3.0 * (v > 0.0 ? v : 0.0));
+        xs[0] = m; xs[1] = m - d; xs[2] = m + d;
+        ws[0] = 2.0 / 3.0; ws[1] = 1.0 / 6.0; ws[2] = 1.0 / 6.0;
+        k = 3;
+      }
+      double ea = 0.0, exa = 0.0, eb2 = 0.0;
+      for (int s = 0; s < k; ++s) {
+        double a = drift(pr, xs[s], M);
+        double b = diffusion(pr, xs[s], M);
+        ea += ws[s] * a;
+        exa += ws[s] * (xs[s] - m) * a;
+        eb2 += ws[s] * b * b;
+      }
+      dm[i] = ea;
+      dv[i] = 2.0 * exa + eb2;
+    } else {
+      double ex3 = m * m * m + 3.0 * m * v;
+      double cov3 = 3.0 * v * (m * m + v);
+      double eb = pr->B * m + pr->BE * M + pr->B0;
+      dm[i] = -pr->c3 * ex3 + pr->c1 * m + pr->kappa * M + pr->c0;
+      dv[i] = 2.0 * (-pr->c3 * cov3 + pr->c1 * v) + pr->B * pr->B * v + eb * eb;
+    }
   }
 }
-
 void orc_coarse(const orc_problem* pr, const orc_macro* in, orc_macro* out) {
   const int I = pr->n_regions < 2 ? 1 : pr->n_regions;
   const int nc = orc_coarse_steps(pr);

@@ -57,7 +57,17 @@ typedef struct {
   uint32_t problem_tag;
   double tol;                 /* stop when max_n |d(M,V)| < tol */
   int max_iter;               /* at most this many fine sweeps (<= N) */
+  int coarse_model;           /* ORC_COARSE_CLOSURE / _TAYLOR / _SIGMA2 / _SIGMA3 */
 } orc_problem;
+
+/* Coarse moment models (Sec. 2): the Gaussian closure (expectations of the
+ * polynomial coefficients under N(M, Sigma) in closed form), the Taylor
+ * model (Eq. moment_model_class_1), and the Gaussian-assumed density
+ * (Eq. Gaussian_model_McK_V_SDE) with a 2- or 3-point sigma-point rule. */
+#define ORC_COARSE_CLOSURE 0
+#define ORC_COARSE_TAYLOR 1
+#define ORC_COARSE_SIGMA2 2
+#define ORC_COARSE_SIGMA3 3
 
 /* Restriction of one ensemble (Eq. multimodal_R plus the extremes needed by
  * the "fractions unchanged" test of Def. 3.2). */

@@ -44,7 +44,7 @@ class OrcProblem(C.Structure):
         ("T", C.c_double), ("N", C.c_int), ("dt", C.c_double), ("P", C.c_longlong),
         ("coarse_h", C.c_double), ("n_regions", C.c_int), ("threshold", C.c_double),
         ("variant", C.c_int), ("seed", C.c_uint64), ("problem_tag", C.c_uint32),
-        ("tol", C.c_double), ("max_iter", C.c_int),
+        ("tol", C.c_double), ("max_iter", C.c_int), ("coarse_model", C.c_int),
     ]
 
 
@@ -126,6 +126,7 @@ def problem(p) -> OrcProblem:
     return OrcProblem(
         p.c3, p.c1, p.kappa, p.c0, p.B, p.BE, p.B0, p.m0, p.s0, p.T, p.N, p.dt, p.P,
         p.coarse_h, p.n_regions, p.threshold, p.variant, p.seed, p.problem_tag, p.tol, max_iter,
+        p.coarse_model,
     )
 
 

@@ -138,6 +138,7 @@ int validate(const mmp_problem_desc& d) {
   if (d.n_regions < 1 || d.n_regions > 2) return MMP_ERR_INVALID_ARG;
   if (d.variant < MMP_UNIMODAL || d.variant > MMP_LEARNING) return MMP_ERR_INVALID_ARG;
   if (d.precision != MMP_FP64 && d.precision != MMP_MIXED) return MMP_ERR_INVALID_ARG;
+  if (d.coarse_model < MMP_COARSE_CLOSURE || d.coarse_model > MMP_COARSE_SIGMA3) return MMP_ERR_INVALID_ARG;
   const double steps = std::ceil((d.T / d.N) / d.dt - 1e-9);
   if (!(steps >= 1) || steps > 2e9) return MMP_ERR_INVALID_ARG;
   const double csteps = std::ceil((d.T / d.N) / d.coarse_h - 1e-9);
@@ -457,6 +458,7 @@ DriverArgs make_driver_args(const Prob& p, int sweep) {
   a.nc3 = -d.c3; a.c1 = d.c1; a.kappa = d.kappa; a.c0 = d.c0;
   a.B = d.B; a.BE = d.BE; a.B0 = d.B0;
   a.N = d.N; a.I = p.I; a.variant = d.variant; a.precision = d.precision;
+  a.coarse_model = d.coarse_model;
   a.dT = p.dT; a.hc = p.hc; a.nc = p.nc; a.thr = d.threshold; a.P = d.P;
   a.tol = d.tol; a.max_sweeps = p.max_sweeps;
   a.stats = p.stats; a.stats_u0 = p.stats_u0; a.rho = p.rho; a.cache = p.cache; a.aff = p.aff;
@@ -1702,7 +1704,8 @@ unsigned long long state_digest(const mmp_ctx* c) {
     const double dv[] = {d.c3, d.c1, d.kappa, d.c0, d.B, d.BE, d.B0, d.m0, d.s0, d.T, d.dt, d.coarse_h,
                          d.threshold, d.tol};
     const long long iv[] = {d.N, d.P, d.n_regions, d.variant, d.precision, (long long)d.seed,
-                            (long long)d.problem_tag, d.max_iter, p.layout, p.nq, p.G, p.slots_max};
+                            (long long)d.problem_tag, d.max_iter, d.coarse_model, p.layout, p.nq, p.G,
+                            p.slots_max};
     h = fnv(h, dv, sizeof(dv));
     h = fnv(h, iv, sizeof(iv));
   }

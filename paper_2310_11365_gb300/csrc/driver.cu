@@ -44,27 +44,74 @@ __device__ void macro_store(const DriverArgs& a, double* r, const Macro& m) {
   r[7] = V;
 }
 
-// Coarse propagator C_n: Gaussian-closure moment ODE per region with the
-// fractions frozen (Def. 3.2), forward Euler with nc substeps.  For c3 = 0
-// it is the Taylor model of Eq. (moment_model_class_1), exact for linear
-// SDEs (Lemma 2.1).  Per region i with M = sum_j P_j m_j:
-//   m' = -c3 (m^3 + 3 m v) + c1 m + kappa M + c0
-//   v' = 2 (-3 c3 v (m^2 + v) + c1 v) + B^2 v + (B m + BE M + B0)^2
+// Coarse propagator C_n: a moment ODE per region with the fractions frozen
+// (Def. 3.2), forward Euler with nc substeps, the mean field M = sum_j P_j m_j
+// (the region's own mean when I = 1).  Models (Sec. 2), for the drift
+// a(x) = -c3 x^3 + c1 x + kappa M + c0 and diffusion b(x) = B x + BE M + B0:
+//   closure (Gaussian-assumed density, expectations in closed form):
+//     m' = -c3 (m^3 + 3 m v) + c1 m + kappa M + c0
+//     v' = 2 (-3 c3 v (m^2 + v) + c1 v) + B^2 v + (B m + BE M + B0)^2
+//   Taylor (Eq. moment_model_class_1): m' = a(m) + a_XX(m) v / 2,
+//     v' = (2 a_X(m) + B^2) v + b(m)^2
+//   sigma-point (Eq. Gaussian_model_McK_V_SDE with a k-point rule on
+//     N(m, v)): m' = E[a], v' = 2 E[(X - m) a] + E[b^2]; k = 2: m -+ sqrt(v),
+//     weights 1/2; k = 3: m, m -+ sqrt(3 v), weights 2/3, 1/6, 1/6.
+// For c3 = 0 every model is the exact moment ODE of the linear SDE (Lemma 2.1).
+__device__ double drift_at(const DriverArgs& a, double x, double M) {
+  return a.nc3 * x * x * x + a.c1 * x + a.kappa * M + a.c0;
+}
+__device__ double diffusion_at(const DriverArgs& a, double x, double M) {
+  return a.B * x + a.BE * M + a.B0;
+}
+
+__device__ void coarse_rhs(const DriverArgs& a, double m, double v, double M, double& dm, double& dv) {
+  const double c3 = -a.nc3;
+  if (a.coarse_model == MMP_COARSE_TAYLOR) {
+    const double ax = -3.0 * c3 * m * m + a.c1;
+    const double axx = -6.0 * c3 * m;
+    const double b = diffusion_at(a, m, M);
+    dm = drift_at(a, m, M) + 0.5 * axx * v;
+    dv = (2.0 * ax + a.B * a.B) * v + b * b;
+  } else if (a.coarse_model == MMP_COARSE_SIGMA2 || a.coarse_model == MMP_COARSE_SIGMA3) {
+    double xs[3], ws[3];
+    int k;
+    if (a.coarse_model == MMP_COARSE_SIGMA2) {
+      const double d = sqrt(v > 0.0 ? v : 0.0);
+      xs[0] = m - d; xs[1] = m + d;
+      ws[0] = 0.5; ws[1] = 0.5;
+      k = 2;
+    } else {
+      const double d = sqrt(3.0 * (v > 0.0 ? v : 0.0));
+      xs[0] = m; xs[1] = m - d; xs[2] = m + d;
+      ws[0] = 2.0 / 3.0; ws[1] = 1.0 / 6.0; ws[2] = 1.0 / 6.0;
+      k = 3;
+    }
+    double ea = 0.0, exa = 0.0, eb2 = 0.0;
+    for (int s = 0; s < k; ++s) {
+      const double av = drift_at(a, xs[s], M);
+      const double bv = diffusion_at(a, xs[s], M);
+      ea += ws[s] * av;
+      exa += ws[s] * (xs[s] - m) * av;
+      eb2 += ws[s] * bv * bv;
+    }
+    dm = ea;
+    dv = 2.0 * exa + eb2;
+  } else {
+    const double ex3 = m * m * m + 3.0 * m * v;
+    const double cov3 = 3.0 * v * (m * m + v);
+    const double eb = a.B * m + a.BE * M + a.B0;
+    dm = -c3 * ex3 + a.c1 * m + a.kappa * M + a.c0;
+    dv = 2.0 * (-c3 * cov3 + a.c1 * v) + a.B * a.B * v + eb * eb;
+  }
+}
+
 __device__ void coarse(const DriverArgs& a, const Macro& in, Macro& out) {
   out = in;
-  const double c3 = -a.nc3;
   for (int s = 0; s < a.nc; ++s) {
     double M = out.mean[0];
     if (a.I > 1) M = out.frac[0] * out.mean[0] + out.frac[1] * out.mean[1];
     double dm[2], dv[2];
-    for (int i = 0; i < a.I; ++i) {
-      const double m = out.mean[i], v = out.var[i];
-      const double ex3 = m * m * m + 3.0 * m * v;
-      const double cov3 = 3.0 * v * (m * m + v);
-      const double eb = a.B * m + a.BE * M + a.B0;
-      dm[i] = -c3 * ex3 + a.c1 * m + a.kappa * M + a.c0;
-      dv[i] = 2.0 * (-c3 * cov3 + a.c1 * v) + a.B * a.B * v + eb * eb;
-    }
+    for (int i = 0; i < a.I; ++i) coarse_rhs(a, out.mean[i], out.var[i], M, dm[i], dv[i]);
     for (int i = 0; i < a.I; ++i) {
       out.mean[i] = out.mean[i] + a.hc * dm[i];
       out.var[i] = out.var[i] + a.hc * dv[i];

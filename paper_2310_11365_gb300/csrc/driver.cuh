@@ -8,6 +8,7 @@ namespace mmp {
 struct DriverArgs {
   double nc3, c1, kappa, c0, B, BE, B0;  // model (nc3 = -c3)
   int N, I, variant, precision;
+  int coarse_model;                      // MMP_COARSE_*
   double dT, hc;                         // slice length, coarse substep
   int nc;                                // coarse substeps per slice
   double thr;

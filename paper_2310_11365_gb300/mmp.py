@@ -58,7 +58,7 @@ class ProblemDesc(C.Structure):
         ("T", C.c_double), ("N", C.c_int), ("dt", C.c_double), ("P", C.c_longlong),
         ("coarse_h", C.c_double), ("n_regions", C.c_int), ("threshold", C.c_double),
         ("variant", C.c_int), ("precision", C.c_int), ("seed", C.c_ulonglong),
-        ("problem_tag", C.c_uint), ("tol", C.c_double), ("max_iter", C.c_int),
+        ("problem_tag", C.c_uint), ("tol", C.c_double), ("max_iter", C.c_int), ("coarse_model", C.c_int),
     ]
 
 
@@ -127,7 +127,7 @@ def desc(p: workloads.Problem) -> ProblemDesc:
     prec = MMP_MIXED if p.precision == "mixed" else MMP_FP64
     return ProblemDesc(p.c3, p.c1, p.kappa, p.c0, p.B, p.BE, p.B0, p.m0, p.s0, p.T, p.N, p.dt, p.P,
                        p.coarse_h, p.n_regions, p.threshold, p.variant, prec, p.seed, p.problem_tag,
-                       p.tol, p.max_iter)
+                       p.tol, p.max_iter, p.coarse_model)
 
 
 def _descs(problems) -> C.Array:

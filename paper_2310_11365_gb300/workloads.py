@@ -27,6 +27,7 @@ from dataclasses import dataclass, replace
 import numpy as np
 
 UNIMODAL, MULTIMODAL, LEARNING = 0, 1, 2
+CLOSURE, TAYLOR, SIGMA2, SIGMA3 = 0, 1, 2, 3  # coarse moment models
 SEED_BASE = 0x231011365
 
 
@@ -54,6 +55,7 @@ class Problem:
     tol: float = 1e-8
     max_iter: int = 0          # 0 means N
     precision: str = "fp64"    # "fp64" or "mixed" (FP32 particles)
+    coarse_model: int = 0      # CLOSURE, TAYLOR, SIGMA2 or SIGMA3
 
     def scaled(self, **kw) -> "Problem":
         return replace(copy.copy(self), **kw)
