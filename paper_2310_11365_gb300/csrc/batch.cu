@@ -16,9 +16,12 @@
 
 namespace mmp {
 
-// Four CTAs per SM (64 registers a thread): a batch holds many small tasks
-// whose CTAs are far from filling shared memory.
-constexpr int kBatchOcc = 4;
+// Two CTAs per SM, 128 registers a thread and four quads in flight, as the
+// per-problem kernel: the batch sizes its shared memory for the largest
+// quads-per-thread count of its problems, which at the measured caps (~27)
+// leaves room for two CTAs per SM anyway (sized for four, the kernel spilled
+// and ran config 5 11 % slower).
+constexpr int kBatchOcc = 2;
 
 template <typename R, bool MULT>
 __global__ void __launch_bounds__(kTPB, kBatchOcc) k_fine_batch(const BatchArgs b) {
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(kTPB, kBatchOcc) k_fine_batch(const BatchArgs 
     grp.G = tk.G;
     grp.g = s_rank;
     grp.epoch = 0;
-    if (!fine_task<R, 0, MULT, 2>(sa, tk.slice, s_rank, grp, sh, xs)) return;
+    if (!fine_task<R, 0, MULT, kStepUnrollSmem>(sa, tk.slice, s_rank, grp, sh, xs)) return;
     __syncthreads();  // every thread is done with sa and s_task
   }
 }
