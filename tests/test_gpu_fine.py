@@ -39,7 +39,7 @@ def _check_stats(st, ref, P, rtol):
     assert abs(st[11] - ref["gvar"]) <= rtol * max(ref["gvar"], 1e-300)
 
 
-@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 257, 1000, 4097, 50_001, 400_003])
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 6, 257, 1000, 4097, 50_001, 123_458, 400_002, 400_003])
 def test_fine_fp64_matches_oracle(mmplib, orc, P):
     p = W.config2(P=P, N=8, T=0.4, dt=2e-3, precision="fp64", m0=0.3, s0=0.5)  # n_f = 25
     u0 = orc.initial(p)
@@ -65,7 +65,7 @@ def test_fine_fp64_multimodal_and_multiplicative(mmplib, orc):
         assert abs(st[k] - ref) <= 1e-12 * max(1.0, abs(ref))
 
 
-@pytest.mark.parametrize("P", [999, 200_001])
+@pytest.mark.parametrize("P", [999, 200_001, 200_002, 200_003])
 def test_fine_mixed_within_bounds(mmplib, orc, P):
     """FP32 particles on the same draws as the FP64 oracle: per-particle and
     moment errors stay inside the stated mixed-precision bounds."""
