@@ -667,21 +667,25 @@ void orc_fine_serial(const orc_problem* pr, const double* u0_in, orc_stats* stat
 /* ------------------------------------------------------------------------
  * Adjoint of the serial fine propagator F_{N-1} o ... o F_0 (the limit the
  * Parareal iteration reproduces, Property 3.3).  Reverse-mode
- * differentiation of the Euler-Maruyama recursion of Sec. 1.2 with the mean
- * field m_j = (1/P) sum_q x_{j,q}:
- *   d x_{j+1,p} / d x_{j,q} = delta_pq (1 + h a_x(x_{j,p})) + h kappa / P,
+ * differentiation of the Euler-Maruyama recursion of Sec. 1.2,
+ *   x_{j+1,p} = x_{j,p} + h a(x_{j,p}, m_j) + sqrt(h) b(x_{j,p}, m_j) xi_{j,p},
+ * with the mean field m_j = (1/P) sum_q x_{j,q}, a = -c3 x^3 + c1 x + kappa m + c0
+ * and b = B x + BE m + B0:
+ *   d x_{j+1,p} / d x_{j,q} = delta_pq (1 + h a_x(x_{j,p}) + sqrt(h) B xi_{j,p})
+ *                             + (h kappa + sqrt(h) BE xi_{j,p}) / P,
  *   a_x(x) = -3 c3 x^2 + c1,
- * so with lambda_j = dL/dx_j:
- *   lambda_{j,q} = lambda_{j+1,q} (1 + h a_x(x_{j,q})) + (h kappa / P) sum_p lambda_{j+1,p}
- *                  + [loss at x_j]
+ * so with lambda_j = dL/dx_j, S_j = sum_p lambda_{j+1,p} and
+ * Z_j = sum_p lambda_{j+1,p} xi_{j,p}:
+ *   lambda_{j,q} = lambda_{j+1,q} (1 + h a_x(x_{j,q}) + sqrt(h) B xi_{j,q})
+ *                  + (h kappa S_j + sqrt(h) BE Z_j) / P + [loss at x_j]
  * and the explicit parameter derivatives of step j are
- *   d/dc3 = -h x^3, d/dc1 = h x, d/dkappa = h m_j, d/dc0 = h, d/dB0 = sqrt(h) xi.
+ *   d/dc3 = -h x^3, d/dc1 = h x, d/dkappa = h m_j, d/dc0 = h,
+ *   d/dB0 = sqrt(h) xi, d/dB = sqrt(h) x xi, d/dBE = sqrt(h) m_j xi.
  * The loss at slice end n injects gm/P + gv (2/P)(x - M_n)
  * (dV/dx_q = (2/P)(x_q - M) for the population variance).
  * ---------------------------------------------------------------------- */
 int orc_adjoint(const orc_problem* pr, const double* u0_in, const double* gm, const double* gv,
-                double grad[5], double* moments) {
-  if (pr->B != 0.0 || pr->BE != 0.0) return -1;
+                double grad[ORC_N_THETA], double* moments) {
   const long long P = pr->P;
   const int N = pr->N;
   const int nf = orc_fine_steps(pr);
@@ -719,7 +723,7 @@ int orc_adjoint(const orc_problem* pr, const double* u0_in, const double* gm, co
     }
   }
   /* reverse */
-  for (int k = 0; k < 5; ++k) grad[k] = 0.0;
+  for (int k = 0; k < ORC_N_THETA; ++k) grad[k] = 0.0;
   for (long long j = J - 1; j >= 0; --j) {
     if ((j + 1) % nf == 0) {
       const int n = (int)((j + 1) / nf);
@@ -729,7 +733,7 @@ int orc_adjoint(const orc_problem* pr, const double* u0_in, const double* gm, co
     }
     const double* x = X + (size_t)j * P;
     const int n = (int)(j / nf), js = (int)(j % nf);
-    double S = 0.0;
+    double S = 0.0, Z = 0.0;
     for (long long p = 0; p < P; ++p) {
       const double xv = x[p];
       const double xi = orc_normal(pr, 0, (uint32_t)js, (uint32_t)n, p);
@@ -738,12 +742,17 @@ int orc_adjoint(const orc_problem* pr, const double* u0_in, const double* gm, co
       grad[2] += lam[p] * (h * m[j]);
       grad[3] += lam[p] * h;
       grad[4] += lam[p] * (sqrt_h * xi);
+      grad[5] += lam[p] * (sqrt_h * xv * xi);
+      grad[6] += lam[p] * (sqrt_h * m[j] * xi);
       S += lam[p];
+      Z += lam[p] * xi;
     }
+    const double shift = (h * pr->kappa * S + sqrt_h * pr->BE * Z) / (double)P;
     for (long long p = 0; p < P; ++p) {
       const double xv = x[p];
+      const double xi = orc_normal(pr, 0, (uint32_t)js, (uint32_t)n, p);
       const double ax = -3.0 * pr->c3 * xv * xv + pr->c1;
-      lam[p] = lam[p] * (1.0 + h * ax) + (h * pr->kappa / (double)P) * S;
+      lam[p] = lam[p] * (1.0 + h * ax + sqrt_h * pr->B * xi) + shift;
     }
   }
   free(X); free(m); free(lam); free(Mn); free(Vn);
@@ -751,7 +760,7 @@ int orc_adjoint(const orc_problem* pr, const double* u0_in, const double* gm, co
 }
 
 int orc_adjoint_loss(const orc_problem* pr, const double* u0_in, const double* m_tgt,
-                     const double* v_tgt, double grad[5], double* loss) {
+                     const double* v_tgt, double grad[ORC_N_THETA], double* loss) {
   const int N = pr->N;
   double* mom = (double*)malloc(sizeof(double) * 2 * (size_t)(N + 1));
   double* gm = (double*)calloc((size_t)N, sizeof(double));

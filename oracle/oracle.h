@@ -153,18 +153,19 @@ int orc_parareal(const orc_problem* pr, const double* u0_in, double* hist, orc_m
 void orc_fine_serial(const orc_problem* pr, const double* u0_in, orc_stats* stats, double* parts);
 
 /* -- adjoint of the serial fine propagator ------------------------------ */
+#define ORC_N_THETA 7
 /* Gradient of L = sum_{n=1..N} gm[n-1] M_n + gv[n-1] V_n, where (M_n, V_n)
  * are the mean and population variance of the serial fine run at slice end
- * n, with respect to theta = (c3, c1, kappa, c0, B0), by the discrete
- * adjoint of the Euler-Maruyama recursion on the same draws (additive noise
- * only: B = BE = 0).  Stores the whole trajectory (P (N n_f + 1) doubles).
- * moments (optional) receives (M_n, V_n), n = 0..N.  Returns 0, or -1 for
- * multiplicative noise. */
+ * n, with respect to theta = (c3, c1, kappa, c0, B0, B, BE), by the discrete
+ * adjoint of the Euler-Maruyama recursion on the same draws (additive,
+ * state-proportional and mean-field diffusion alike).  Stores the whole
+ * trajectory (P (N n_f + 1) doubles).  moments (optional) receives
+ * (M_n, V_n), n = 0..N.  Returns 0. */
 int orc_adjoint(const orc_problem* pr, const double* u0_in, const double* gm, const double* gv,
-                double grad[5], double* moments);
+                double grad[ORC_N_THETA], double* moments);
 /* L = sum_n (M_n - m_tgt[n-1])^2 + (V_n - v_tgt[n-1])^2 and its gradient. */
 int orc_adjoint_loss(const orc_problem* pr, const double* u0_in, const double* m_tgt,
-                     const double* v_tgt, double grad[5], double* loss);
+                     const double* v_tgt, double grad[ORC_N_THETA], double* loss);
 
 #ifdef __cplusplus
 }

@@ -302,30 +302,33 @@ def fine_serial(p, u0: np.ndarray | None = None, want_parts: bool = False) -> di
     return out
 
 
+N_THETA = 7  # (c3, c1, kappa, c0, B0, B, BE)
+
+
 def adjoint(p, gm, gv, u0: np.ndarray | None = None):
     """Gradient of sum_n gm[n] M_n + gv[n] V_n (n = 1..N) w.r.t.
-    (c3, c1, kappa, c0, B0), and the moments (M_n, V_n), n = 0..N."""
+    (c3, c1, kappa, c0, B0, B, BE), and the moments (M_n, V_n), n = 0..N."""
     pr = problem(p)
     gma = np.ascontiguousarray(gm, dtype=np.float64)
     gva = np.ascontiguousarray(gv, dtype=np.float64)
-    grad = np.zeros(5)
+    grad = np.zeros(N_THETA)
     mom = np.zeros(2 * (p.N + 1))
     u0a = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64)
     rc = lib().orc_adjoint(C.byref(pr), _dp(u0a), _dp(gma), _dp(gva), _dp(grad), _dp(mom))
     if rc != 0:
-        raise ValueError("adjoint needs additive noise")
+        raise ValueError(f"orc_adjoint returned {rc}")
     return grad, mom.reshape(p.N + 1, 2)
 
 
 def adjoint_loss(p, m_tgt, v_tgt, u0: np.ndarray | None = None):
-    """L = sum_n (M_n - m*_n)^2 + (V_n - v*_n)^2 and dL/d(c3, c1, kappa, c0, B0)."""
+    """L = sum_n (M_n - m*_n)^2 + (V_n - v*_n)^2 and dL/d(c3, c1, kappa, c0, B0, B, BE)."""
     pr = problem(p)
     mt = np.ascontiguousarray(m_tgt, dtype=np.float64)
     vt = np.ascontiguousarray(v_tgt, dtype=np.float64)
-    grad = np.zeros(5)
+    grad = np.zeros(N_THETA)
     L = C.c_double()
     u0a = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64)
     rc = lib().orc_adjoint_loss(C.byref(pr), _dp(u0a), _dp(mt), _dp(vt), _dp(grad), C.byref(L))
     if rc != 0:
-        raise ValueError("adjoint needs additive noise")
+        raise ValueError(f"orc_adjoint_loss returned {rc}")
     return L.value, grad

@@ -1,13 +1,14 @@
 """Pins of the oracle's adjoint of the serial fine propagator: central
-differences with common random numbers, the Taylor remainder, and closed
-forms of the linear model's mean."""
+differences with common random numbers (additive, state-proportional and
+mean-field diffusion), the Taylor remainder, and closed forms of the linear
+model's mean."""
 import math
 
 import numpy as np
 
 from paper_2310_11365_gb300 import workloads as W
 
-PARAMS = ("c3", "c1", "kappa", "c0", "B0")
+PARAMS = ("c3", "c1", "kappa", "c0", "B0", "B", "BE")
 
 
 def _loss(orc, p, m_tgt, v_tgt):
@@ -15,12 +16,7 @@ def _loss(orc, p, m_tgt, v_tgt):
     return float(np.sum((ser["gmean"][1:] - m_tgt) ** 2 + (ser["gvar"][1:] - v_tgt) ** 2))
 
 
-def test_adjoint_matches_central_differences(orc):
-    """Double-well model, same draws in every evaluation: the adjoint
-    gradient of L = sum (M-m*)^2 + (V-v*)^2 equals central differences
-    (h = 1e-5) to 1e-6 relative in every parameter."""
-    p = W.double_well(0.25, 0.5, 0.1, 0.7, m0=0.2, s0=0.5, T=1.0, N=4, dt=0.01, P=301, seed=17)
-    ref = W.double_well(0.25, 0.5, 0.15, 0.65, m0=0.2, s0=0.5, T=1.0, N=4, dt=0.01, P=301, seed=18)
+def _check_central_differences(orc, p, ref):
     st = orc.fine_serial(ref)
     m_tgt, v_tgt = st["gmean"][1:], st["gvar"][1:]
     L, g = orc.adjoint_loss(p, m_tgt, v_tgt)
@@ -33,13 +29,35 @@ def test_adjoint_matches_central_differences(orc):
         assert abs(g[k] - fd) <= 1e-6 * max(abs(fd), 1e-8), (name, g[k], fd)
 
 
+def test_adjoint_matches_central_differences(orc):
+    """Double-well model with additive noise, same draws in every
+    evaluation: the adjoint gradient of L = sum (M-m*)^2 + (V-v*)^2 equals
+    central differences (h = 1e-5) to 1e-6 relative in every coefficient,
+    the diffusion's B and BE (zero here) included."""
+    p = W.double_well(0.25, 0.5, 0.1, 0.7, m0=0.2, s0=0.5, T=1.0, N=4, dt=0.01, P=301, seed=17)
+    ref = W.double_well(0.25, 0.5, 0.15, 0.65, m0=0.2, s0=0.5, T=1.0, N=4, dt=0.01, P=301, seed=18)
+    _check_central_differences(orc, p, ref)
+
+
+def test_adjoint_general_diffusion_central_differences(orc):
+    """Cubic drift with b = B x + BE E[X] + B0 (state-proportional and
+    mean-field noise, Sec. 2's general diffusion): the reverse recursion's
+    noise terms (sqrt(h) B xi on the diagonal, sqrt(h) BE xi / P in the
+    mean-field column) agree with central differences in all seven
+    coefficients."""
+    p = W.Problem(c3=0.6, c1=-0.4, kappa=0.5, c0=0.1, B=0.3, BE=-0.25, B0=0.35, m0=0.4, s0=0.3,
+                  T=1.0, N=4, dt=0.01, P=257, seed=29)
+    ref = p.scaled(kappa=0.7, B=0.2, BE=0.1, seed=30)
+    _check_central_differences(orc, p, ref)
+
+
 def test_adjoint_taylor_remainder(orc):
     """L(theta + eps d) - L(theta) - eps grad.d shrinks like eps^2."""
-    p = W.cubic(1.0, 0.5, m0=0.5, s0=0.2, T=1.0, N=4, dt=0.01, P=257, seed=5)
+    p = W.cubic(1.0, 0.5, m0=0.5, s0=0.2, T=1.0, N=4, dt=0.01, P=257, seed=5).scaled(B=0.2, BE=0.1)
     m_tgt = np.full(p.N, 0.3)
     v_tgt = np.full(p.N, 0.05)
     L0, g = orc.adjoint_loss(p, m_tgt, v_tgt)
-    d = np.array([0.3, -0.7, 0.5, 0.2, -0.4])
+    d = np.array([0.3, -0.7, 0.5, 0.2, -0.4, 0.25, -0.35])
     rem = []
     for eps in (1e-2, 5e-3):
         q = p.scaled(**{name: getattr(p, name) + eps * d[k] for k, name in enumerate(PARAMS)})
