@@ -358,7 +358,7 @@ def config4_run() -> dict:
            "forward_particle_steps_per_s": J * p.P / (f_ms / 1e3),
            "backward_particle_steps_per_s": J * p.P / (b_ms / 1e3),
            "loss": float(np.sum(gm ** 2 + gv ** 2) / 4.0),
-           "grad_c3_c1_kappa_c0_B0": [float(x) for x in grad]}
+           "grad_c3_c1_kappa_c0_B0_B_BE": [float(x) for x in grad]}
     s.close()
     return out
 

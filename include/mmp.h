@@ -179,16 +179,22 @@ int mmp_get_plan(mmp_ctx* ctx, int prob, int* quads_per_thread, int* ctas_per_sl
                  int* max_concurrent_slices, int* particles_in_shared);
 
 /* Replace problem `prob`'s drift and diffusion coefficients by
- * theta = (c3, c1, kappa, c0, B0) (host, 5 doubles, finite).  The launch
- * shape does not depend on them, so nothing is re-planned; a recorded
- * adjoint forward run is invalidated. */
-int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta);
+ * theta = (c3, c1, kappa, c0, B0) (n_theta = 5; B and BE unchanged) or
+ * (c3, c1, kappa, c0, B0, B, BE) (n_theta = 7); host doubles, finite, else
+ * MMP_ERR_INVALID_ARG.  The launch shape does not depend on them, so nothing
+ * is re-planned.  Making B or BE nonzero (or both zero) switches the fine
+ * kernel between its additive-noise and general forms: MMP_ERR_UNSUPPORTED
+ * (nothing changed) in a batched context or if the other form does not fit
+ * the problem's launch shape.  A recorded adjoint forward run is
+ * invalidated. */
+int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta, int n_theta);
 
 /* Adjoint of the serial fine propagator F_{N-1} o ... o F_0 (the run the
  * Parareal iteration converges to exactly, Property 3.3).  The paper has no
  * adjoint; this is the reverse mode of its Euler-Maruyama recursion
- * (Sec. 1.2), mean-field coupling included, for calibrating the model
- * coefficients to moment targets.
+ * (Sec. 1.2) with drift a = -c3 x^3 + c1 x + kappa m + c0 and diffusion
+ * b = B x + BE m + B0, mean-field coupling included, for calibrating the
+ * model coefficients to moment targets.
  *
  * mmp_adjoint_workspace_size: bytes of caller-owned device workspace for a
  * checkpoint every `ckpt_every` fine steps: one particle row per checkpoint,
@@ -198,15 +204,19 @@ int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta);
  * mmp_adjoint_forward: runs the serial fine propagation from u0 with the
  * current coefficients, recording checkpoints and per-step mean-field values
  * into `ws`; writes the slice-end moments (M_n, V_n), n = 0..N, to host
- * `moments_out` [(N+1) * 2] (may be NULL).  Synchronising.  Additive noise
- * only (B = BE = 0), else MMP_ERR_UNSUPPORTED.
+ * `moments_out` [(N+1) * 2] (may be NULL).  Synchronising.
  *
  * mmp_adjoint_backward: given cotangents gm[n-1] = dL/dM_n, gv[n-1] = dL/dV_n
- * for n = 1..N (host, N doubles each), writes dL/d(c3, c1, kappa, c0, B0)
- * to host `grad_out` [5].  Needs the workspace of the last forward run of
- * this problem (else MMP_ERR_STATE).  Each segment of ckpt_every steps is
- * recomputed from its checkpoint with the same draws, then reversed with one
- * group sum of the adjoint per step.  Synchronising. */
+ * for n = 1..N (host, N doubles each), writes
+ * dL/d(c3, c1, kappa, c0, B0, B, BE) to host `grad_out` [MMP_N_THETA]
+ * (the derivatives in B and BE are those at the current values, zero
+ * included).  Needs the workspace of the last forward run of this problem
+ * (else MMP_ERR_STATE).  Each segment of ckpt_every steps is recomputed
+ * from its checkpoint with the same draws, then reversed with one group
+ * exchange of the adjoint per step (one sum for additive noise; with B or
+ * BE nonzero also the sums that form Z_j = sum_p lambda_{j+1,p} xi_{j,p}).
+ * Synchronising. */
+#define MMP_N_THETA 7
 int mmp_adjoint_workspace_size(mmp_ctx* ctx, int prob, int ckpt_every, size_t* bytes);
 int mmp_adjoint_forward(mmp_ctx* ctx, int prob, int ckpt_every, void* ws, size_t ws_bytes,
                         double* moments_out);

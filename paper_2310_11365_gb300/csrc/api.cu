@@ -16,6 +16,7 @@
 #include "fine.cuh"
 #include "misc.cuh"
 #include "mmp_internal.cuh"
+static_assert(mmp::kNGrad == MMP_N_THETA, "adjoint gradient length");
 
 namespace mmp {
 const void* fine_kernel_f32(int nq, bool mult);
@@ -763,7 +764,7 @@ struct AdjLayout {
 int adjoint_layout(mmp_ctx* c, Prob& p, int ckpt_every, char* base, AdjLayout& L) {
   const long long J = (long long)p.d.N * p.nf;
   L.n_seg = (int)((J + ckpt_every - 1) / ckpt_every);
-  const void* fn = adjoint_kernel(p.d.precision);
+  const void* fn = adjoint_kernel(p.d.precision, p.mult);
   size_t limit = 0;
   const int arc = allow_dynamic_smem(fn, c->dev.dev, &limit);
   if (arc) return arc;
@@ -1170,18 +1171,41 @@ int mmp_fine_serial(mmp_ctx* ctx, int prob, int n_end, double* stats_out, void* 
   return status_to_error(st[0]);
 }
 
-int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta) {
+int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta, int n_theta) {
   int rc = check_prob(ctx, prob);
   if (rc) return rc;
-  if (theta == nullptr) return MMP_ERR_INVALID_ARG;
-  for (int k = 0; k < 5; ++k)
+  if (theta == nullptr || (n_theta != 5 && n_theta != 7)) return MMP_ERR_INVALID_ARG;
+  for (int k = 0; k < n_theta; ++k)
     if (!std::isfinite(theta[k])) return MMP_ERR_INVALID_ARG;
   Prob& p = ctx->probs[prob];
+  const double B = n_theta == 7 ? theta[5] : p.d.B;
+  const double BE = n_theta == 7 ? theta[6] : p.d.BE;
+  const bool mult = B != 0.0 || BE != 0.0;
+  if (mult != p.mult) {
+    // the fine kernel changes form: a batch shares one form, and a single
+    // problem keeps its launch shape only if the other form fits it too
+    if (ctx->batch) return MMP_ERR_UNSUPPORTED;
+    const void* fn = fine_kernel(p.d.precision, p.layout, p.nq, mult);
+    if (fn == nullptr) return MMP_ERR_UNSUPPORTED;
+    const size_t smem = fine_smem_bytes(p.d.precision, p.layout, p.nq);
+    if (p.layout == kLayoutSmem) {
+      size_t limit = 0;
+      rc = allow_dynamic_smem(fn, ctx->dev.dev, &limit);
+      if (rc) return rc;
+      if (smem > limit) return MMP_ERR_UNSUPPORTED;
+    }
+    int occ = 0;
+    MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, smem));
+    if ((long long)occ * ctx->dev.sms < (long long)p.slots_max * p.G) return MMP_ERR_UNSUPPORTED;
+  }
   p.d.c3 = theta[0];
   p.d.c1 = theta[1];
   p.d.kappa = theta[2];
   p.d.c0 = theta[3];
   p.d.B0 = theta[4];
+  p.d.B = B;
+  p.d.BE = BE;
+  p.mult = mult;
   p.adj_ready = false;
   return MMP_OK;
 }
@@ -1203,7 +1227,6 @@ int mmp_adjoint_forward(mmp_ctx* ctx, int prob, int ckpt_every, void* ws, size_t
   if (rc) return rc;
   if (ws == nullptr || ((uintptr_t)ws % kAlign) != 0 || ckpt_every < 1) return MMP_ERR_INVALID_ARG;
   Prob& p = ctx->probs[prob];
-  if (p.mult) return MMP_ERR_UNSUPPORTED;
   AdjLayout L;
   rc = adjoint_layout(ctx, p, ckpt_every, (char*)ws, L);
   if (rc) return rc;
@@ -1267,6 +1290,7 @@ int mmp_adjoint_backward(mmp_ctx* ctx, int prob, const double* gm, const double*
                            ctx->stream));
   AdjointArgs a;
   a.nc3 = -p.d.c3; a.c1 = p.d.c1; a.kappa = p.d.kappa; a.h = p.h; a.sqrt_h = p.sqrt_h;
+  a.B = p.d.B; a.BE = p.d.BE;
   a.nf = p.nf; a.J = (long long)N * p.nf; a.c = p.adj_ckpt_every; a.n_seg = L.n_seg;
   a.P = p.d.P; a.Q = p.Q; a.pitch = p.pitch;
   a.key0 = p.key0; a.key1 = p.key1; a.ptag = p.d.problem_tag;
@@ -1276,9 +1300,9 @@ int mmp_adjoint_backward(mmp_ctx* ctx, int prob, const double* gm, const double*
   a.partials = L.partials; a.flags = L.flags; a.tags = L.tags; a.status = p.status;
   a.wait_limit_ns = ctx->limit_ns;
   a.sms = ctx->dev.sms;
-  MMP_CUDA(launch_adjoint(p.d.precision, a, ctx->stream));
+  MMP_CUDA(launch_adjoint(p.d.precision, p.mult, a, ctx->stream));
   ctx->other_launches += 1;
-  MMP_CUDA(cudaMemcpyAsync(grad_out, L.grad, sizeof(double) * 5, cudaMemcpyDeviceToHost, ctx->stream));
+  MMP_CUDA(cudaMemcpyAsync(grad_out, L.grad, sizeof(double) * kNGrad, cudaMemcpyDeviceToHost, ctx->stream));
   MMP_CUDA(cudaStreamSynchronize(ctx->stream));
   unsigned stw[4];
   MMP_CUDA(cudaMemcpy(stw, p.status, sizeof(stw), cudaMemcpyDeviceToHost));

@@ -37,7 +37,8 @@ struct FineArgs {
   unsigned long long wait_limit_ns;
   int tight_polls = 0;         // polls before a group wait backs off (launches of <= 1 CTA per SM)
   // optional recording for the adjoint (serial runs only, one task):
-  void* rec_uni = nullptr;     // [global step][3] (m_j, h (kappa m_j + c0), B0 sqrt h), precision R
+  void* rec_uni = nullptr;     // [global step][3], precision R: (m_j, h (kappa m_j + c0), B0 sqrt h) in the
+                               // shift form, (m_j, kappa m_j + c0, (BE m_j + B0) sqrt h) in the general form
   void* rec_ckpt = nullptr;    // particle rows at global steps 0, c, 2c, ... (row gstep / c)
   int ckpt_every = 1;          // c
   long long step_offset = 0;   // global index of this slice's first step

@@ -622,6 +622,7 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   double m_in = 0.0;
   R d = (R)0;                  // shift form: the pending shift d_{j-1}
   R base = (R)0, boff = (R)0;  // general form: kappa m_j + c0, (BE m_j + B0) sqrt(h)
+  R mj = (R)0;                 // general form: m_j (recorded for the adjoint)
   if (!kLag || nf == 0) {
     if (warp == 0) {
       ST sum;
@@ -635,6 +636,7 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
     if (sh.abort) return false;
     const R m = (R)SS::mean(SS::gsum(sh, 1), inv_p, a.P);
     m_in = (double)m;
+    mj = m;
     base = fmaR(kap, m, c0r);
     boff = mulR(fmaR(ber, m, b0r), sqh);
   }
@@ -642,8 +644,17 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   // ---------------- Euler-Maruyama steps --------------------------------
   for (int j = 0; j < nf; ++j) {
     const long long gs = a.step_offset + j;
-    const bool ckpt = kLag && a.rec_ckpt != nullptr && gs % a.ckpt_every == 0;
+    const bool ckpt = a.rec_ckpt != nullptr && gs % a.ckpt_every == 0;
     R* ck_row = ckpt ? (R*)a.rec_ckpt + (size_t)(gs / a.ckpt_every) * a.pitch : nullptr;
+    if constexpr (!kLag) {
+      if (a.rec_uni != nullptr && g == 0 && tid == 0) {
+        // the adjoint replays step j from exactly these values
+        R* u = (R*)a.rec_uni + 3 * gs;
+        u[0] = mj;
+        u[1] = base;
+        u[2] = boff;
+      }
+    }
     R s = (R)0;
 #pragma unroll kStepUnroll
     for (int i = 0; i < loop_n; ++i) {
@@ -661,6 +672,7 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
           em_partial_pair(v[0], v[1], nr[0], c[0], sn[0], hn3, hc1, b0sq);
           em_partial_pair(v[2], v[3], nr[1], c[1], sn[1], hn3, hc1, b0sq);
         } else {
+          if (ckpt) Quad<R>::store(ck_row + 4 * (size_t)q, v);
           R z[4];
           normals4<R>(o, z);
 #pragma unroll
@@ -749,6 +761,7 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
       __syncthreads();
       if (sh.abort) return false;
       const R m = (R)SS::mean(SS::gsum(sh, j & 1), inv_p, a.P);
+      mj = m;
       base = fmaR(kap, m, c0r);
       boff = mulR(fmaR(ber, m, b0r), sqh);
     }

@@ -22,6 +22,7 @@ MMP_FP64, MMP_MIXED = 0, 1
 MMP_UNIMODAL, MMP_MULTIMODAL, MMP_LEARNING = 0, 1, 2
 MOMENT_STRIDE = 8
 STAT_STRIDE = 16
+N_THETA = 7         # MMP_N_THETA: (c3, c1, kappa, c0, B0, B, BE)
 
 ERRORS = {
     -1: "MMP_ERR_INVALID_ARG", -2: "MMP_ERR_WORKSPACE", -3: "MMP_ERR_UNSUPPORTED",
@@ -97,7 +98,7 @@ def load():
         "mmp_set_timing": ([vp, i], i),
         "mmp_timing": ([vp, i, d, C.POINTER(ll), d, C.POINTER(ll)], i),
         "mmp_fine_static": ([pd, i, vp, vp, vp, vp], i),
-        "mmp_set_params": ([vp, i, d], i),
+        "mmp_set_params": ([vp, i, d, i], i),
         "mmp_adjoint_workspace_size": ([vp, i, i, C.POINTER(C.c_size_t)], i),
         "mmp_adjoint_forward": ([vp, i, i, vp, C.c_size_t, d], i),
         "mmp_adjoint_backward": ([vp, i, d, d, vp, C.c_size_t, d], i),
@@ -306,8 +307,9 @@ def mmp_fine_static(p: workloads.Problem, n: int, u_in_ptr: int, u_out_ptr: int,
 
 
 def mmp_set_params(ctx, prob: int, theta) -> None:
-    t = np.ascontiguousarray(theta, dtype=np.float64)
-    _check(load().mmp_set_params(ctx, prob, t.ctypes.data_as(C.POINTER(C.c_double))), "mmp_set_params")
+    """theta = (c3, c1, kappa, c0, B0) or (c3, c1, kappa, c0, B0, B, BE)."""
+    t = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    _check(load().mmp_set_params(ctx, prob, t.ctypes.data_as(C.POINTER(C.c_double)), t.size), "mmp_set_params")
 
 
 def mmp_adjoint_workspace_size(ctx, prob: int, ckpt_every: int) -> int:
@@ -326,7 +328,7 @@ def mmp_adjoint_forward(ctx, prob: int, ckpt_every: int, ws_ptr: int, ws_bytes: 
 def mmp_adjoint_backward(ctx, prob: int, gm, gv, ws_ptr: int, ws_bytes: int) -> np.ndarray:
     gma = np.ascontiguousarray(gm, dtype=np.float64)
     gva = np.ascontiguousarray(gv, dtype=np.float64)
-    grad = np.empty(5, np.float64)
+    grad = np.empty(N_THETA, np.float64)
     dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
     _check(load().mmp_adjoint_backward(ctx, prob, dp(gma), dp(gva), C.c_void_p(ws_ptr), ws_bytes, dp(grad)),
            "mmp_adjoint_backward")
@@ -429,7 +431,7 @@ class Solver:
 
 # ---- adjoint as a torch.autograd.Function -----------------------------------
 
-THETA_NAMES = ("c3", "c1", "kappa", "c0", "B0")
+THETA_NAMES = ("c3", "c1", "kappa", "c0", "B0", "B", "BE")
 
 
 class Adjoint:
@@ -455,21 +457,24 @@ def _autograd_function():
     import torch
 
     class FineMoments(torch.autograd.Function):
-        """theta = (c3, c1, kappa, c0, B0) -> slice-end moments [(N+1), 2]
-        (mean, population variance) of the serial fine run; the backward is
-        the library's adjoint kernel."""
+        """theta = (c3, c1, kappa, c0, B0[, B, BE]) -> slice-end moments
+        [(N+1), 2] (mean, population variance) of the serial fine run; the
+        backward is the library's adjoint kernel (gradient in as many
+        coefficients as theta holds)."""
 
         @staticmethod
         def forward(ctx, theta, adj):
             mom = adj.forward(theta.detach().cpu().double().numpy())
             ctx.adj = adj
+            ctx.n_theta = theta.numel()
+            ctx.dtype = theta.dtype
             return torch.from_numpy(mom).to(theta.dtype)
 
         @staticmethod
         def backward(ctx, g):
             g = g.detach().cpu().double().numpy()
             grad = ctx.adj.backward(g[1:, 0], g[1:, 1])
-            return torch.from_numpy(grad), None
+            return torch.from_numpy(grad[: ctx.n_theta]).to(ctx.dtype), None
 
     return FineMoments
 
