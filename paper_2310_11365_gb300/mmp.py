@@ -14,6 +14,8 @@ import numpy as np
 
 from . import workloads
 
+Problem = workloads.Problem  # the problem record every call takes
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libmmp.so")
 
@@ -429,6 +431,20 @@ class Solver:
             pass
 
 
+def run(problems, stream=None) -> list[dict]:
+    """Solve one problem or a list of problems (batched in one context when
+    they share a precision and kernel form) to convergence; per problem its
+    status (sweeps, converged, last_change, dev_err) and its moments
+    [(N+1), MOMENT_STRIDE] (per-region fraction, mean, variance; global
+    mean and variance)."""
+    s = Solver(problems, stream)
+    try:
+        s.run()
+        return [dict(s.status(i), moments=s.moments(i)) for i in range(len(s.problems))]
+    finally:
+        s.close()
+
+
 # ---- adjoint as a torch.autograd.Function -----------------------------------
 
 THETA_NAMES = ("c3", "c1", "kappa", "c0", "B0", "B", "BE")
@@ -479,15 +495,24 @@ def _autograd_function():
     return FineMoments
 
 
-FineMoments = None
+_fine_moments_cls = None
+
+
+def __getattr__(name: str):
+    # mmp.FineMoments is built on first access, so that importing the
+    # binding does not import torch
+    global _fine_moments_cls
+    if name == "FineMoments":
+        if _fine_moments_cls is None:
+            _fine_moments_cls = _autograd_function()
+        return _fine_moments_cls
+    raise AttributeError(name)
 
 
 def fine_moments(theta, adj: Adjoint):
-    """Differentiable slice-end moments of the serial fine run."""
-    global FineMoments
-    if FineMoments is None:
-        FineMoments = _autograd_function()
-    return FineMoments.apply(theta, adj)
+    """Differentiable slice-end moments of the serial fine run
+    (FineMoments.apply(theta, adj))."""
+    return __getattr__("FineMoments").apply(theta, adj)
 
 
 def double_well_theta(kappa, sigma, a, b):

@@ -76,6 +76,19 @@ def double_well(a: float, b: float, kappa: float, sigma: float, **kw) -> Problem
     return Problem(c3=4.0 * a, c1=2.0 * b - kappa, kappa=kappa, c0=0.0, B0=sigma, **kw)
 
 
+def gbm(**kw) -> Problem:
+    """The modified geometric Brownian motion of the paper's linear example
+    (Sec. 5.1): dX = (alpha X + beta E[X] + a) dt + (sigma X + omega E[X] + b) dW
+    with alpha = -1/2, beta = 4/5, a = 1/3, sigma = omega = sqrt(1/2)/2,
+    b = 1/6, X0 ~ N(1, 1/4) and N = 10 slices.  T, dt and P are not given
+    there; T = 1, dt = 1e-3, P = 1e5 here."""
+    s = 0.5 * np.sqrt(0.5)
+    p = Problem(c3=0.0, c1=-0.5, kappa=0.8, c0=1.0 / 3.0, B=s, BE=s, B0=1.0 / 6.0, m0=1.0, s0=0.5,
+                T=1.0, N=10, dt=1e-3, P=100_000, coarse_h=0.25, seed=SEED_BASE + 6, tol=1e-8,
+                precision="fp64")
+    return p.scaled(**kw) if kw else p
+
+
 # --- the five measured workloads -----------------------------------------
 
 def config1(**kw) -> Problem:

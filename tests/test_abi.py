@@ -57,3 +57,22 @@ def test_null_arguments(mmplib):
     assert lib.mmp_create(None, None, 0, None, 0, None) == -1
     assert lib.mmp_lift(None) == -1
     assert lib.mmp_status(None, 0, None, None, None, None) == -1
+
+
+def test_python_surface(mmplib):
+    """The binding's user-facing names: the problem record, the one-call
+    solve, and the autograd function over the adjoint (built on first
+    access, so that importing the binding does not import torch)."""
+    import torch
+
+    assert mmplib.Problem is W.Problem
+    assert callable(mmplib.run) and callable(mmplib.fine_moments)
+    assert issubclass(mmplib.FineMoments, torch.autograd.Function)
+    assert mmplib.FineMoments is mmplib.FineMoments
+    assert mmplib.N_THETA == len(mmplib.THETA_NAMES) == 7
+
+
+def test_set_params_arity(mmplib):
+    lib = mmplib.load()
+    theta = (C.c_double * 7)(*([0.0] * 7))
+    assert lib.mmp_set_params(None, 0, theta, 7) == -1
