@@ -141,17 +141,27 @@ void orc_fine(const orc_problem* pr, int n, const double* u_in, double* u_out, d
  * Eq. (multimodal_R), per region D_i the fraction, mean and variance.
  * reading: variances are population variances (1/n_i), which makes the
  * mixture identity exact and keeps Lemma 3.1.
- * reading: with I = 2, D_0 = {x < thr} and D_1 = {x >= thr}.
+ * reading: the regions are consecutive intervals of the real line split at
+ * t_1 < t_2 < t_3: D_0 = {x < t_1}, D_i = {t_i <= x < t_{i+1}} and
+ * D_{I-1} = {x >= t_{I-1}}; with I = 2 this is D_0 = {x < thr}, D_1 = {x >= thr}.
  * ---------------------------------------------------------------------- */
 int orc_region(const orc_problem* pr, double x) {
-  if (pr->n_regions < 2) return 0;
-  return x < pr->threshold ? 0 : 1;
+  const int I = pr->n_regions;
+  if (I < 2 || x < pr->threshold) return 0;
+  if (I < 3 || x < pr->threshold2) return 1;
+  if (I < 4 || x < pr->threshold3) return 2;
+  return 3;
+}
+
+/* lower boundary t_i of region i >= 1 */
+static double region_lower(const orc_problem* pr, int i) {
+  return i == 1 ? pr->threshold : (i == 2 ? pr->threshold2 : pr->threshold3);
 }
 
 void orc_restrict(const orc_problem* pr, const double* u, orc_stats* st) {
   const long long P = pr->P;
   memset(st, 0, sizeof(*st));
-  double sum[ORC_MAX_REGIONS] = {0, 0};
+  double sum[ORC_MAX_REGIONS] = {0};
   for (int i = 0; i < ORC_MAX_REGIONS; ++i) {
     st->min[i] = INFINITY;
     st->max[i] = -INFINITY;
@@ -165,7 +175,7 @@ void orc_restrict(const orc_problem* pr, const double* u, orc_stats* st) {
   }
   for (int i = 0; i < ORC_MAX_REGIONS; ++i)
     st->mean[i] = st->count[i] > 0 ? sum[i] / (double)st->count[i] : 0.0;
-  double ss[ORC_MAX_REGIONS] = {0, 0};
+  double ss[ORC_MAX_REGIONS] = {0};
   for (long long p = 0; p < P; ++p) {
     int i = orc_region(pr, u[p]);
     double d = u[p] - st->mean[i];
@@ -435,6 +445,308 @@ double orc_extrapolate(double p_k, double alpha, double beta, double dt_ahead) {
 }
 
 /* ------------------------------------------------------------------------
+ * The general model of the particle fractions, Sec. 3.6
+ * Eq. (generalised_model_multimodal_PFs): dP/dt = A P, where omega_ij >= 0
+ * is the rate from region D_i to D_j (i != j), A_ji = omega_ij and
+ * A_ii = -sum_{j != i} omega_ij (columns sum to zero, so sum_i P_i is kept).
+ * Over one slice P(t_{n+1}) = Phi P(t_n) with Phi = expm(A dT).
+ * reading (the paper fits theta = {omega_ij} by Levenberg-Marquardt, with
+ * H_i(P_k, m, theta) = (expm(A m dT) P_k)_i, and gives no further detail):
+ * with I >= 3 regions all I fractions of the exact slice ends t_0..t_k are
+ * fitted (P(t_0) fixed).  The rates are exit rates, so the fit runs on
+ * theta_ij = log omega_ij (every rate stays positive, Phi stays a stochastic
+ * matrix and the extrapolated fractions stay in [0, 1] with sum 1; an
+ * unconstrained fit of a handful of noisy fractions drives some rates
+ * negative), starting from equal rates 1 / (I k dT).  The Jacobian is the
+ * exact derivative of the computed expm (forward mode through the Taylor
+ * polynomial and the squarings) times omega.  Damping and stopping as in
+ * the two-region fit above; then up to three Gauss-Newton steps, each kept
+ * only if it does not raise the cost.  The fit is used only from k >= I
+ * (the k I residuals minus the k fixed sums outnumber the I (I - 1) rates)
+ * and only if every rate is finite.  With I = 2 the App. H form above is
+ * this model with alpha = -(omega_01 + omega_10),
+ * beta = omega_10 / (omega_01 + omega_10).
+ * ---------------------------------------------------------------------- */
+void orc_rate_generator(int I, const double* om, double* A) {
+  for (int r = 0; r < I * I; ++r) A[r] = 0.0;
+  for (int i = 0; i < I; ++i) {
+    for (int j = 0; j < I; ++j) {
+      if (j == i) continue;
+      const double w = om[i * (I - 1) + (j < i ? j : j - 1)];
+      A[j * I + i] += w;
+      A[i * I + i] -= w;
+    }
+  }
+}
+
+/* C = X Y for n x n row-major matrices (sums over k in increasing order) */
+static void matmul(int n, const double* X, const double* Y, double* C) {
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += X[i * n + k] * Y[k * n + j];
+      C[i * n + j] = s;
+    }
+  }
+}
+
+void orc_expm(int n, const double* X, const double* dX, double* E, double* dE) {
+  double norm = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double c = 0.0;
+    for (int i = 0; i < n; ++i) c += fabs(X[i * n + j]);
+    if (c > norm) norm = c;
+  }
+  int sq = 0;
+  double scale = 1.0;
+  while (norm * scale > 0.5 && sq < 60) {
+    scale *= 0.5;
+    ++sq;
+  }
+  double Y[64], dY[64], T[64], dT[64], W[64], dW[64];
+  for (int r = 0; r < n * n; ++r) {
+    Y[r] = X[r] * scale;
+    dY[r] = dX ? dX[r] * scale : 0.0;
+    T[r] = 0.0;
+    dT[r] = 0.0;
+  }
+  for (int i = 0; i < n; ++i) T[i * n + i] = 1.0;
+  /* Horner: T <- I + Y T / m for m = 16 .. 1 */
+  for (int m = 16; m >= 1; --m) {
+    matmul(n, Y, T, W);
+    if (dX) {
+      double U[64];
+      matmul(n, dY, T, dW);
+      matmul(n, Y, dT, U);
+      for (int r = 0; r < n * n; ++r) dT[r] = (dW[r] + U[r]) / (double)m;
+    }
+    for (int r = 0; r < n * n; ++r) T[r] = W[r] / (double)m;
+    for (int i = 0; i < n; ++i) T[i * n + i] += 1.0;
+  }
+  for (int s = 0; s < sq; ++s) {
+    if (dX) {
+      double U[64];
+      matmul(n, dT, T, dW);
+      matmul(n, T, dT, U);
+      for (int r = 0; r < n * n; ++r) dT[r] = dW[r] + U[r];
+    }
+    matmul(n, T, T, W);
+    for (int r = 0; r < n * n; ++r) T[r] = W[r];
+  }
+  for (int r = 0; r < n * n; ++r) {
+    E[r] = T[r];
+    if (dE) dE[r] = dT[r];
+  }
+}
+
+static void matvec(int n, const double* M, const double* x, double* y) {
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += M[i * n + k] * x[k];
+    y[i] = s;
+  }
+}
+
+static void rate_phi(int I, const double* om, double dT, double* Phi) {
+  double A[16];
+  orc_rate_generator(I, om, A);
+  for (int r = 0; r < I * I; ++r) A[r] *= dT;
+  orc_expm(I, A, NULL, Phi, NULL);
+}
+
+static double rate_cost(int I, int k, const double* fr, double dT, const double* om) {
+  double Phi[16], p[4], q[4];
+  rate_phi(I, om, dT, Phi);
+  for (int i = 0; i < I; ++i) p[i] = fr[i];
+  double s = 0.0;
+  for (int n = 1; n <= k; ++n) {
+    matvec(I, Phi, p, q);
+    for (int i = 0; i < I; ++i) {
+      p[i] = q[i];
+      const double r = fr[n * I + i] - p[i];
+      s += r * r;
+    }
+  }
+  return s;
+}
+
+/* Normal equations of the fit at omega: JtJ [np x np] and g = J^T r, with
+ * J = d(model)/d(omega) and r = data - model. */
+static void rate_normal(int I, int k, const double* fr, double dT, const double* om, double* JtJ, double* g) {
+  const int np = I * (I - 1);
+  double A[16], Phi[16], dPhi[12][16];
+  orc_rate_generator(I, om, A);
+  for (int r = 0; r < I * I; ++r) A[r] *= dT;
+  for (int p = 0; p < np; ++p) {
+    double e[12] = {0.0}, dA[16];
+    e[p] = 1.0;
+    orc_rate_generator(I, e, dA);
+    for (int r = 0; r < I * I; ++r) dA[r] *= dT;
+    orc_expm(I, A, dA, Phi, dPhi[p]);
+  }
+  if (np == 0) orc_expm(I, A, NULL, Phi, NULL);
+  for (int r = 0; r < np * np; ++r) JtJ[r] = 0.0;
+  for (int p = 0; p < np; ++p) g[p] = 0.0;
+  double P[4], Q[4], S[12][4], S2[4], S3[4];
+  for (int i = 0; i < I; ++i) P[i] = fr[i];
+  for (int p = 0; p < np; ++p)
+    for (int i = 0; i < I; ++i) S[p][i] = 0.0;
+  for (int n = 1; n <= k; ++n) {
+    /* S_p <- dPhi_p P + Phi S_p (the derivative of P_n), then P <- Phi P */
+    for (int p = 0; p < np; ++p) {
+      matvec(I, dPhi[p], P, S2);
+      matvec(I, Phi, S[p], S3);
+      for (int i = 0; i < I; ++i) S[p][i] = S2[i] + S3[i];
+    }
+    matvec(I, Phi, P, Q);
+    for (int i = 0; i < I; ++i) P[i] = Q[i];
+    for (int i = 0; i < I; ++i) {
+      const double r = fr[n * I + i] - P[i];
+      for (int p = 0; p < np; ++p) {
+        g[p] += S[p][i] * r;
+        for (int q = 0; q < np; ++q) JtJ[p * np + q] += S[p][i] * S[q][i];
+      }
+    }
+  }
+}
+
+/* Solve M x = b for a symmetric positive definite M (Cholesky); 0 on success */
+static int spd_solve(int n, const double* M, const double* b, double* x) {
+  double L[144];
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = M[i * n + j];
+      for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+      if (i == j) {
+        if (!(s > 0.0) || !isfinite(s)) return -1;
+        L[i * n + i] = sqrt(s);
+      } else {
+        L[i * n + j] = s / L[j * n + j];
+      }
+    }
+  }
+  double y[12];
+  for (int i = 0; i < n; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+    y[i] = s / L[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+    x[i] = s / L[i * n + i];
+  }
+  return 0;
+}
+
+int orc_rate_fit(int I, int k, const double* fr, double dT, double* om) {
+  const int np = I * (I - 1);
+  if (I < 2 || I > 4 || k < I) return -1;
+  double th[12], nth[12], nw[12];
+  /* initial rates: the one-step regression P_n ~ Phi0 P_{n-1} (least squares
+   * over n = 1..k), Phi0 ~ I + A dT, so omega_ij ~ Phi0_ji / dT, floored at
+   * a small positive rate; equal rates 1 / (I k dT) if the regression is
+   * singular */
+  {
+    double Sxx[16] = {0.0}, Syx[16] = {0.0};
+    for (int n = 1; n <= k; ++n)
+      for (int a = 0; a < I; ++a)
+        for (int b = 0; b < I; ++b) {
+          Sxx[a * I + b] += fr[(n - 1) * I + a] * fr[(n - 1) * I + b];
+          Syx[a * I + b] += fr[n * I + a] * fr[(n - 1) * I + b];
+        }
+    const double floor_rate = 1e-3 / ((double)k * dT);
+    int ok = 1;
+    double Phi0[16];
+    for (int a = 0; a < I && ok; ++a) {
+      /* row a of Phi0 solves Sxx x = (row a of Syx) (Sxx is symmetric) */
+      double rhs[4], x[4];
+      for (int b = 0; b < I; ++b) rhs[b] = Syx[a * I + b];
+      if (spd_solve(I, Sxx, rhs, x) != 0) ok = 0;
+      for (int b = 0; b < I; ++b) Phi0[a * I + b] = x[b];
+    }
+    for (int i = 0; i < I; ++i)
+      for (int j = 0; j < I; ++j) {
+        if (j == i) continue;
+        const double w = ok ? Phi0[j * I + i] / dT : 1.0 / ((double)I * (double)k * dT);
+        th[i * (I - 1) + (j < i ? j : j - 1)] = log(isfinite(w) && w > floor_rate ? w : floor_rate);
+      }
+  }
+  for (int p = 0; p < np; ++p) om[p] = exp(th[p]);
+  double lambda = 1e-3;
+  double cost = rate_cost(I, k, fr, dT, om);
+  double JtJ[144], g[12], M[144], st[12];
+  /* normal equations in theta: J_theta = J_omega diag(omega) */
+  for (int it = 0; it < 100; ++it) {
+    rate_normal(I, k, fr, dT, om, JtJ, g);
+    for (int p = 0; p < np; ++p) {
+      g[p] *= om[p];
+      for (int q = 0; q < np; ++q) JtJ[p * np + q] *= om[p] * om[q];
+    }
+    for (int r = 0; r < np * np; ++r) M[r] = JtJ[r];
+    for (int p = 0; p < np; ++p) M[p * np + p] = JtJ[p * np + p] * (1.0 + lambda);
+    if (spd_solve(np, M, g, st) != 0) {
+      lambda *= 10.0;
+      if (lambda > 1e12) break;
+      continue;
+    }
+    for (int p = 0; p < np; ++p) {
+      nth[p] = th[p] + fmax(-2.0, fmin(2.0, st[p]));  /* at most a factor e^2 per step */
+      nw[p] = exp(nth[p]);
+    }
+    const double ncost = rate_cost(I, k, fr, dT, nw);
+    if (isfinite(ncost) && ncost < cost) {
+      double rel = 0.0;
+      for (int p = 0; p < np; ++p) {
+        th[p] = nth[p];
+        om[p] = nw[p];
+        rel = fmax(rel, fabs(st[p]) / (fabs(th[p]) + 1e-300));
+      }
+      cost = ncost;
+      lambda /= 10.0;
+      if (rel < 1e-15) break;
+    } else {
+      lambda *= 10.0;
+      if (lambda > 1e12) break;
+    }
+  }
+  /* Gauss-Newton refinement, each step kept only if the cost does not rise */
+  for (int it = 0; it < 3; ++it) {
+    rate_normal(I, k, fr, dT, om, JtJ, g);
+    for (int p = 0; p < np; ++p) {
+      g[p] *= om[p];
+      for (int q = 0; q < np; ++q) JtJ[p * np + q] *= om[p] * om[q];
+    }
+    if (spd_solve(np, JtJ, g, st) != 0) break;
+    for (int p = 0; p < np; ++p) {
+      nth[p] = th[p] + st[p];
+      nw[p] = exp(nth[p]);
+    }
+    const double ncost = rate_cost(I, k, fr, dT, nw);
+    if (!(isfinite(ncost) && ncost <= cost)) break;
+    for (int p = 0; p < np; ++p) {
+      th[p] = nth[p];
+      om[p] = nw[p];
+    }
+    cost = ncost;
+  }
+  for (int p = 0; p < np; ++p)
+    if (!isfinite(om[p]) || !(om[p] >= 0.0)) return -2;
+  return 0;
+}
+
+void orc_rate_propagate(int I, const double* om, double dT, const double* p_in, int m, double* p_out) {
+  double Phi[16], p[4], q[4];
+  rate_phi(I, om, dT, Phi);
+  for (int i = 0; i < I; ++i) p[i] = p_in[i];
+  for (int s = 0; s < m; ++s) {
+    matvec(I, Phi, p, q);
+    for (int i = 0; i < I; ++i) p[i] = q[i];
+  }
+  for (int i = 0; i < I; ++i) p_out[i] = p[i];
+}
+
+/* ------------------------------------------------------------------------
  * Classical Parareal, Sec. 3.1 Eq. (original_parareal), with the noisy fine
  * propagator of Lemma 4.1: F(u) = Fm u + Fa + eps.
  * ---------------------------------------------------------------------- */
@@ -477,8 +789,8 @@ static void macro_from_stats(const orc_problem* pr, const orc_stats* st, orc_mac
 static void lift(const orc_problem* pr, int n, const orc_macro* rho, const orc_stats* st0,
                  const double* u0, double* out) {
   const int I = pr->n_regions < 2 ? 1 : pr->n_regions;
-  int doit[ORC_MAX_REGIONS] = {0, 0};
-  double mu[ORC_MAX_REGIONS] = {0, 0}, sg[ORC_MAX_REGIONS] = {0, 0};
+  int doit[ORC_MAX_REGIONS] = {0};
+  double mu[ORC_MAX_REGIONS] = {0}, sg[ORC_MAX_REGIONS] = {0};
   for (int i = 0; i < I; ++i) {
     doit[i] = st0->count[i] > 0 && rho->var[i] >= 0.0;
     mu[i] = rho->mean[i];
@@ -498,7 +810,7 @@ int orc_parareal(const orc_problem* pr, const double* u0_in, double* hist, orc_m
   const long long P = pr->P;
   const int I = pr->n_regions < 2 ? 1 : pr->n_regions;
   const int multimodal = pr->variant != ORC_UNIMODAL && I > 1;
-  const int learning = pr->variant == ORC_LEARNING && I == 2;
+  const int learning = pr->variant == ORC_LEARNING && I >= 2;
   const double dT = pr->T / N;
   int K = pr->max_iter < N ? pr->max_iter : N;
   if (K < 1) K = 1;
@@ -545,7 +857,19 @@ int orc_parareal(const orc_problem* pr, const double* u0_in, double* hist, orc_m
       for (int i = 0; i < I; ++i) fr[(n + 1) * ORC_MAX_REGIONS + i] = (double)rst[n].count[i] / (double)P;
     /* learning (Def. 3.4): after sweep k the slice ends t_0..t_k are exact;
      * fit on them and extrapolate the fractions beyond t_k. */
-    if (learning && k >= 2) {
+    if (learning && I >= 3 && k >= I) {
+      /* the general rate model on all fractions (Eq. generalised_model_multimodal_PFs) */
+      double* frk = (double*)malloc(sizeof(double) * (size_t)(k + 1) * I);
+      double om[12];
+      for (int n = 0; n <= k; ++n)
+        for (int i = 0; i < I; ++i) frk[n * I + i] = fr[n * ORC_MAX_REGIONS + i];
+      if (orc_rate_fit(I, k, frk, dT, om) == 0) {
+        for (int n = k + 1; n <= N; ++n)
+          orc_rate_propagate(I, om, dT, fr + (size_t)(n - 1) * ORC_MAX_REGIONS, 1, fr + (size_t)n * ORC_MAX_REGIONS);
+      }
+      free(frk);
+    }
+    if (learning && I == 2 && k >= 2) {
       for (int n = 0; n <= k; ++n) {
         frac0[n] = fr[n * ORC_MAX_REGIONS + 0];
         tpts[n] = n * dT;
@@ -570,8 +894,8 @@ int orc_parareal(const orc_problem* pr, const double* u0_in, double* hist, orc_m
       const orc_stats* b = &rst[n];
       orc_macro nxt;
       memset(&nxt, 0, sizeof(nxt));
-      int doit[ORC_MAX_REGIONS] = {0, 0};
-      double mu[ORC_MAX_REGIONS] = {0, 0}, sg[ORC_MAX_REGIONS] = {0, 0};
+      int doit[ORC_MAX_REGIONS] = {0};
+      double mu[ORC_MAX_REGIONS] = {0}, sg[ORC_MAX_REGIONS] = {0};
       for (int i = 0; i < I; ++i) {
         if (b->count[i] == 0) {
           /* reading (Def. 3.2/3.4): an empty region carries the coarse
@@ -591,10 +915,13 @@ int orc_parareal(const orc_problem* pr, const double* u0_in, double* hist, orc_m
            * reading: a region with V = 0 (redraw branch) is not moved. */
           if (b->var[i] == 0.0) {
             accept = 0;
-          } else if (i == 0) {
-            accept = transformed(b->max[0], am, av, b->mean[0], b->var[0]) < pr->threshold;
           } else {
-            accept = transformed(b->min[1], am, av, b->mean[1], b->var[1]) >= pr->threshold;
+            /* D_i = [t_i, t_{i+1}): the smallest particle stays at or above
+             * t_i, the largest below t_{i+1} */
+            if (i > 0)
+              accept = transformed(b->min[i], am, av, b->mean[i], b->var[i]) >= region_lower(pr, i);
+            if (accept && i < I - 1)
+              accept = transformed(b->max[i], am, av, b->mean[i], b->var[i]) < region_lower(pr, i + 1);
           }
         }
         if (accept) {

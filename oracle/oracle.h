@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define ORC_MAX_REGIONS 2
+#define ORC_MAX_REGIONS 4
 
 enum { ORC_UNIMODAL = 0, ORC_MULTIMODAL = 1, ORC_LEARNING = 2 };
 
@@ -50,14 +50,15 @@ typedef struct {
   double dt;                  /* requested fine step */
   long long P;                /* particles */
   double coarse_h;            /* largest coarse step */
-  int n_regions;              /* 1 or 2 */
-  double threshold;           /* D_0 = {x < thr}, D_1 = {x >= thr} */
+  int n_regions;              /* 1 .. ORC_MAX_REGIONS */
+  double threshold;           /* t_1: D_0 = {x < t_1}, D_1 = {t_1 <= x (< t_2)}, ... */
   int variant;                /* ORC_UNIMODAL / ORC_MULTIMODAL / ORC_LEARNING */
   uint64_t seed;
   uint32_t problem_tag;
   double tol;                 /* stop when max_n |d(M,V)| < tol */
   int max_iter;               /* at most this many fine sweeps (<= N) */
   int coarse_model;           /* ORC_COARSE_CLOSURE / _TAYLOR / _SIGMA2 / _SIGMA3 */
+  double threshold2, threshold3;  /* t_2, t_3 (n_regions 3, 4): D_2 = {t_2 <= x (< t_3)}, D_3 = {x >= t_3} */
 } orc_problem;
 
 /* Coarse moment models (Sec. 2): the Gaussian closure (expectations of the
@@ -123,6 +124,22 @@ void orc_coarse(const orc_problem* pr, const orc_macro* in, orc_macro* out);
 int orc_lsq_fit(int n_pts, const double* t, const double* y, double p0, double dT,
                 double* alpha, double* beta);
 double orc_extrapolate(double p_k, double alpha, double beta, double dt_ahead);
+
+/* The general model of the fractions (Eq. generalised_model_multimodal_PFs):
+ * dP/dt = A P with the rates omega_ij >= 0 (i != j) from D_i to D_j,
+ * A_ji = omega_ij, A_ii = -sum_{j != i} omega_ij.  omega is stored as
+ * omega[i (I-1) + (j < i ? j : j - 1)], I (I-1) values. */
+void orc_rate_generator(int I, const double* omega, double* A);
+/* E = expm(X) for an n x n row-major X (n <= 8), by scaling and squaring
+ * with a degree-16 Taylor polynomial; if dX is not NULL, dE receives the
+ * derivative of that computation in the direction dX. */
+void orc_expm(int n, const double* X, const double* dX, double* E, double* dE);
+/* Fit omega to the fractions fr[n I + i] at t_n = n dT, n = 0..k (fr at
+ * t_0 fixed) by Levenberg-Marquardt on log omega; returns 0 if the fit is
+ * usable (every rate finite), -1 if k < I, -2 otherwise. */
+int orc_rate_fit(int I, int k, const double* fr, double dT, double* omega);
+/* p_out = expm(A m dT) p_in as m steps of Phi = expm(A dT). */
+void orc_rate_propagate(int I, const double* omega, double dT, const double* p_in, int m, double* p_out);
 
 /* -- Parareal ------------------------------------------------------------ */
 /* Generic iteration of Eq. mM_parareal_other_k_NEW for classical scalar

@@ -19,7 +19,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 UNIMODAL, MULTIMODAL, LEARNING = 0, 1, 2
-MAX_REGIONS = 2
+MAX_REGIONS = 4
 
 
 def build(force: bool = False) -> str:
@@ -45,6 +45,7 @@ class OrcProblem(C.Structure):
         ("coarse_h", C.c_double), ("n_regions", C.c_int), ("threshold", C.c_double),
         ("variant", C.c_int), ("seed", C.c_uint64), ("problem_tag", C.c_uint32),
         ("tol", C.c_double), ("max_iter", C.c_int), ("coarse_model", C.c_int),
+        ("threshold2", C.c_double), ("threshold3", C.c_double),
     ]
 
 
@@ -102,6 +103,14 @@ def lib():
         _lib.orc_lsq_fit.restype = C.c_int
         _lib.orc_extrapolate.argtypes = [C.c_double] * 4
         _lib.orc_extrapolate.restype = C.c_double
+        _lib.orc_rate_generator.argtypes = [C.c_int, d, d]
+        _lib.orc_rate_generator.restype = None
+        _lib.orc_expm.argtypes = [C.c_int, d, d, d, d]
+        _lib.orc_expm.restype = None
+        _lib.orc_rate_fit.argtypes = [C.c_int, C.c_int, d, C.c_double, d]
+        _lib.orc_rate_fit.restype = C.c_int
+        _lib.orc_rate_propagate.argtypes = [C.c_int, d, C.c_double, d, C.c_int, d]
+        _lib.orc_rate_propagate.restype = None
         _lib.orc_parareal_scalar.argtypes = [C.c_int, C.c_int] + [C.c_double] * 5 + [d, d]
         _lib.orc_parareal.argtypes = [pp, d, d, C.POINTER(OrcMacro), d, C.POINTER(OrcResult)]
         _lib.orc_parareal.restype = C.c_int
@@ -126,7 +135,7 @@ def problem(p) -> OrcProblem:
     return OrcProblem(
         p.c3, p.c1, p.kappa, p.c0, p.B, p.BE, p.B0, p.m0, p.s0, p.T, p.N, p.dt, p.P,
         p.coarse_h, p.n_regions, p.threshold, p.variant, p.seed, p.problem_tag, p.tol, max_iter,
-        p.coarse_model,
+        p.coarse_model, p.threshold2, p.threshold3,
     )
 
 
@@ -207,8 +216,8 @@ def match(p, n: int, mu, sigma, do_region, u: np.ndarray) -> np.ndarray:
 
 def macro(frac, mean, var) -> OrcMacro:
     pad = lambda v: list(v) + [0.0] * (MAX_REGIONS - len(v))
-    return OrcMacro((C.c_double * 2)(*pad(frac)), (C.c_double * 2)(*pad(mean)),
-                    (C.c_double * 2)(*pad(var)))
+    return OrcMacro((C.c_double * MAX_REGIONS)(*pad(frac)), (C.c_double * MAX_REGIONS)(*pad(mean)),
+                    (C.c_double * MAX_REGIONS)(*pad(var)))
 
 
 def mixture(p, frac, mean, var):
@@ -250,6 +259,42 @@ def lsq_fit(t, y, p0: float, dT: float):
 
 def extrapolate(p_k: float, alpha: float, beta: float, dt_ahead: float) -> float:
     return lib().orc_extrapolate(p_k, alpha, beta, dt_ahead)
+
+
+def rate_generator(I: int, omega) -> np.ndarray:
+    """A of dP/dt = A P from the rates omega[i (I-1) + (j < i ? j : j-1)] (D_i -> D_j)."""
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    A = np.zeros(I * I)
+    lib().orc_rate_generator(I, _dp(om), _dp(A))
+    return A.reshape(I, I)
+
+
+def expm(X, dX=None):
+    """The oracle's matrix exponential (and its derivative in direction dX)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    n = X.shape[0]
+    E = np.zeros(n * n)
+    dE = np.zeros(n * n)
+    dXa = None if dX is None else np.ascontiguousarray(dX, dtype=np.float64)
+    lib().orc_expm(n, _dp(X), _dp(dXa), _dp(E), _dp(dE) if dX is not None else None)
+    return (E.reshape(n, n), dE.reshape(n, n)) if dX is not None else E.reshape(n, n)
+
+
+def rate_fit(fr, dT: float):
+    """Fit the rates to fractions fr [(k+1), I]; returns (rc, omega)."""
+    fr = np.ascontiguousarray(fr, dtype=np.float64)
+    k, I = fr.shape[0] - 1, fr.shape[1]
+    om = np.zeros(max(I * (I - 1), 1))
+    rc = lib().orc_rate_fit(I, k, _dp(fr), dT, _dp(om))
+    return rc, om[: I * (I - 1)]
+
+
+def rate_propagate(I: int, omega, dT: float, p_in, m: int) -> np.ndarray:
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    pi = np.ascontiguousarray(p_in, dtype=np.float64)
+    out = np.zeros(I)
+    lib().orc_rate_propagate(I, _dp(om), dT, _dp(pi), m, _dp(out))
+    return out
 
 
 def parareal_scalar(N, K, u0, Fm, Fa, Gm, Ga, noise=None) -> np.ndarray:

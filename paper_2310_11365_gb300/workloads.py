@@ -56,6 +56,8 @@ class Problem:
     max_iter: int = 0          # 0 means N
     precision: str = "fp64"    # "fp64" or "mixed" (FP32 particles)
     coarse_model: int = 0      # CLOSURE, TAYLOR, SIGMA2 or SIGMA3
+    threshold2: float = 0.0    # region boundaries t_2 < t_3 for n_regions 3 and 4
+    threshold3: float = 0.0
 
     def scaled(self, **kw) -> "Problem":
         return replace(copy.copy(self), **kw)
