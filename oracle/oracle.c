@@ -454,14 +454,18 @@ double orc_extrapolate(double p_k, double alpha, double beta, double dt_ahead) {
  * H_i(P_k, m, theta) = (expm(A m dT) P_k)_i, and gives no further detail):
  * with I >= 3 regions all I fractions of the exact slice ends t_0..t_k are
  * fitted (P(t_0) fixed).  The rates are exit rates, so the fit runs on
- * theta_ij = log omega_ij (every rate stays positive, Phi stays a stochastic
- * matrix and the extrapolated fractions stay in [0, 1] with sum 1; an
- * unconstrained fit of a handful of noisy fractions drives some rates
- * negative), starting from equal rates 1 / (I k dT).  The Jacobian is the
- * exact derivative of the computed expm (forward mode through the Taylor
- * polynomial and the squarings) times omega.  Damping and stopping as in
- * the two-region fit above; then up to three Gauss-Newton steps, each kept
- * only if it does not raise the cost.  The fit is used only from k >= I
+ * theta_ij with omega_ij = theta_ij^2 (every rate stays >= 0, Phi stays a
+ * stochastic matrix and the extrapolated fractions stay in [0, 1] with sum
+ * 1; an unconstrained fit of a handful of noisy fractions drives some rates
+ * negative; the square keeps the fit free of transcendental functions, so
+ * that it is reproducible bit for bit).  Start: the one-step regression
+ * P_n ~ Phi0 P_{n-1} (least squares over n = 1..k) with Phi0 ~ I + A dT,
+ * i.e. omega_ij ~ Phi0_ji / dT, floored at 1e-3 / (k dT).  The Jacobian is
+ * the exact derivative of the computed expm (forward mode through the
+ * Taylor polynomial and the squarings) times 2 theta.  Damping and stopping
+ * as in the two-region fit above, with each step of theta_ij capped at twice
+ * max(|theta_ij|, sqrt(floor)); then up to three Gauss-Newton steps, each
+ * kept only if it does not raise the cost.  The fit is used only from k >= I
  * (the k I residuals minus the k fixed sums outnumber the I (I - 1) rates)
  * and only if every rate is finite.  With I = 2 the App. H form above is
  * this model with alpha = -(omega_01 + omega_10),
@@ -669,19 +673,20 @@ int orc_rate_fit(int I, int k, const double* fr, double dT, double* om) {
       for (int j = 0; j < I; ++j) {
         if (j == i) continue;
         const double w = ok ? Phi0[j * I + i] / dT : 1.0 / ((double)I * (double)k * dT);
-        th[i * (I - 1) + (j < i ? j : j - 1)] = log(isfinite(w) && w > floor_rate ? w : floor_rate);
+        th[i * (I - 1) + (j < i ? j : j - 1)] = sqrt(isfinite(w) && w > floor_rate ? w : floor_rate);
       }
   }
-  for (int p = 0; p < np; ++p) om[p] = exp(th[p]);
+  const double th_floor = sqrt(1e-3 / ((double)k * dT));
+  for (int p = 0; p < np; ++p) om[p] = th[p] * th[p];
   double lambda = 1e-3;
   double cost = rate_cost(I, k, fr, dT, om);
   double JtJ[144], g[12], M[144], st[12];
-  /* normal equations in theta: J_theta = J_omega diag(omega) */
+  /* normal equations in theta: J_theta = J_omega diag(2 theta) */
   for (int it = 0; it < 100; ++it) {
     rate_normal(I, k, fr, dT, om, JtJ, g);
     for (int p = 0; p < np; ++p) {
-      g[p] *= om[p];
-      for (int q = 0; q < np; ++q) JtJ[p * np + q] *= om[p] * om[q];
+      g[p] *= 2.0 * th[p];
+      for (int q = 0; q < np; ++q) JtJ[p * np + q] *= (2.0 * th[p]) * (2.0 * th[q]);
     }
     for (int r = 0; r < np * np; ++r) M[r] = JtJ[r];
     for (int p = 0; p < np; ++p) M[p * np + p] = JtJ[p * np + p] * (1.0 + lambda);
@@ -691,8 +696,10 @@ int orc_rate_fit(int I, int k, const double* fr, double dT, double* om) {
       continue;
     }
     for (int p = 0; p < np; ++p) {
-      nth[p] = th[p] + fmax(-2.0, fmin(2.0, st[p]));  /* at most a factor e^2 per step */
-      nw[p] = exp(nth[p]);
+      /* a step changes theta by at most twice its size (or the floor's) */
+      const double cap = 2.0 * fmax(fabs(th[p]), th_floor);
+      nth[p] = th[p] + fmax(-cap, fmin(cap, st[p]));
+      nw[p] = nth[p] * nth[p];
     }
     const double ncost = rate_cost(I, k, fr, dT, nw);
     if (isfinite(ncost) && ncost < cost) {
@@ -714,13 +721,13 @@ int orc_rate_fit(int I, int k, const double* fr, double dT, double* om) {
   for (int it = 0; it < 3; ++it) {
     rate_normal(I, k, fr, dT, om, JtJ, g);
     for (int p = 0; p < np; ++p) {
-      g[p] *= om[p];
-      for (int q = 0; q < np; ++q) JtJ[p * np + q] *= om[p] * om[q];
+      g[p] *= 2.0 * th[p];
+      for (int q = 0; q < np; ++q) JtJ[p * np + q] *= (2.0 * th[p]) * (2.0 * th[q]);
     }
     if (spd_solve(np, JtJ, g, st) != 0) break;
     for (int p = 0; p < np; ++p) {
       nth[p] = th[p] + st[p];
-      nw[p] = exp(nth[p]);
+      nw[p] = nth[p] * nth[p];
     }
     const double ncost = rate_cost(I, k, fr, dT, nw);
     if (!(isfinite(ncost) && ncost <= cost)) break;

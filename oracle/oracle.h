@@ -135,7 +135,7 @@ void orc_rate_generator(int I, const double* omega, double* A);
  * derivative of that computation in the direction dX. */
 void orc_expm(int n, const double* X, const double* dX, double* E, double* dE);
 /* Fit omega to the fractions fr[n I + i] at t_n = n dT, n = 0..k (fr at
- * t_0 fixed) by Levenberg-Marquardt on log omega; returns 0 if the fit is
+ * t_0 fixed) by Levenberg-Marquardt on theta, omega = theta^2; returns 0 if the fit is
  * usable (every rate finite), -1 if k < I, -2 otherwise. */
 int orc_rate_fit(int I, int k, const double* fr, double dT, double* omega);
 /* p_out = expm(A m dT) p_in as m steps of Phi = expm(A dT). */
