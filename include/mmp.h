@@ -62,8 +62,10 @@ extern "C" {
  * n_f = ceil(T/(N dt) - 1e-9) Euler-Maruyama steps of h = T/(N n_f).
  * The coarse propagator is the Gaussian-closure moment ODE per region
  * (exact for c3 = 0, Lemma 2.1) integrated by forward Euler with
- * n_c = ceil(T/(N coarse_h) - 1e-9) substeps.  With n_regions = 2 the
- * regions are D_0 = {x < threshold}, D_1 = {x >= threshold}.
+ * n_c = ceil(T/(N coarse_h) - 1e-9) substeps.  With I = n_regions > 1 the
+ * regions are consecutive intervals split at t_1 = threshold < t_2 =
+ * threshold2 < t_3 = threshold3 (the first I - 1 of them):
+ * D_0 = {x < t_1}, D_i = {t_i <= x < t_{i+1}}, D_{I-1} = {x >= t_{I-1}}.
  * Random numbers: Philox-4x32-10 with key (seed mod 2^32, seed div 2^32)
  * and counter (p div 4, step, slice | tag << 24, problem_tag). */
 typedef struct {
@@ -75,8 +77,8 @@ typedef struct {
   double dt;                 /* requested fine step, > 0                      */
   long long P;               /* particles, 1..2^31                            */
   double coarse_h;           /* largest coarse step, > 0                      */
-  int n_regions;             /* 1 or 2                                        */
-  double threshold;          /* region boundary (n_regions = 2)               */
+  int n_regions;             /* 1 .. MMP_MAX_REGIONS                          */
+  double threshold;          /* t_1, the first region boundary (n_regions > 1)  */
   int variant;               /* MMP_UNIMODAL / MMP_MULTIMODAL / MMP_LEARNING  */
   int precision;             /* MMP_FP64 / MMP_MIXED                          */
   unsigned long long seed;
@@ -84,7 +86,12 @@ typedef struct {
   double tol;                /* stop when max_n max(|dM|,|dV|) < tol          */
   int max_iter;              /* at most this many fine sweeps; <= 0 means N   */
   int coarse_model;          /* MMP_COARSE_CLOSURE (0) / _TAYLOR / _SIGMA2 / _SIGMA3 */
+  double threshold2;         /* t_2 (n_regions >= 3), > t_1                   */
+  double threshold3;         /* t_3 (n_regions = 4), > t_2                    */
 } mmp_problem_desc;
+
+/* Largest n_regions. */
+#define MMP_MAX_REGIONS 4
 
 /* Coarse moment models (Sec. 2), each integrated by forward Euler per
  * region with the fractions frozen:
@@ -102,13 +109,18 @@ typedef struct {
 typedef struct mmp_ctx mmp_ctx;
 
 /* Number of doubles per slice in the moments returned by mmp_get_moments:
- * frac_0, mean_0, var_0, frac_1, mean_1, var_1, M, V (region 1 zero when
- * n_regions = 1). */
-#define MMP_MOMENT_STRIDE 8
+ * frac_0, mean_0, var_0, frac_1, mean_1, var_1, M, V, frac_2, mean_2,
+ * var_2, frac_3, mean_3, var_3, 0, 0 (the regions past n_regions zero).
+ * Region i's triple starts at MMP_MOMENT_REGION(i). */
+#define MMP_MOMENT_STRIDE 16
+#define MMP_MOMENT_REGION(i) ((i) < 2 ? 3 * (i) : 3 * (i) + 2)
 /* Number of doubles per ensemble in restriction records (mmp_fine_serial,
- * mmp_restrict): count_0, mean_0, var_0, min_0, max_0, count_1, mean_1,
- * var_1, min_1, max_1, mean, var, region_flips, input_mean, 0, 0. */
-#define MMP_STAT_STRIDE 16
+ * mmp_fine, mmp_fine_static): count_0, mean_0, var_0, min_0, max_0,
+ * count_1, .., max_1, mean, var, region_flips, input_mean, 0, 0, then
+ * count_2, .., max_2, count_3, .., max_3, and six zeros.  Region i's
+ * five values start at MMP_STAT_REGION(i). */
+#define MMP_STAT_STRIDE 32
+#define MMP_STAT_REGION(i) ((i) < 2 ? 5 * (i) : 5 * (i) + 6)
 
 const char* mmp_strerror(int code);
 int mmp_version(void);

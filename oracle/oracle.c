@@ -666,8 +666,11 @@ int orc_rate_fit(int I, int k, const double* fr, double dT, double* om) {
       /* row a of Phi0 solves Sxx x = (row a of Syx) (Sxx is symmetric) */
       double rhs[4], x[4];
       for (int b = 0; b < I; ++b) rhs[b] = Syx[a * I + b];
-      if (spd_solve(I, Sxx, rhs, x) != 0) ok = 0;
-      for (int b = 0; b < I; ++b) Phi0[a * I + b] = x[b];
+      if (spd_solve(I, Sxx, rhs, x) != 0) {
+        ok = 0;
+      } else {
+        for (int b = 0; b < I; ++b) Phi0[a * I + b] = x[b];
+      }
     }
     for (int i = 0; i < I; ++i)
       for (int j = 0; j < I; ++j) {

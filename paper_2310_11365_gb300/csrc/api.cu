@@ -100,6 +100,7 @@ struct Prob {
   char* S[2] = {nullptr, nullptr};
   double *stats = nullptr, *stats_u0 = nullptr, *ser_stats = nullptr, *tmp_stats = nullptr;
   double *rho = nullptr, *cache = nullptr, *aff = nullptr, *ctl = nullptr, *partials = nullptr;
+  double* fit = nullptr;  // rate-model fit scratch (learning with three or more regions)
   unsigned *flags = nullptr, *status = nullptr;
   unsigned long long* tags = nullptr;  // followed by flags: one block, cleared per launch
   // host view of the iteration
@@ -125,7 +126,7 @@ int query_device(Device& d) {
 
 bool finite_all(const mmp_problem_desc& d) {
   const double v[] = {d.c3, d.c1, d.kappa, d.c0, d.B, d.BE, d.B0, d.m0, d.s0,
-                      d.T, d.dt, d.coarse_h, d.threshold, d.tol};
+                      d.T, d.dt, d.coarse_h, d.threshold, d.threshold2, d.threshold3, d.tol};
   for (double x : v)
     if (!std::isfinite(x)) return false;
   return true;
@@ -136,7 +137,9 @@ int validate(const mmp_problem_desc& d) {
   if (!(d.T > 0) || !(d.dt > 0) || !(d.coarse_h > 0) || d.s0 < 0 || d.tol < 0) return MMP_ERR_INVALID_ARG;
   if (d.N < 1 || d.N > 65535) return MMP_ERR_INVALID_ARG;
   if (d.P < 1 || d.P > (1LL << 31) - 8) return MMP_ERR_INVALID_ARG;
-  if (d.n_regions < 1 || d.n_regions > 2) return MMP_ERR_INVALID_ARG;
+  if (d.n_regions < 1 || d.n_regions > kMaxRegions) return MMP_ERR_INVALID_ARG;
+  if (d.n_regions >= 3 && !(d.threshold2 > d.threshold)) return MMP_ERR_INVALID_ARG;
+  if (d.n_regions >= 4 && !(d.threshold3 > d.threshold2)) return MMP_ERR_INVALID_ARG;
   if (d.variant < MMP_UNIMODAL || d.variant > MMP_LEARNING) return MMP_ERR_INVALID_ARG;
   if (d.precision != MMP_FP64 && d.precision != MMP_MIXED) return MMP_ERR_INVALID_ARG;
   if (d.coarse_model < MMP_COARSE_CLOSURE || d.coarse_model > MMP_COARSE_SIGMA3) return MMP_ERR_INVALID_ARG;
@@ -323,9 +326,10 @@ size_t layout(Prob& p, char* base, size_t start) {
   p.ser_stats = (double*)ptr(sizeof(double) * kStat * (N + 1));
   p.tmp_stats = (double*)ptr(sizeof(double) * kStat);
   p.rho = (double*)ptr(sizeof(double) * kMom * (N + 1));
-  p.cache = (double*)ptr(sizeof(double) * 4 * N);
-  p.aff = (double*)ptr(sizeof(double) * 2 * kAff * (N + 1));
+  p.cache = (double*)ptr(sizeof(double) * 2 * kMaxRegions * N);
+  p.aff = (double*)ptr(sizeof(double) * kMaxRegions * kAff * (N + 1));
   p.ctl = (double*)ptr(sizeof(double) * 16);
+  p.fit = p.I >= 3 && p.d.variant == MMP_LEARNING ? (double*)ptr(sizeof(double) * kFitScratch) : nullptr;
   p.partials = (double*)ptr(sizeof(double) * kSeatDoubles * (size_t)p.slots_max * p.G);
   p.tags = (unsigned long long*)ptr(sync_bytes(p));
   p.flags = base ? (unsigned*)(p.tags + (size_t)p.slots_max * kSlots * p.G) : nullptr;
@@ -438,7 +442,7 @@ FineArgs fine_args_of(const Prob& p, unsigned long long limit_ns) {
   a.B = d.B; a.BE = d.BE; a.B0 = d.B0;
   a.h = p.h; a.sqrt_h = p.sqrt_h; a.nf = p.nf;
   a.P = d.P; a.Q = p.Q; a.pitch = p.pitch;
-  a.n_regions = p.I; a.thr = d.threshold;
+  a.n_regions = p.I; a.thr = d.threshold; a.thr2 = d.threshold2; a.thr3 = d.threshold3;
   a.key0 = p.key0; a.key1 = p.key1; a.ptag = d.problem_tag;
   a.slice_begin = 0; a.n_tasks = 0;
   a.src0 = p.u0; a.src = nullptr; a.dst = nullptr; a.dst_fixed = 0;
@@ -460,10 +464,11 @@ DriverArgs make_driver_args(const Prob& p, int sweep) {
   a.B = d.B; a.BE = d.BE; a.B0 = d.B0;
   a.N = d.N; a.I = p.I; a.variant = d.variant; a.precision = d.precision;
   a.coarse_model = d.coarse_model;
-  a.dT = p.dT; a.hc = p.hc; a.nc = p.nc; a.thr = d.threshold; a.P = d.P;
+  a.dT = p.dT; a.hc = p.hc; a.nc = p.nc; a.P = d.P;
+  a.thr = d.threshold; a.thr2 = d.threshold2; a.thr3 = d.threshold3;
   a.tol = d.tol; a.max_sweeps = p.max_sweeps;
   a.stats = p.stats; a.stats_u0 = p.stats_u0; a.rho = p.rho; a.cache = p.cache; a.aff = p.aff;
-  a.ctl = p.ctl; a.status = p.status; a.sweep = sweep;
+  a.ctl = p.ctl; a.fit = p.fit; a.status = p.status; a.sweep = sweep;
   return a;
 }
 
@@ -1475,7 +1480,7 @@ extern "C" int mmp_fine_static(const mmp_problem_desc* desc, int n, const void* 
   a.B = d.B; a.BE = d.BE; a.B0 = d.B0;
   a.h = p.h; a.sqrt_h = p.sqrt_h; a.nf = p.nf;
   a.P = d.P; a.Q = p.Q; a.pitch = p.pitch;
-  a.n_regions = p.I; a.thr = d.threshold;
+  a.n_regions = p.I; a.thr = d.threshold; a.thr2 = d.threshold2; a.thr3 = d.threshold3;
   a.key0 = p.key0; a.key1 = p.key1; a.ptag = d.problem_tag;
   a.slice_begin = n; a.n_tasks = 1;
   a.src0 = u_in; a.src = nullptr; a.dst = u_out; a.dst_fixed = 1;
@@ -1726,7 +1731,7 @@ unsigned long long state_digest(const mmp_ctx* c) {
   for (const Prob& p : c->probs) {
     const mmp_problem_desc& d = p.d;
     const double dv[] = {d.c3, d.c1, d.kappa, d.c0, d.B, d.BE, d.B0, d.m0, d.s0, d.T, d.dt, d.coarse_h,
-                         d.threshold, d.tol};
+                         d.threshold, d.threshold2, d.threshold3, d.tol};
     const long long iv[] = {d.N, d.P, d.n_regions, d.variant, d.precision, (long long)d.seed,
                             (long long)d.problem_tag, d.max_iter, d.coarse_model, p.layout, p.nq, p.G,
                             p.slots_max};

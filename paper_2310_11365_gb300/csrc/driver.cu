@@ -12,12 +12,20 @@ namespace mmp {
 namespace {
 
 struct Macro {
-  double frac[2], mean[2], var[2];
+  double frac[kMaxRegions], mean[kMaxRegions], var[kMaxRegions];
 };
 
+__device__ void macro_zero(Macro& m) {
+  for (int i = 0; i < kMaxRegions; ++i) {
+    m.frac[i] = 0.0; m.mean[i] = 0.0; m.var[i] = 0.0;
+  }
+}
+
 __device__ void macro_load(const double* r, Macro& m) {
-  m.frac[0] = r[0]; m.mean[0] = r[1]; m.var[0] = r[2];
-  m.frac[1] = r[3]; m.mean[1] = r[4]; m.var[1] = r[5];
+  for (int i = 0; i < kMaxRegions; ++i) {
+    const double* ri = r + mom_region(i);
+    m.frac[i] = ri[0]; m.mean[i] = ri[1]; m.var[i] = ri[2];
+  }
 }
 
 // Global (M, V) of a macro state: Eq. (mixture_of_distributions_mean_variance)
@@ -28,20 +36,24 @@ __device__ void mixture(const DriverArgs& a, const Macro& r, double& M, double& 
     V = r.var[0];
     return;
   }
-  const double m = r.frac[0] * r.mean[0] + r.frac[1] * r.mean[1];
-  const double s = r.frac[0] * (r.mean[0] * r.mean[0] + r.var[0]) +
-                   r.frac[1] * (r.mean[1] * r.mean[1] + r.var[1]);
+  double m = 0.0, s = 0.0;
+  for (int i = 0; i < a.I; ++i) m += r.frac[i] * r.mean[i];
+  for (int i = 0; i < a.I; ++i) s += r.frac[i] * (r.mean[i] * r.mean[i] + r.var[i]);
   M = m;
   V = s - m * m;
 }
 
 __device__ void macro_store(const DriverArgs& a, double* r, const Macro& m) {
-  r[0] = m.frac[0]; r[1] = m.mean[0]; r[2] = m.var[0];
-  r[3] = m.frac[1]; r[4] = m.mean[1]; r[5] = m.var[1];
+  for (int i = 0; i < kMaxRegions; ++i) {
+    double* ri = r + mom_region(i);
+    ri[0] = m.frac[i]; ri[1] = m.mean[i]; ri[2] = m.var[i];
+  }
   double M, V;
   mixture(a, m, M, V);
-  r[6] = M;
-  r[7] = V;
+  r[kMomM] = M;
+  r[kMomV] = V;
+  r[14] = 0.0;
+  r[15] = 0.0;
 }
 
 // Coarse propagator C_n: a moment ODE per region with the fractions frozen
@@ -109,8 +121,11 @@ __device__ void coarse(const DriverArgs& a, const Macro& in, Macro& out) {
   out = in;
   for (int s = 0; s < a.nc; ++s) {
     double M = out.mean[0];
-    if (a.I > 1) M = out.frac[0] * out.mean[0] + out.frac[1] * out.mean[1];
-    double dm[2], dv[2];
+    if (a.I > 1) {
+      M = 0.0;
+      for (int i = 0; i < a.I; ++i) M += out.frac[i] * out.mean[i];
+    }
+    double dm[kMaxRegions], dv[kMaxRegions];
     for (int i = 0; i < a.I; ++i) coarse_rhs(a, out.mean[i], out.var[i], M, dm[i], dv[i]);
     for (int i = 0; i < a.I; ++i) {
       out.mean[i] = out.mean[i] + a.hc * dm[i];
@@ -119,17 +134,25 @@ __device__ void coarse(const DriverArgs& a, const Macro& in, Macro& out) {
   }
 }
 
-// The transform of the driver's acceptance test, evaluated exactly as the
-// fine kernel will apply it (same precision, same rounding of parameters).
-__device__ bool stays_in_region(const DriverArgs& a, int i, double extreme, double delta, double sm1,
+// Region boundary t_i (i = 1, 2, 3).
+__device__ double boundary(const DriverArgs& a, int i) { return i == 1 ? a.thr : (i == 2 ? a.thr2 : a.thr3); }
+
+// Def. 3.2's test that matching region i = [t_i, t_{i+1}) moves no particle
+// out of it: the affine map is increasing, so its smallest particle must stay
+// at or above t_i and its largest below t_{i+1}.  The transform is evaluated
+// exactly as the fine kernel will apply it (same precision, same rounding).
+__device__ bool stays_in_region(const DriverArgs& a, int i, double lo, double hi, double delta, double sm1,
                                 double m) {
   if (a.precision == MMP_MIXED) {
-    const float y = apply_affine((float)extreme, (float)delta, (float)sm1, (float)m);
-    const float thr = (float)a.thr;
-    return i == 0 ? (y < thr) : !(y < thr);
+    bool ok = true;
+    if (i > 0) ok = !(apply_affine((float)lo, (float)delta, (float)sm1, (float)m) < (float)boundary(a, i));
+    if (ok && i < a.I - 1) ok = apply_affine((float)hi, (float)delta, (float)sm1, (float)m) < (float)boundary(a, i + 1);
+    return ok;
   }
-  const double y = apply_affine(extreme, delta, sm1, m);
-  return i == 0 ? (y < a.thr) : !(y < a.thr);
+  bool ok = true;
+  if (i > 0) ok = !(apply_affine(lo, delta, sm1, m) < boundary(a, i));
+  if (ok && i < a.I - 1) ok = apply_affine(hi, delta, sm1, m) < boundary(a, i + 1);
+  return ok;
 }
 
 __device__ void set_aff(double* af, int mode, double p, double q, double r) {
@@ -269,6 +292,342 @@ __device__ bool lsq_fit(const DriverArgs& a, int npts, double p0, double& alpha,
   return al < 0.0 && be >= 0.0 && be <= 1.0 && isfinite(al) && isfinite(be);
 }
 
+// ---------------------------------------------------------------------------
+// Learning with I >= 3 regions: the rate model of the fractions (Sec. 3.6,
+// Eq. generalised_model_multimodal_PFs), dP/dt = A P with rates
+// omega_ij >= 0 from D_i to D_j (A_ji = omega_ij, A_ii = -sum_j omega_ij),
+// P(t_{n+1}) = Phi P(t_n), Phi = expm(A dT).  Fitted by Levenberg-Marquardt
+// on theta with omega = theta^2 to the exact fractions of t_0..t_k (k >= I):
+// start from the one-step regression P_n ~ Phi0 P_{n-1} (omega_ij ~
+// Phi0_ji / dT, floored at 1e-3 / (k dT)); the Jacobian is the derivative
+// of the computed expm (degree-16 Taylor polynomial after scaling to norm
+// <= 1/2, then squarings) in each rate's direction; damping 1e-3 scaled by
+// diag(J^T J), /10 on success, x10 on failure, at most 100 iterations, each
+// step of theta capped at twice max(|theta|, sqrt(floor)), stop on a
+// relative step below 1e-15 or damping above 1e12; then up to three
+// Gauss-Newton steps kept only if the cost does not rise.  One lane runs
+// the fit in IEEE arithmetic and sqrt only, step for step in a fixed order,
+// so that it is reproducible bit for bit.
+// ---------------------------------------------------------------------------
+constexpr int kMaxRates = kMaxRegions * (kMaxRegions - 1);
+
+// The fit's working arrays live in the problem's scratch block of device
+// memory (DriverArgs::fit, kFitScratch doubles), at fixed offsets, one
+// region per function so that no callee overwrites a caller's live data.
+// (With these arrays on the thread's stack, about 7 KB, some builds of the
+// driver kernels computed different fits from the same inputs; in global
+// memory every build reproduces the oracle's fit bit for bit.)
+enum FitOffsets : int {
+  kFitTh = 0, kFitNth = 12, kFitNw = 24, kFitJtJ = 36, kFitG = 180, kFitM = 192, kFitSt = 336,   // rate_fit
+  kFitSxx = 348, kFitSyx = 364, kFitPhi0 = 380, kFitRhs = 396, kFitX = 400,                     // regression
+  kFitL = 404, kFitY = 548,                                                                     // spd_solve
+  kFitNA = 560, kFitNPhi = 576, kFitDPhi = 592, kFitE = 784, kFitDA = 796, kFitP = 812,        // rate_normal
+  kFitQ = 816, kFitS = 820, kFitS2 = 868, kFitS3 = 872,
+  kFitCPhi = 880, kFitCp = 896, kFitCq = 900,                                                   // rate_cost
+  kFitEx = 904,                                                                                 // expm_dir: 7 x 16
+  kFitGA = 1016,                                                                                // rate_phi
+  kFitEnd = 1032
+};
+static_assert(kFitEnd <= kFitScratch, "fit scratch");
+
+__device__ double frac_at(const DriverArgs& a, int n, int i) {
+  const double* st = n == 0 ? a.stats_u0 : a.stats + (size_t)(n - 1) * kStat;
+  return st[stat_region(i)] / (double)a.P;
+}
+
+__device__ void rate_generator(int I, const double* om, double* A) {
+  for (int r = 0; r < I * I; ++r) A[r] = 0.0;
+  for (int i = 0; i < I; ++i) {
+    for (int j = 0; j < I; ++j) {
+      if (j == i) continue;
+      const double w = om[i * (I - 1) + (j < i ? j : j - 1)];
+      A[j * I + i] += w;
+      A[i * I + i] -= w;
+    }
+  }
+}
+
+__device__ void mat_mul(int n, const double* X, const double* Y, double* C) {
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += X[i * n + k] * Y[k * n + j];
+      C[i * n + j] = s;
+    }
+  }
+}
+
+__device__ void mat_vec(int n, const double* M, const double* x, double* y) {
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += M[i * n + k] * x[k];
+    y[i] = s;
+  }
+}
+
+// E = expm(X) (n <= 4) and, if dX is not null, dE = its derivative in the
+// direction dX, through the same scaling, Horner and squaring steps.
+__device__ void expm_dir(double* ws, int n, const double* X, const double* dX, double* E, double* dE) {
+  double* Y = ws + kFitEx;
+  double* dY = Y + 16;
+  double* T = Y + 32;
+  double* dT = Y + 48;
+  double* W = Y + 64;
+  double* dW = Y + 80;
+  double* U = Y + 96;
+  double norm = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double c = 0.0;
+    for (int i = 0; i < n; ++i) c += fabs(X[i * n + j]);
+    if (c > norm) norm = c;
+  }
+  int sq = 0;
+  double scale = 1.0;
+  while (norm * scale > 0.5 && sq < 60) {
+    scale *= 0.5;
+    ++sq;
+  }
+  for (int r = 0; r < n * n; ++r) {
+    Y[r] = X[r] * scale;
+    dY[r] = dX ? dX[r] * scale : 0.0;
+    T[r] = 0.0;
+    dT[r] = 0.0;
+  }
+  for (int i = 0; i < n; ++i) T[i * n + i] = 1.0;
+  for (int m = 16; m >= 1; --m) {
+    mat_mul(n, Y, T, W);
+    if (dX) {
+      mat_mul(n, dY, T, dW);
+      mat_mul(n, Y, dT, U);
+      for (int r = 0; r < n * n; ++r) dT[r] = (dW[r] + U[r]) / (double)m;
+    }
+    for (int r = 0; r < n * n; ++r) T[r] = W[r] / (double)m;
+    for (int i = 0; i < n; ++i) T[i * n + i] += 1.0;
+  }
+  for (int s = 0; s < sq; ++s) {
+    if (dX) {
+      mat_mul(n, dT, T, dW);
+      mat_mul(n, T, dT, U);
+      for (int r = 0; r < n * n; ++r) dT[r] = dW[r] + U[r];
+    }
+    mat_mul(n, T, T, W);
+    for (int r = 0; r < n * n; ++r) T[r] = W[r];
+  }
+  for (int r = 0; r < n * n; ++r) {
+    E[r] = T[r];
+    if (dE) dE[r] = dT[r];
+  }
+}
+
+__device__ void rate_phi(double* ws, int I, const double* om, double dT, double* Phi) {
+  double* A = ws + kFitGA;
+  rate_generator(I, om, A);
+  for (int r = 0; r < I * I; ++r) A[r] *= dT;
+  expm_dir(ws, I, A, nullptr, Phi, nullptr);
+}
+
+__device__ double rate_cost(const DriverArgs& a, double* ws, int I, int k, const double* om) {
+  double* Phi = ws + kFitCPhi;
+  double* p = ws + kFitCp;
+  double* q = ws + kFitCq;
+  rate_phi(ws, I, om, a.dT, Phi);
+  for (int i = 0; i < I; ++i) p[i] = frac_at(a, 0, i);
+  double s = 0.0;
+  for (int n = 1; n <= k; ++n) {
+    mat_vec(I, Phi, p, q);
+    for (int i = 0; i < I; ++i) {
+      p[i] = q[i];
+      const double r = frac_at(a, n, i) - p[i];
+      s += r * r;
+    }
+  }
+  return s;
+}
+
+// J^T J and J^T r at omega (J = d model / d omega, r = data - model)
+__device__ void rate_normal(const DriverArgs& a, double* ws, int I, int k, const double* om, double* JtJ,
+                            double* g) {
+  const int np = I * (I - 1);
+  double* A = ws + kFitNA;
+  double* Phi = ws + kFitNPhi;
+  double* dPhi = ws + kFitDPhi;  // [np][16]
+  double* e = ws + kFitE;
+  double* dA = ws + kFitDA;
+  double* P = ws + kFitP;
+  double* Q = ws + kFitQ;
+  double* S = ws + kFitS;        // [np][4]
+  double* S2 = ws + kFitS2;
+  double* S3 = ws + kFitS3;
+  rate_generator(I, om, A);
+  for (int r = 0; r < I * I; ++r) A[r] *= a.dT;
+  for (int p = 0; p < np; ++p) {
+    for (int q = 0; q < kMaxRates; ++q) e[q] = 0.0;
+    e[p] = 1.0;
+    rate_generator(I, e, dA);
+    for (int r = 0; r < I * I; ++r) dA[r] *= a.dT;
+    expm_dir(ws, I, A, dA, Phi, dPhi + 16 * p);
+  }
+  for (int r = 0; r < np * np; ++r) JtJ[r] = 0.0;
+  for (int p = 0; p < np; ++p) g[p] = 0.0;
+  for (int i = 0; i < I; ++i) P[i] = frac_at(a, 0, i);
+  for (int p = 0; p < np; ++p)
+    for (int i = 0; i < I; ++i) S[4 * p + i] = 0.0;
+  for (int n = 1; n <= k; ++n) {
+    for (int p = 0; p < np; ++p) {
+      mat_vec(I, dPhi + 16 * p, P, S2);
+      mat_vec(I, Phi, S + 4 * p, S3);
+      for (int i = 0; i < I; ++i) S[4 * p + i] = S2[i] + S3[i];
+    }
+    mat_vec(I, Phi, P, Q);
+    for (int i = 0; i < I; ++i) P[i] = Q[i];
+    for (int i = 0; i < I; ++i) {
+      const double r = frac_at(a, n, i) - P[i];
+      for (int p = 0; p < np; ++p) {
+        g[p] += S[4 * p + i] * r;
+        for (int q = 0; q < np; ++q) JtJ[p * np + q] += S[4 * p + i] * S[4 * q + i];
+      }
+    }
+  }
+}
+
+// M x = b for symmetric positive definite M (Cholesky); false if not SPD
+__device__ bool spd_solve(double* ws, int n, const double* M, const double* b, double* x) {
+  double* L = ws + kFitL;
+  double* y = ws + kFitY;
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = M[i * n + j];
+      for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+      if (i == j) {
+        if (!(s > 0.0) || !isfinite(s)) return false;
+        L[i * n + i] = sqrt(s);
+      } else {
+        L[i * n + j] = s / L[j * n + j];
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+    y[i] = s / L[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+    x[i] = s / L[i * n + i];
+  }
+  return true;
+}
+
+// normal equations in theta: J_theta = J_omega diag(2 theta)
+__device__ void to_theta(int np, const double* th, double* JtJ, double* g) {
+  for (int p = 0; p < np; ++p) {
+    g[p] *= 2.0 * th[p];
+    for (int q = 0; q < np; ++q) JtJ[p * np + q] *= (2.0 * th[p]) * (2.0 * th[q]);
+  }
+}
+
+__device__ bool rate_fit(const DriverArgs& a, int I, int k, double* om) {
+  const int np = I * (I - 1);
+  if (I < 2 || I > kMaxRegions || k < I || a.fit == nullptr) return false;
+  double* ws = a.fit;
+  const double dT = a.dT;
+  double* th = ws + kFitTh;
+  double* nth = ws + kFitNth;
+  double* nw = ws + kFitNw;
+  {
+    double* Sxx = ws + kFitSxx;
+    double* Syx = ws + kFitSyx;
+    double* Phi0 = ws + kFitPhi0;
+    double* rhs = ws + kFitRhs;
+    double* x = ws + kFitX;
+    for (int r = 0; r < 16; ++r) {
+      Sxx[r] = 0.0;
+      Syx[r] = 0.0;
+    }
+    for (int n = 1; n <= k; ++n)
+      for (int p = 0; p < I; ++p)
+        for (int q = 0; q < I; ++q) {
+          Sxx[p * I + q] += frac_at(a, n - 1, p) * frac_at(a, n - 1, q);
+          Syx[p * I + q] += frac_at(a, n, p) * frac_at(a, n - 1, q);
+        }
+    const double floor_rate = 1e-3 / ((double)k * dT);
+    bool ok = true;
+    for (int p = 0; p < I && ok; ++p) {
+      for (int q = 0; q < I; ++q) rhs[q] = Syx[p * I + q];
+      if (!spd_solve(ws, I, Sxx, rhs, x)) {
+        ok = false;
+      } else {
+        for (int q = 0; q < I; ++q) Phi0[p * I + q] = x[q];
+      }
+    }
+    for (int i = 0; i < I; ++i)
+      for (int j = 0; j < I; ++j) {
+        if (j == i) continue;
+        const double w = ok ? Phi0[j * I + i] / dT : 1.0 / ((double)I * (double)k * dT);
+        th[i * (I - 1) + (j < i ? j : j - 1)] = sqrt(isfinite(w) && w > floor_rate ? w : floor_rate);
+      }
+  }
+  const double th_floor = sqrt(1e-3 / ((double)k * dT));
+  for (int p = 0; p < np; ++p) om[p] = th[p] * th[p];
+  double lambda = 1e-3;
+  double cost = rate_cost(a, ws, I, k, om);
+  double* JtJ = ws + kFitJtJ;
+  double* g = ws + kFitG;
+  double* M = ws + kFitM;
+  double* st = ws + kFitSt;
+  for (int it = 0; it < 100; ++it) {
+    rate_normal(a, ws, I, k, om, JtJ, g);
+    to_theta(np, th, JtJ, g);
+    for (int r = 0; r < np * np; ++r) M[r] = JtJ[r];
+    for (int p = 0; p < np; ++p) M[p * np + p] = JtJ[p * np + p] * (1.0 + lambda);
+    if (!spd_solve(ws, np, M, g, st)) {
+      lambda *= 10.0;
+      if (lambda > 1e12) break;
+      continue;
+    }
+    for (int p = 0; p < np; ++p) {
+      const double cap = 2.0 * fmax(fabs(th[p]), th_floor);
+      nth[p] = th[p] + fmax(-cap, fmin(cap, st[p]));
+      nw[p] = nth[p] * nth[p];
+    }
+    const double ncost = rate_cost(a, ws, I, k, nw);
+    if (isfinite(ncost) && ncost < cost) {
+      double rel = 0.0;
+      for (int p = 0; p < np; ++p) {
+        th[p] = nth[p];
+        om[p] = nw[p];
+        rel = fmax(rel, fabs(st[p]) / (fabs(th[p]) + 1e-300));
+      }
+      cost = ncost;
+      lambda /= 10.0;
+      if (rel < 1e-15) break;
+    } else {
+      lambda *= 10.0;
+      if (lambda > 1e12) break;
+    }
+  }
+  for (int it = 0; it < 3; ++it) {
+    rate_normal(a, ws, I, k, om, JtJ, g);
+    to_theta(np, th, JtJ, g);
+    if (!spd_solve(ws, np, JtJ, g, st)) break;
+    for (int p = 0; p < np; ++p) {
+      nth[p] = th[p] + st[p];
+      nw[p] = nth[p] * nth[p];
+    }
+    const double ncost = rate_cost(a, ws, I, k, nw);
+    if (!(isfinite(ncost) && ncost <= cost)) break;
+    for (int p = 0; p < np; ++p) {
+      th[p] = nth[p];
+      om[p] = nw[p];
+    }
+    cost = ncost;
+  }
+  for (int p = 0; p < np; ++p)
+    if (!isfinite(om[p]) || !(om[p] >= 0.0)) return false;
+  return true;
+}
+
 }  // namespace
 
 // One warp per problem.  sweep == 0: lifting (k = 0).  sweep k >= 1: the
@@ -283,15 +642,18 @@ __device__ void driver_body(const DriverArgs& a) {
     // rho^0_0 = R(u0); rho^0_{n+1} = C_n(rho^0_n); u^0_n = T(rho^0_n, u0)
     const double* s0 = a.stats_u0;
     Macro r;
-    r.frac[0] = s0[0] / (double)a.P; r.mean[0] = s0[1]; r.var[0] = s0[2];
-    r.frac[1] = s0[5] / (double)a.P; r.mean[1] = s0[6]; r.var[1] = s0[7];
-    if (I < 2) { r.frac[1] = 0.0; r.mean[1] = 0.0; r.var[1] = 0.0; }
+    macro_zero(r);
+    for (int i = 0; i < I; ++i) {
+      const double* si = s0 + stat_region(i);
+      r.frac[i] = si[0] / (double)a.P; r.mean[i] = si[1]; r.var[i] = si[2];
+    }
     macro_store(a, a.rho, r);
     for (int n = 0; n <= N; ++n) {
-      double* af = a.aff + (size_t)n * 2 * kAff;
-      for (int i = 0; i < 2; ++i) {
+      double* af = a.aff + (size_t)n * kMaxRegions * kAff;
+      for (int i = 0; i < kMaxRegions; ++i) {
         if (i < I) {
-          matching_record(af + i * kAff, s0[i * 5], s0[i * 5 + 1], s0[i * 5 + 2], r.mean[i], r.var[i]);
+          const double* si = s0 + stat_region(i);
+          matching_record(af + i * kAff, si[0], si[1], si[2], r.mean[i], r.var[i]);
         } else {
           set_aff(af + i * kAff, kMatchIdentity, 0.0, 0.0, 0.0);
         }
@@ -299,8 +661,11 @@ __device__ void driver_body(const DriverArgs& a) {
       if (n == N) break;
       Macro nx;
       coarse(a, r, nx);
-      double* c = a.cache + (size_t)n * 4;
-      c[0] = nx.mean[0]; c[1] = nx.var[0]; c[2] = nx.mean[1]; c[3] = nx.var[1];
+      double* c = a.cache + (size_t)n * 2 * kMaxRegions;
+      for (int i = 0; i < kMaxRegions; ++i) {
+        c[2 * i] = nx.mean[i];
+        c[2 * i + 1] = nx.var[i];
+      }
       macro_store(a, a.rho + (size_t)(n + 1) * kMom, nx);
       r = nx;
     }
@@ -310,8 +675,8 @@ __device__ void driver_body(const DriverArgs& a) {
     ctl[3] = 0.0;  // done
     ctl[4] = 0.0;  // accepted
     ctl[5] = 0.0;  // rejected
-    ctl[6] = 0.0;  // fit alpha
-    ctl[7] = 0.0;  // fit beta
+    ctl[6] = 0.0;  // fit alpha (two regions)
+    ctl[7] = 0.0;  // fit beta (two regions)
     ctl[8] = 0.0;  // fit used
     return;
   }
@@ -320,12 +685,18 @@ __device__ void driver_body(const DriverArgs& a) {
   // Def. 3.4: fit the fractions of the exact slice ends t_0..t_k
   bool learn = false;
   double alpha = 0.0, beta = 0.0;
+  double om[kMaxRates];
   if (a.variant == MMP_LEARNING && I == 2 && k >= 2) {
     const double p0 = frac0_at(a, 0);
     learn = lsq_fit(a, k, p0, alpha, beta);
   }
   if (lane != 0) return;
+  if (a.variant == MMP_LEARNING && I >= 3 && k >= I) learn = rate_fit(a, I, k, om);
+  double Phi[16];
+  if (learn && I >= 3) rate_phi(a.fit, I, om, a.dT, Phi);
   const double pk = frac0_at(a, k);
+  double phat[kMaxRegions];  // extrapolated fractions (I >= 3), from those of t_k
+  for (int i = 0; i < I; ++i) phat[i] = frac_at(a, k, i);
 
   double change = 0.0;
   int acc = 0, rej = 0;
@@ -336,16 +707,15 @@ __device__ void driver_body(const DriverArgs& a) {
     Macro av;
     coarse(a, cur, av);
     const double* b = a.stats + (size_t)n * kStat;
-    double* cache = a.cache + (size_t)n * 4;
-    double* af = a.aff + (size_t)(n + 1) * 2 * kAff;
+    double* cache = a.cache + (size_t)n * 2 * kMaxRegions;
+    double* af = a.aff + (size_t)(n + 1) * kMaxRegions * kAff;
     Macro nx;
-    for (int i = 0; i < 2; ++i) {
-      nx.frac[i] = 0.0; nx.mean[i] = 0.0; nx.var[i] = 0.0;
-      set_aff(af + i * kAff, kMatchIdentity, 0.0, 0.0, 0.0);
-    }
+    macro_zero(nx);
+    for (int i = 0; i < kMaxRegions; ++i) set_aff(af + i * kAff, kMatchIdentity, 0.0, 0.0, 0.0);
     for (int i = 0; i < I; ++i) {
-      const double cnt = b[i * 5], bm = b[i * 5 + 1], bv = b[i * 5 + 2];
-      const double bmin = b[i * 5 + 3], bmax = b[i * 5 + 4];
+      const double* bi = b + stat_region(i);
+      const double cnt = bi[0], bm = bi[1], bv = bi[2];
+      const double bmin = bi[3], bmax = bi[4];
       if (!(fabs(bm) < INFINITY) || !(bv < INFINITY)) numeric_bad = true;
       if (cnt <= 0.0) {
         // empty region: carry the coarse prediction, move nothing
@@ -367,7 +737,7 @@ __device__ void driver_body(const DriverArgs& a) {
         if (bv == 0.0) {
           accept = false;
         } else {
-          accept = stays_in_region(a, i, i == 0 ? bmax : bmin, delta, sm1, bm);
+          accept = stays_in_region(a, i, bmin, bmax, delta, sm1, bm);
         }
       }
       if (accept) {
@@ -383,18 +753,30 @@ __device__ void driver_body(const DriverArgs& a) {
     }
     // fractions come from the fine propagator (Def. 3.2), or from the
     // learned model beyond the exact slices (Def. 3.4)
-    for (int i = 0; i < I; ++i) nx.frac[i] = b[i * 5] / (double)a.P;
+    for (int i = 0; i < I; ++i) nx.frac[i] = b[stat_region(i)] / (double)a.P;
     if (learn && n + 1 > k) {
-      const double p0hat = pk + (pk - beta) * expm1(alpha * (double)(n + 1 - k) * a.dT);
-      nx.frac[0] = p0hat;
-      nx.frac[1] = 1.0 - p0hat;
+      if (I == 2) {
+        const double p0hat = pk + (pk - beta) * expm1(alpha * (double)(n + 1 - k) * a.dT);
+        nx.frac[0] = p0hat;
+        nx.frac[1] = 1.0 - p0hat;
+      } else {
+        double q[kMaxRegions];
+        mat_vec(I, Phi, phat, q);
+        for (int i = 0; i < I; ++i) {
+          phat[i] = q[i];
+          nx.frac[i] = q[i];
+        }
+      }
     }
     if (I < 2) nx.frac[0] = 1.0;
-    cache[0] = av.mean[0]; cache[1] = av.var[0]; cache[2] = av.mean[1]; cache[3] = av.var[1];
+    for (int i = 0; i < kMaxRegions; ++i) {
+      cache[2 * i] = av.mean[i];
+      cache[2 * i + 1] = av.var[i];
+    }
     double* rr = a.rho + (size_t)(n + 1) * kMom;
-    const double oldM = rr[6], oldV = rr[7];
+    const double oldM = rr[kMomM], oldV = rr[kMomV];
     macro_store(a, rr, nx);
-    change = fmax(change, fmax(fabs(rr[6] - oldM), fabs(rr[7] - oldV)));
+    change = fmax(change, fmax(fabs(rr[kMomM] - oldM), fabs(rr[kMomV] - oldV)));
     cur = nx;
   }
   if (numeric_bad || !(change < INFINITY)) atomicOr(a.status, kStatusNumeric);

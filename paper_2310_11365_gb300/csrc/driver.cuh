@@ -5,22 +5,25 @@
 
 namespace mmp {
 
+constexpr int kFitScratch = 1088;  // doubles of fit scratch per problem (rate model, I >= 3)
+
 struct DriverArgs {
   double nc3, c1, kappa, c0, B, BE, B0;  // model (nc3 = -c3)
   int N, I, variant, precision;
   int coarse_model;                      // MMP_COARSE_*
   double dT, hc;                         // slice length, coarse substep
   int nc;                                // coarse substeps per slice
-  double thr;
+  double thr, thr2, thr3;  // region boundaries t_1 < t_2 < t_3 (the first I - 1)
   long long P;
   double tol;
   int max_sweeps;
-  const double* stats;     // [N][16] restriction of F_n(u^{k-1}_n), row n
-  const double* stats_u0;  // [16] restriction of u0
-  double* rho;             // [N+1][8] macro state: frac0, mean0, var0, frac1, mean1, var1, M, V
-  double* cache;           // [N][4] C_n(rho^{k-1}_n): mean0, var0, mean1, var1
-  double* aff;             // [N+1][2][4] matching records for the inputs u^k_n
+  const double* stats;     // [N][kStat] restriction of F_n(u^{k-1}_n), row n
+  const double* stats_u0;  // [kStat] restriction of u0
+  double* rho;             // [N+1][kMom] macro state (MMP_MOMENT_STRIDE layout)
+  double* cache;           // [N][2 kMaxRegions] C_n(rho^{k-1}_n): (mean_i, var_i) per region
+  double* aff;             // [N+1][kMaxRegions][kAff] matching records for the inputs u^k_n
   double* ctl;             // control block (see k_driver)
+  double* fit;             // [kFitScratch] working arrays of the rate-model fit
   unsigned* status;
   int sweep;               // 0 = lifting, k >= 1 = after fine sweep k
 };

@@ -16,17 +16,17 @@ struct FineArgs {
   long long P;                 // particles
   int Q;                       // quads = ceil(P / 4)
   long long pitch;             // elements between slice rows (multiple of 4)
-  int n_regions;
-  double thr;
+  int n_regions;               // 1 .. kMaxRegions
+  double thr, thr2, thr3;      // region boundaries t_1 < t_2 < t_3 (the first n_regions - 1)
   uint32_t key0, key1, ptag;   // Philox key and problem tag
   int slice_begin, n_tasks;    // task t is slice slice_begin + t
   const void* src0;            // input of slice 0, and of every slice when src == nullptr
   const void* src;             // rows: input of slice n is row n - 1
   void* dst;                   // output rows (nullptr: no store)
   int dst_fixed;               // 1: every task writes row 0
-  const double* aff;           // matching records [row][2][4] (nullptr: identity)
+  const double* aff;           // matching records [row][kMaxRegions][kAff] (nullptr: identity)
   int aff_fixed;
-  double* stats;               // restriction records [row][16]
+  double* stats;               // restriction records [row][kStat]
   int stats_fixed;
   int G;                       // CTAs per slice
   int nq;                      // quads per thread (shared-memory layout)

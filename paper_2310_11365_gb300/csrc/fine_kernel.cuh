@@ -65,8 +65,20 @@ struct GroupShared {
   double gsumd[2];
   double tot[kNV];            // group totals, broadcast
   float cf[16];               // float copies of the task's coefficients (see fine_task)
+  float afff[kMaxRegions][3]; // the task's matching records (a, b, c) per region, float particles
+  double affd[kMaxRegions][3];// the same for double particles
+  int amode[kMaxRegions];     // their modes
   int abort;
 };
+
+// Region index of x: D_0 = {x < t1}, D_i = {t_i <= x < t_{i+1}}, D_{I-1} = {x >= t_{I-1}}.
+template <typename R>
+__device__ __forceinline__ int region_of(R x, int I, R t1, R t2, R t3) {
+  if (I < 2 || x < t1) return 0;
+  if (I < 3 || x < t2) return 1;
+  if (I < 4 || x < t3) return 2;
+  return 3;
+}
 
 // Group-reduction context of one CTA.
 //
@@ -521,6 +533,21 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
     sh.cf[11] = (float)a.sqrt_h;
     sh.cf[12] = (float)(a.h * a.nc3);
     sh.cf[13] = (float)(a.h * a.c1);
+    sh.cf[14] = (float)a.thr2;
+    sh.cf[15] = (float)a.thr3;
+  }
+  if (tid < kMaxRegions) {
+    // this slice's matching record of region tid (identity past n_regions)
+    int mode = kMatchIdentity;
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+    if (a.aff != nullptr && tid < a.n_regions) {
+      const double* af = a.aff + ((size_t)(a.aff_fixed ? 0 : n) * kMaxRegions + tid) * kAff;
+      mode = (int)af[0];
+      p0 = af[1]; p1 = af[2]; p2 = af[3];
+    }
+    sh.amode[tid] = mode;
+    sh.affd[tid][0] = p0; sh.affd[tid][1] = p1; sh.affd[tid][2] = p2;
+    sh.afff[tid][0] = (float)p0; sh.afff[tid][1] = (float)p1; sh.afff[tid][2] = (float)p2;
   }
   __syncthreads();
   const bool fl = sizeof(R) == 4;
@@ -538,7 +565,11 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   const R sqh = fl ? (R)sh.cf[11] : (R)a.sqrt_h;
   const R hn3 = fl ? (R)sh.cf[12] : (R)(a.h * a.nc3);
   const R hc1 = fl ? (R)sh.cf[13] : (R)(a.h * a.c1);
-  const bool two = a.n_regions > 1;
+  const R thr2 = fl ? (R)sh.cf[14] : (R)a.thr2;
+  const R thr3 = fl ? (R)sh.cf[15] : (R)a.thr3;
+  const int nreg = a.n_regions;
+  auto region = [&](R x) { return region_of<R>(x, nreg, thr, thr2, thr3); };
+  auto aff_param = [&](int r, int k) -> R { return fl ? (R)sh.afff[r][k] : (R)sh.affd[r][k]; };
   const unsigned E = grp.epoch;  // first epoch of this task
 
   {
@@ -548,17 +579,11 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   int flips = 0;
   R s_in = (R)0;
   {
-    int mode0 = kMatchIdentity, mode1 = kMatchIdentity;
-    R a0 = 0, b0 = 0, c0m = 0, a1 = 0, b1 = 0, c1m = 0;
-    if (a.aff != nullptr) {
-      const double* af = a.aff + (size_t)(a.aff_fixed ? 0 : n) * 2 * kAff;
-      mode0 = (int)af[0];
-      mode1 = two ? (int)af[kAff] : kMatchIdentity;
-      a0 = (R)af[1]; b0 = (R)af[2]; c0m = (R)af[3];
-      a1 = (R)af[kAff + 1]; b1 = (R)af[kAff + 2]; c1m = (R)af[kAff + 3];
+    bool match = false, redraw = false;
+    for (int r = 0; r < nreg; ++r) {
+      match = match || sh.amode[r] != kMatchIdentity;
+      redraw = redraw || sh.amode[r] == kMatchRedraw;
     }
-    const bool match = mode0 != kMatchIdentity || mode1 != kMatchIdentity;
-    const bool redraw = mode0 == kMatchRedraw || mode1 == kMatchRedraw;
 #pragma unroll kUnroll
     for (int i = 0; i < loop_n; ++i) {
       R v[4] = {0, 0, 0, 0};
@@ -573,26 +598,34 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
           for (int w = 0; w < 4; ++w) v[w] = w < plast ? src[4 * (size_t)q + w] : (R)0;
         }
         if (match) {
-          R z[4] = {0, 0, 0, 0};
-          R zr[4] = {0, 0, 0, 0};
+          int reg[4];
+#pragma unroll
+          for (int w = 0; w < 4; ++w) reg[w] = region(v[w]);
+          R y[4];
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const int r = reg[w];
+            y[w] = sh.amode[r] == kMatchAffine
+                       ? apply_affine(v[w], aff_param(r, 0), aff_param(r, 1), aff_param(r, 2))
+                       : v[w];
+          }
           if (redraw) {
-            normals4<R>(philox4x32_10(rng_counter((uint32_t)q, 0u, (uint32_t)n, 2u, a.ptag), a.key0, a.key1), z);
-            if (two)
-              normals4<R>(philox4x32_10(rng_counter((uint32_t)q, 1u, (uint32_t)n, 2u, a.ptag), a.key0, a.key1), zr);
+            // V u = 0 branch: tag-2 draws of region r's stream (j = r)
+            for (int r = 0; r < nreg; ++r) {
+              if (sh.amode[r] != kMatchRedraw) continue;
+              if (reg[0] != r && reg[1] != r && reg[2] != r && reg[3] != r) continue;
+              R z[4];
+              normals4<R>(philox4x32_10(rng_counter((uint32_t)q, (uint32_t)r, (uint32_t)n, 2u, a.ptag), a.key0,
+                                        a.key1), z);
+#pragma unroll
+              for (int w = 0; w < 4; ++w)
+                if (reg[w] == r) y[w] = fmaR(aff_param(r, 1), z[w], aff_param(r, 0));
+            }
           }
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
-            const R xv = v[w];
-            const int r = (two && !(xv < thr)) ? 1 : 0;
-            const int mode = r ? mode1 : mode0;
-            R y = xv;
-            if (mode == kMatchAffine) {
-              y = r ? apply_affine(xv, a1, b1, c1m) : apply_affine(xv, a0, b0, c0m);
-            } else if (mode == kMatchRedraw) {
-              y = r ? fmaR(b1, zr[w], a1) : fmaR(b0, z[w], a0);
-            }
-            v[w] = y;
-            if (two && ((!(y < thr)) ? 1 : 0) != r && (4 * (long long)q + w < a.P)) flips += 1;
+            if (nreg > 1 && region(y[w]) != reg[w] && (4 * (long long)q + w < a.P)) flips += 1;
+            v[w] = y[w];
           }
         }
         // zero the lanes past P so that sums see only real particles
@@ -772,8 +805,8 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   // pass 1 (with the store): apply the pending shift, counts and sums per region
   {
     R* dst = a.dst != nullptr ? (R*)a.dst + (size_t)(a.dst_fixed ? 0 : n) * a.pitch : nullptr;
-    int n0 = 0, n1 = 0;
-    Acc<R> s0, s1;
+    int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+    Acc<R> s0, s1, s2, s3;
     const bool shift = kLag && nf > 0;
 #pragma unroll kUnroll
     for (int i = 0; i < loop_n; ++i) {
@@ -799,36 +832,50 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
           if (w < valid) {
-            if (two && !(x4[w] < thr)) {
-              n1 += 1;
-              s1.add(x4[w]);
-            } else {
+            const int r = region(x4[w]);
+            if (r == 0) {
               n0 += 1;
               s0.add(x4[w]);
+            } else if (r == 1) {
+              n1 += 1;
+              s1.add(x4[w]);
+            } else if (r == 2) {
+              n2 += 1;
+              s2.add(x4[w]);
+            } else {
+              n3 += 1;
+              s3.add(x4[w]);
             }
           }
         }
       }
     }
-    double v[5] = {(double)n0, s0.get(), (double)n1, s1.get(), (double)flips};
-    warp_reduce_to_shared<5>(sh, v, 0u, 0u);
+    double v[9] = {(double)n0, s0.get(), (double)n1, s1.get(), (double)flips,
+                   (double)n2, s2.get(), (double)n3, s3.get()};
+    warp_reduce_to_shared<9>(sh, v, 0u, 0u);
     __syncthreads();
     const unsigned e = grp.epoch++;
-    if (warp == 0 && !group_finish<5>(sh, grp, e, 0u, 0u) && lane == 0) sh.abort = 1;
+    if (warp == 0 && !group_finish<9>(sh, grp, e, 0u, 0u) && lane == 0) sh.abort = 1;
     __syncthreads();
     if (sh.abort) return false;
   }
-  const double cnt0 = sh.tot[0], cnt1 = sh.tot[2];
-  const double mean0 = cnt0 > 0 ? sh.tot[1] / cnt0 : 0.0;
-  const double mean1 = cnt1 > 0 ? sh.tot[3] / cnt1 : 0.0;
-  const double gmean = (sh.tot[1] + sh.tot[3]) / (double)a.P;
+  double cnt[kMaxRegions], mean[kMaxRegions];
+  {
+    const int ci[kMaxRegions] = {0, 2, 5, 7};
+    for (int r = 0; r < kMaxRegions; ++r) {
+      cnt[r] = sh.tot[ci[r]];
+      mean[r] = cnt[r] > 0 ? sh.tot[ci[r] + 1] / cnt[r] : 0.0;
+    }
+  }
+  const double gmean = (((sh.tot[1] + sh.tot[3]) + sh.tot[6]) + sh.tot[8]) / (double)a.P;
   const double flips_tot = sh.tot[4];
   __syncthreads();
   // pass 2: centred sums and extremes
   {
-    const Centre<R> cg(gmean), c0c(mean0), c1c(mean1);
-    Acc<R> ss0, ss1, ssg;
+    const Centre<R> cg(gmean), c0c(mean[0]), c1c(mean[1]), c2c(mean[2]), c3c(mean[3]);
+    Acc<R> ss0, ss1, ss2, ss3, ssg;
     R lo0 = (R)INFINITY, hi0 = (R)-INFINITY, lo1 = (R)INFINITY, hi1 = (R)-INFINITY;
+    R lo2 = (R)INFINITY, hi2 = (R)-INFINITY, lo3 = (R)INFINITY, hi3 = (R)-INFINITY;
 #pragma unroll kUnroll
     for (int i = 0; i < loop_n; ++i) {
       if (i < nq) {
@@ -842,49 +889,61 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
             const R xv = x4[w];
             const R dg = cg.diff(xv);
             ssg.add(dg * dg);
-            if (two && !(xv < thr)) {
-              const R dd = c1c.diff(xv);
-              ss1.add(dd * dd);
-              lo1 = lo1 < xv ? lo1 : xv;
-              hi1 = hi1 > xv ? hi1 : xv;
-            } else {
+            const int r = region(xv);
+            if (r == 0) {
               const R dd = c0c.diff(xv);
               ss0.add(dd * dd);
               lo0 = lo0 < xv ? lo0 : xv;
               hi0 = hi0 > xv ? hi0 : xv;
+            } else if (r == 1) {
+              const R dd = c1c.diff(xv);
+              ss1.add(dd * dd);
+              lo1 = lo1 < xv ? lo1 : xv;
+              hi1 = hi1 > xv ? hi1 : xv;
+            } else if (r == 2) {
+              const R dd = c2c.diff(xv);
+              ss2.add(dd * dd);
+              lo2 = lo2 < xv ? lo2 : xv;
+              hi2 = hi2 > xv ? hi2 : xv;
+            } else {
+              const R dd = c3c.diff(xv);
+              ss3.add(dd * dd);
+              lo3 = lo3 < xv ? lo3 : xv;
+              hi3 = hi3 > xv ? hi3 : xv;
             }
           }
         }
       }
     }
-    double v[7] = {ss0.get(), ss1.get(), ssg.get(), (double)lo0, (double)hi0, (double)lo1, (double)hi1};
-    const unsigned mn = (1u << 3) | (1u << 5), mx = (1u << 4) | (1u << 6);
-    warp_reduce_to_shared<7>(sh, v, mn, mx);
+    double v[13] = {ss0.get(), ss1.get(), ssg.get(), (double)lo0, (double)hi0, (double)lo1, (double)hi1,
+                    ss2.get(), ss3.get(), (double)lo2, (double)hi2, (double)lo3, (double)hi3};
+    const unsigned mn = (1u << 3) | (1u << 5) | (1u << 9) | (1u << 11);
+    const unsigned mx = (1u << 4) | (1u << 6) | (1u << 10) | (1u << 12);
+    warp_reduce_to_shared<13>(sh, v, mn, mx);
     __syncthreads();
     const unsigned e = grp.epoch++;
-    if (warp == 0 && !group_finish<7>(sh, grp, e, mn, mx) && lane == 0) sh.abort = 1;
+    if (warp == 0 && !group_finish<13>(sh, grp, e, mn, mx) && lane == 0) sh.abort = 1;
     __syncthreads();
     if (sh.abort) return false;
   }
   if (g == 0 && tid == 0 && a.stats != nullptr) {
     double* st = a.stats + (size_t)(a.stats_fixed ? 0 : n) * kStat;
-    st[0] = cnt0;
-    st[1] = mean0;
-    st[2] = cnt0 > 0 ? sh.tot[0] / cnt0 : 0.0;
-    st[3] = sh.tot[3];
-    st[4] = sh.tot[4];
-    st[5] = cnt1;
-    st[6] = mean1;
-    st[7] = cnt1 > 0 ? sh.tot[1] / cnt1 : 0.0;
-    st[8] = sh.tot[5];
-    st[9] = sh.tot[6];
-    st[10] = gmean;
-    st[11] = sh.tot[2] / (double)a.P;
-    st[12] = flips_tot;
-    st[13] = m_in;
-    st[14] = 0.0;
-    st[15] = 0.0;
-    if (!(fabs(gmean) < INFINITY) || !(st[11] < INFINITY)) atomicOr(a.status, kStatusNumeric);
+    const int si[kMaxRegions] = {0, 1, 7, 8};   // centred sum of region r in sh.tot
+    const int li[kMaxRegions] = {3, 5, 9, 11};  // its minimum (maximum at li + 1)
+    for (int k = 0; k < kStat; ++k) st[k] = 0.0;
+    for (int r = 0; r < kMaxRegions; ++r) {
+      double* sr = st + stat_region(r);
+      sr[0] = cnt[r];
+      sr[1] = mean[r];
+      sr[2] = cnt[r] > 0 ? sh.tot[si[r]] / cnt[r] : 0.0;
+      sr[3] = sh.tot[li[r]];
+      sr[4] = sh.tot[li[r] + 1];
+    }
+    st[kStatM] = gmean;
+    st[kStatV] = sh.tot[2] / (double)a.P;
+    st[kStatFlips] = flips_tot;
+    st[kStatInMean] = m_in;
+    if (!(fabs(gmean) < INFINITY) || !(st[kStatV] < INFINITY)) atomicOr(a.status, kStatusNumeric);
     if (flips_tot > 0.0) atomicOr(a.status, kStatusRegionFlip);
   }
   }

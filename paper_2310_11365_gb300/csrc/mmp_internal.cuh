@@ -14,12 +14,19 @@ namespace mmp {
 
 constexpr int kTPB = 256;          // threads per block of the fine kernel
 constexpr int kWarps = kTPB / 32;
-constexpr int kNV = 8;             // values per group reduction slot
+constexpr int kNV = 16;            // values per group reduction slot
 constexpr int kSlots = 4;          // publication slots per CTA (a ring indexed by epoch)
 constexpr int kSeatDoubles = kSlots * kNV;  // reduction scratch per CTA of a group
 constexpr int kStat = MMP_STAT_STRIDE;
 constexpr int kMom = MMP_MOMENT_STRIDE;
 constexpr int kAff = 4;            // doubles per (slice, region) matching record
+constexpr int kMaxRegions = MMP_MAX_REGIONS;
+// offsets of region r's values in a moment row and a restriction record
+__host__ __device__ constexpr int mom_region(int r) { return MMP_MOMENT_REGION(r); }
+__host__ __device__ constexpr int stat_region(int r) { return MMP_STAT_REGION(r); }
+constexpr int kMomM = 6, kMomV = 7;        // global mean, variance in a moment row
+constexpr int kStatM = 10, kStatV = 11;    // global mean, variance in a restriction record
+constexpr int kStatFlips = 12, kStatInMean = 13;
 constexpr int kMaxNQ = 8;          // largest quads-per-thread template
 
 // Polls of a bounded group wait before it backs off with nanosleep, for

@@ -22,8 +22,19 @@ LIB_PATH = os.path.join(_HERE, "lib", "libmmp.so")
 MMP_OK = 0
 MMP_FP64, MMP_MIXED = 0, 1
 MMP_UNIMODAL, MMP_MULTIMODAL, MMP_LEARNING = 0, 1, 2
-MOMENT_STRIDE = 8
-STAT_STRIDE = 16
+MOMENT_STRIDE = 16   # MMP_MOMENT_STRIDE
+STAT_STRIDE = 32     # MMP_STAT_STRIDE
+MAX_REGIONS = 4      # MMP_MAX_REGIONS
+
+
+def moment_region(i: int) -> int:
+    """Offset of region i's (fraction, mean, variance) in a moment row."""
+    return 3 * i if i < 2 else 3 * i + 2
+
+
+def stat_region(i: int) -> int:
+    """Offset of region i's (count, mean, variance, min, max) in a restriction record."""
+    return 5 * i if i < 2 else 5 * i + 6
 N_THETA = 7         # MMP_N_THETA: (c3, c1, kappa, c0, B0, B, BE)
 
 ERRORS = {
@@ -62,6 +73,7 @@ class ProblemDesc(C.Structure):
         ("coarse_h", C.c_double), ("n_regions", C.c_int), ("threshold", C.c_double),
         ("variant", C.c_int), ("precision", C.c_int), ("seed", C.c_ulonglong),
         ("problem_tag", C.c_uint), ("tol", C.c_double), ("max_iter", C.c_int), ("coarse_model", C.c_int),
+        ("threshold2", C.c_double), ("threshold3", C.c_double),
     ]
 
 
@@ -130,7 +142,7 @@ def desc(p: workloads.Problem) -> ProblemDesc:
     prec = MMP_MIXED if p.precision == "mixed" else MMP_FP64
     return ProblemDesc(p.c3, p.c1, p.kappa, p.c0, p.B, p.BE, p.B0, p.m0, p.s0, p.T, p.N, p.dt, p.P,
                        p.coarse_h, p.n_regions, p.threshold, p.variant, prec, p.seed, p.problem_tag,
-                       p.tol, p.max_iter, p.coarse_model)
+                       p.tol, p.max_iter, p.coarse_model, p.threshold2, p.threshold3)
 
 
 def _descs(problems) -> C.Array:

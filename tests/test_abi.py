@@ -35,7 +35,10 @@ def test_strerror_and_version(mmplib):
 
 @pytest.mark.parametrize("bad", [
     dict(N=0), dict(N=70000), dict(P=0), dict(T=-1.0), dict(dt=0.0), dict(coarse_h=0.0),
-    dict(n_regions=3), dict(variant=7), dict(s0=-0.1), dict(c3=float("nan")), dict(tol=-1.0),
+    dict(n_regions=5), dict(n_regions=0), dict(variant=7), dict(s0=-0.1), dict(c3=float("nan")),
+    dict(tol=-1.0), dict(n_regions=3, threshold=0.5, threshold2=0.5),
+    dict(n_regions=4, threshold=-1.0, threshold2=0.0, threshold3=-0.5),
+    dict(n_regions=3, threshold=0.0, threshold2=float("inf")),
 ])
 def test_invalid_descriptor_rejected_on_host(mmplib, bad):
     p = W.config1(**bad)

@@ -28,7 +28,7 @@ def _static(mmplib, p, n, u_in):
     import torch
 
     out = torch.full_like(u_in, float("nan"))
-    st = torch.full((16,), float("nan"), dtype=torch.float64, device="cuda")
+    st = torch.full((mmplib.STAT_STRIDE,), float("nan"), dtype=torch.float64, device="cuda")
     mmplib.mmp_fine_static(p, n, u_in.data_ptr(), out.data_ptr(), st.data_ptr())
     torch.cuda.synchronize()
     return out, st.cpu().numpy()
