@@ -71,6 +71,13 @@ struct GroupShared {
   int abort;
 };
 
+// A compile-time region count (the prologue and the epilogue are compiled
+// for at most 2 and for at most 4 regions; a task takes the first when it can).
+template <int N>
+struct RegionsUpTo {
+  static constexpr int value = N;
+};
+
 // Region index of x: D_0 = {x < t1}, D_i = {t_i <= x < t_{i+1}}, D_{I-1} = {x >= t_{I-1}}.
 template <typename R>
 __device__ __forceinline__ int region_of(R x, int I, R t1, R t2, R t3) {
@@ -236,12 +243,14 @@ struct Centre;
 template <>
 struct Centre<float> {
   float hi, lo;
+  Centre() = default;
   __device__ __forceinline__ explicit Centre(double m) : hi((float)m), lo((float)(m - (double)(float)m)) {}
   __device__ __forceinline__ float diff(float x) const { return __fsub_rn(__fsub_rn(x, hi), lo); }
 };
 template <>
 struct Centre<double> {
   double m;
+  Centre() = default;
   __device__ __forceinline__ explicit Centre(double mm) : m(mm) {}
   __device__ __forceinline__ double diff(double x) const { return x - m; }
 };
@@ -578,12 +587,24 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   // ---------------- prologue: load, match, sum --------------------------
   int flips = 0;
   R s_in = (R)0;
-  {
+  // The matching records of this task's regions sit in registers (NR of
+  // them, loops over regions unrolled); with at most two regions the region
+  // of x is one comparison.
+  auto prologue = [&](auto nr_c) {
+    constexpr int NR = decltype(nr_c)::value;
+    int md[NR];
+    R pa[NR], pb[NR], pc[NR];
     bool match = false, redraw = false;
-    for (int r = 0; r < nreg; ++r) {
-      match = match || sh.amode[r] != kMatchIdentity;
-      redraw = redraw || sh.amode[r] == kMatchRedraw;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      md[r] = sh.amode[r];
+      pa[r] = aff_param(r, 0);
+      pb[r] = aff_param(r, 1);
+      pc[r] = aff_param(r, 2);
+      match = match || md[r] != kMatchIdentity;
+      redraw = redraw || md[r] == kMatchRedraw;
     }
+    auto reg_of = [&](R x) -> int { return NR == 2 ? ((nreg > 1 && !(x < thr)) ? 1 : 0) : region(x); };
 #pragma unroll kUnroll
     for (int i = 0; i < loop_n; ++i) {
       R v[4] = {0, 0, 0, 0};
@@ -599,32 +620,40 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
         }
         if (match) {
           int reg[4];
-#pragma unroll
-          for (int w = 0; w < 4; ++w) reg[w] = region(v[w]);
           R y[4];
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
-            const int r = reg[w];
-            y[w] = sh.amode[r] == kMatchAffine
-                       ? apply_affine(v[w], aff_param(r, 0), aff_param(r, 1), aff_param(r, 2))
-                       : v[w];
+            reg[w] = reg_of(v[w]);
+            int sm = md[0];
+            R sa = pa[0], sb = pb[0], sc = pc[0];
+#pragma unroll
+            for (int r = 1; r < NR; ++r) {
+              if (reg[w] == r) {
+                sm = md[r];
+                sa = pa[r];
+                sb = pb[r];
+                sc = pc[r];
+              }
+            }
+            y[w] = sm == kMatchAffine ? apply_affine(v[w], sa, sb, sc) : v[w];
           }
           if (redraw) {
             // V u = 0 branch: tag-2 draws of region r's stream (j = r)
-            for (int r = 0; r < nreg; ++r) {
-              if (sh.amode[r] != kMatchRedraw) continue;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+              if (md[r] != kMatchRedraw) continue;
               if (reg[0] != r && reg[1] != r && reg[2] != r && reg[3] != r) continue;
               R z[4];
               normals4<R>(philox4x32_10(rng_counter((uint32_t)q, (uint32_t)r, (uint32_t)n, 2u, a.ptag), a.key0,
                                         a.key1), z);
 #pragma unroll
               for (int w = 0; w < 4; ++w)
-                if (reg[w] == r) y[w] = fmaR(aff_param(r, 1), z[w], aff_param(r, 0));
+                if (reg[w] == r) y[w] = fmaR(pb[r], z[w], pa[r]);
             }
           }
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
-            if (nreg > 1 && region(y[w]) != reg[w] && (4 * (long long)q + w < a.P)) flips += 1;
+            if (nreg > 1 && reg_of(y[w]) != reg[w] && (4 * (long long)q + w < a.P)) flips += 1;
             v[w] = y[w];
           }
         }
@@ -638,6 +667,11 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
       }
       xs.put(i, v);
     }
+  };
+  if (nreg <= 2) {
+    prologue(RegionsUpTo<2>{});
+  } else {
+    prologue(RegionsUpTo<kMaxRegions>{});
   }
   // The sum of the inputs is epoch E.  The shift form reads it at the end
   // of step 0 (or right here when there are no steps); the general form
@@ -802,150 +836,168 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   __syncthreads();
 
   // ---------------- epilogue: store and restrict -----------------------
-  // pass 1 (with the store): apply the pending shift, counts and sums per region
-  {
-    R* dst = a.dst != nullptr ? (R*)a.dst + (size_t)(a.dst_fixed ? 0 : n) * a.pitch : nullptr;
-    int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
-    Acc<R> s0, s1, s2, s3;
-    const bool shift = kLag && nf > 0;
+  // Group reductions, values in this order (the first entries are those of
+  // two regions, so tasks of at most two regions reduce 5 and 7 values):
+  //   pass 1: count_0, sum_0, count_1, sum_1, flips, then (count_r, sum_r), r >= 2;
+  //   pass 2: centred_0, centred_1, centred_global, min_0, max_0, min_1, max_1,
+  //           then centred_r (r >= 2), then (min_r, max_r) (r >= 2).
+  auto epilogue = [&](auto nr_c) -> bool {
+    constexpr int NR = decltype(nr_c)::value;
+    constexpr int NV1 = 2 * NR + 1;
+    constexpr int NV2 = 3 * NR + 1;
+    auto reg_of = [&](R x) -> int { return NR == 2 ? ((nreg > 1 && !(x < thr)) ? 1 : 0) : region(x); };
+    auto i_cnt = [](int r) { return r < 2 ? 2 * r : 5 + 2 * (r - 2); };
+    auto i_ss = [](int r) { return r < 2 ? r : NR + 3 + (r - 2); };
+    auto i_lo = [](int r) { return r < 2 ? 3 + 2 * r : 2 * NR + 1 + 2 * (r - 2); };
+    // pass 1 (with the store): apply the pending shift, counts and sums per region
+    {
+      R* dst = a.dst != nullptr ? (R*)a.dst + (size_t)(a.dst_fixed ? 0 : n) * a.pitch : nullptr;
+      int cnt[NR];
+      Acc<R> sum[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) cnt[r] = 0;
+      const bool shift = kLag && nf > 0;
 #pragma unroll kUnroll
-    for (int i = 0; i < loop_n; ++i) {
-      if (i < nq) {
-        const int q = qb + tid + i * kTPB;
-        R x4[4];
-        xs.get(i, x4);
-        if (shift) {
+      for (int i = 0; i < loop_n; ++i) {
+        if (i < nq) {
+          const int q = qb + tid + i * kTPB;
+          R x4[4];
+          xs.get(i, x4);
+          if (shift) {
 #pragma unroll
-          for (int w = 0; w < 4; ++w) x4[w] = addR(x4[w], d);
-          xs.put(i, x4);
-        }
-        if (dst != nullptr) {
-          if (q != qlast || plast == 4) {
-            Quad<R>::store(dst + 4 * (size_t)q, x4);
-          } else {
-#pragma unroll
-            for (int w = 0; w < 4; ++w)
-              if (w < plast) dst[4 * (size_t)q + w] = x4[w];
+            for (int w = 0; w < 4; ++w) x4[w] = addR(x4[w], d);
+            xs.put(i, x4);
           }
-        }
-        const int valid = q == qlast ? plast : 4;
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          if (w < valid) {
-            const int r = region(x4[w]);
-            if (r == 0) {
-              n0 += 1;
-              s0.add(x4[w]);
-            } else if (r == 1) {
-              n1 += 1;
-              s1.add(x4[w]);
-            } else if (r == 2) {
-              n2 += 1;
-              s2.add(x4[w]);
+          if (dst != nullptr) {
+            if (q != qlast || plast == 4) {
+              Quad<R>::store(dst + 4 * (size_t)q, x4);
             } else {
-              n3 += 1;
-              s3.add(x4[w]);
+#pragma unroll
+              for (int w = 0; w < 4; ++w)
+                if (w < plast) dst[4 * (size_t)q + w] = x4[w];
+            }
+          }
+          const int valid = q == qlast ? plast : 4;
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            if (w < valid) {
+              const int r = reg_of(x4[w]);
+#pragma unroll
+              for (int rr = 0; rr < NR; ++rr) {
+                if (rr == r) {
+                  cnt[rr] += 1;
+                  sum[rr].add(x4[w]);
+                }
+              }
             }
           }
         }
       }
-    }
-    double v[9] = {(double)n0, s0.get(), (double)n1, s1.get(), (double)flips,
-                   (double)n2, s2.get(), (double)n3, s3.get()};
-    warp_reduce_to_shared<9>(sh, v, 0u, 0u);
-    __syncthreads();
-    const unsigned e = grp.epoch++;
-    if (warp == 0 && !group_finish<9>(sh, grp, e, 0u, 0u) && lane == 0) sh.abort = 1;
-    __syncthreads();
-    if (sh.abort) return false;
-  }
-  double cnt[kMaxRegions], mean[kMaxRegions];
-  {
-    const int ci[kMaxRegions] = {0, 2, 5, 7};
-    for (int r = 0; r < kMaxRegions; ++r) {
-      cnt[r] = sh.tot[ci[r]];
-      mean[r] = cnt[r] > 0 ? sh.tot[ci[r] + 1] / cnt[r] : 0.0;
-    }
-  }
-  const double gmean = (((sh.tot[1] + sh.tot[3]) + sh.tot[6]) + sh.tot[8]) / (double)a.P;
-  const double flips_tot = sh.tot[4];
-  __syncthreads();
-  // pass 2: centred sums and extremes
-  {
-    const Centre<R> cg(gmean), c0c(mean[0]), c1c(mean[1]), c2c(mean[2]), c3c(mean[3]);
-    Acc<R> ss0, ss1, ss2, ss3, ssg;
-    R lo0 = (R)INFINITY, hi0 = (R)-INFINITY, lo1 = (R)INFINITY, hi1 = (R)-INFINITY;
-    R lo2 = (R)INFINITY, hi2 = (R)-INFINITY, lo3 = (R)INFINITY, hi3 = (R)-INFINITY;
-#pragma unroll kUnroll
-    for (int i = 0; i < loop_n; ++i) {
-      if (i < nq) {
-        const int q = qb + tid + i * kTPB;
-        const int valid = q == qlast ? plast : 4;
-        R x4[4];
-        xs.get(i, x4);
+      double v[NV1];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          if (w < valid) {
-            const R xv = x4[w];
-            const R dg = cg.diff(xv);
-            ssg.add(dg * dg);
-            const int r = region(xv);
-            if (r == 0) {
-              const R dd = c0c.diff(xv);
-              ss0.add(dd * dd);
-              lo0 = lo0 < xv ? lo0 : xv;
-              hi0 = hi0 > xv ? hi0 : xv;
-            } else if (r == 1) {
-              const R dd = c1c.diff(xv);
-              ss1.add(dd * dd);
-              lo1 = lo1 < xv ? lo1 : xv;
-              hi1 = hi1 > xv ? hi1 : xv;
-            } else if (r == 2) {
-              const R dd = c2c.diff(xv);
-              ss2.add(dd * dd);
-              lo2 = lo2 < xv ? lo2 : xv;
-              hi2 = hi2 > xv ? hi2 : xv;
-            } else {
-              const R dd = c3c.diff(xv);
-              ss3.add(dd * dd);
-              lo3 = lo3 < xv ? lo3 : xv;
-              hi3 = hi3 > xv ? hi3 : xv;
+      for (int r = 0; r < NR; ++r) {
+        v[i_cnt(r)] = (double)cnt[r];
+        v[i_cnt(r) + 1] = sum[r].get();
+      }
+      v[4] = (double)flips;
+      warp_reduce_to_shared<NV1>(sh, v, 0u, 0u);
+      __syncthreads();
+      const unsigned e = grp.epoch++;
+      if (warp == 0 && !group_finish<NV1>(sh, grp, e, 0u, 0u) && lane == 0) sh.abort = 1;
+      __syncthreads();
+      if (sh.abort) return false;
+    }
+    double cnt[NR], mean[NR];
+    double gsum = sh.tot[1] + sh.tot[3];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      cnt[r] = sh.tot[i_cnt(r)];
+      mean[r] = cnt[r] > 0 ? sh.tot[i_cnt(r) + 1] / cnt[r] : 0.0;
+      if (r >= 2) gsum = gsum + sh.tot[i_cnt(r) + 1];
+    }
+    const double gmean = gsum / (double)a.P;
+    const double flips_tot = sh.tot[4];
+    __syncthreads();
+    // pass 2: centred sums and extremes
+    {
+      const Centre<R> cg(gmean);
+      Centre<R> cc[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) cc[r] = Centre<R>(mean[r]);
+      Acc<R> ss[NR], ssg;
+      R lo[NR], hi[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        lo[r] = (R)INFINITY;
+        hi[r] = (R)-INFINITY;
+      }
+#pragma unroll kUnroll
+      for (int i = 0; i < loop_n; ++i) {
+        if (i < nq) {
+          const int q = qb + tid + i * kTPB;
+          const int valid = q == qlast ? plast : 4;
+          R x4[4];
+          xs.get(i, x4);
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            if (w < valid) {
+              const R xv = x4[w];
+              const R dg = cg.diff(xv);
+              ssg.add(dg * dg);
+              const int r = reg_of(xv);
+#pragma unroll
+              for (int rr = 0; rr < NR; ++rr) {
+                if (rr == r) {
+                  const R dd = cc[rr].diff(xv);
+                  ss[rr].add(dd * dd);
+                  lo[rr] = lo[rr] < xv ? lo[rr] : xv;
+                  hi[rr] = hi[rr] > xv ? hi[rr] : xv;
+                }
+              }
             }
           }
         }
       }
+      double v[NV2];
+      unsigned mn = 0u, mx = 0u;
+      v[2] = ssg.get();
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        v[i_ss(r)] = ss[r].get();
+        v[i_lo(r)] = (double)lo[r];
+        v[i_lo(r) + 1] = (double)hi[r];
+        mn |= 1u << i_lo(r);
+        mx |= 1u << (i_lo(r) + 1);
+      }
+      warp_reduce_to_shared<NV2>(sh, v, mn, mx);
+      __syncthreads();
+      const unsigned e = grp.epoch++;
+      if (warp == 0 && !group_finish<NV2>(sh, grp, e, mn, mx) && lane == 0) sh.abort = 1;
+      __syncthreads();
+      if (sh.abort) return false;
     }
-    double v[13] = {ss0.get(), ss1.get(), ssg.get(), (double)lo0, (double)hi0, (double)lo1, (double)hi1,
-                    ss2.get(), ss3.get(), (double)lo2, (double)hi2, (double)lo3, (double)hi3};
-    const unsigned mn = (1u << 3) | (1u << 5) | (1u << 9) | (1u << 11);
-    const unsigned mx = (1u << 4) | (1u << 6) | (1u << 10) | (1u << 12);
-    warp_reduce_to_shared<13>(sh, v, mn, mx);
-    __syncthreads();
-    const unsigned e = grp.epoch++;
-    if (warp == 0 && !group_finish<13>(sh, grp, e, mn, mx) && lane == 0) sh.abort = 1;
-    __syncthreads();
-    if (sh.abort) return false;
-  }
-  if (g == 0 && tid == 0 && a.stats != nullptr) {
-    double* st = a.stats + (size_t)(a.stats_fixed ? 0 : n) * kStat;
-    const int si[kMaxRegions] = {0, 1, 7, 8};   // centred sum of region r in sh.tot
-    const int li[kMaxRegions] = {3, 5, 9, 11};  // its minimum (maximum at li + 1)
-    for (int k = 0; k < kStat; ++k) st[k] = 0.0;
-    for (int r = 0; r < kMaxRegions; ++r) {
-      double* sr = st + stat_region(r);
-      sr[0] = cnt[r];
-      sr[1] = mean[r];
-      sr[2] = cnt[r] > 0 ? sh.tot[si[r]] / cnt[r] : 0.0;
-      sr[3] = sh.tot[li[r]];
-      sr[4] = sh.tot[li[r] + 1];
+    if (g == 0 && tid == 0 && a.stats != nullptr) {
+      double* st = a.stats + (size_t)(a.stats_fixed ? 0 : n) * kStat;
+      for (int k = 0; k < kStat; ++k) st[k] = 0.0;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        double* sr = st + stat_region(r);
+        sr[0] = cnt[r];
+        sr[1] = mean[r];
+        sr[2] = cnt[r] > 0 ? sh.tot[i_ss(r)] / cnt[r] : 0.0;
+        sr[3] = sh.tot[i_lo(r)];
+        sr[4] = sh.tot[i_lo(r) + 1];
+      }
+      st[kStatM] = gmean;
+      st[kStatV] = sh.tot[2] / (double)a.P;
+      st[kStatFlips] = flips_tot;
+      st[kStatInMean] = m_in;
+      if (!(fabs(gmean) < INFINITY) || !(st[kStatV] < INFINITY)) atomicOr(a.status, kStatusNumeric);
+      if (flips_tot > 0.0) atomicOr(a.status, kStatusRegionFlip);
     }
-    st[kStatM] = gmean;
-    st[kStatV] = sh.tot[2] / (double)a.P;
-    st[kStatFlips] = flips_tot;
-    st[kStatInMean] = m_in;
-    if (!(fabs(gmean) < INFINITY) || !(st[kStatV] < INFINITY)) atomicOr(a.status, kStatusNumeric);
-    if (flips_tot > 0.0) atomicOr(a.status, kStatusRegionFlip);
-  }
+    return true;
+  };
+  if (nreg <= 2 ? !epilogue(RegionsUpTo<2>{}) : !epilogue(RegionsUpTo<kMaxRegions>{})) return false;
   }
   return true;
 }
