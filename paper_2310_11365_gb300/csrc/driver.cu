@@ -43,17 +43,21 @@ __device__ void mixture(const DriverArgs& a, const Macro& r, double& M, double& 
   V = s - m * m;
 }
 
-__device__ void macro_store(const DriverArgs& a, double* r, const Macro& m) {
+// Stores the macro state and its global (M, V) in a moment row; returns (M, V).
+__device__ void macro_store(const DriverArgs& a, double* r, const Macro& m, double& M, double& V) {
   for (int i = 0; i < kMaxRegions; ++i) {
     double* ri = r + mom_region(i);
     ri[0] = m.frac[i]; ri[1] = m.mean[i]; ri[2] = m.var[i];
   }
-  double M, V;
   mixture(a, m, M, V);
   r[kMomM] = M;
   r[kMomV] = V;
   r[14] = 0.0;
   r[15] = 0.0;
+}
+__device__ void macro_store(const DriverArgs& a, double* r, const Macro& m) {
+  double M, V;
+  macro_store(a, r, m, M, V);
 }
 
 // Coarse propagator C_n: a moment ODE per region with the fractions frozen
@@ -310,6 +314,10 @@ __device__ bool lsq_fit(const DriverArgs& a, int npts, double p0, double& alpha,
 // so that it is reproducible bit for bit.
 // ---------------------------------------------------------------------------
 constexpr int kMaxRates = kMaxRegions * (kMaxRegions - 1);
+// sweep staging: slices per chunk, doubles per slice (per region count, mean,
+// variance, min, max; the coarse cache; the old global M, V)
+constexpr int kDrvChunk = 64;
+constexpr int kDrvRow = 7 * kMaxRegions + 2;
 
 // The fit's working arrays live in the problem's scratch block of device
 // memory (DriverArgs::fit, kFitScratch doubles), at fixed offsets, one
@@ -690,95 +698,122 @@ __device__ void driver_body(const DriverArgs& a) {
     const double p0 = frac0_at(a, 0);
     learn = lsq_fit(a, k, p0, alpha, beta);
   }
-  if (lane != 0) return;
-  if (a.variant == MMP_LEARNING && I >= 3 && k >= I) learn = rate_fit(a, I, k, om);
+  // The warp stages each chunk of kDrvChunk slices' inputs (restriction
+  // records, coarse cache, old global moments) in shared memory with all 32
+  // lanes; lane 0 then runs the sequential sweep over the chunk from there,
+  // so the chain of slices never waits on a global load.
+  __shared__ double s_stage[kDrvChunk * kDrvRow];
+  Macro cur;
   double Phi[16];
-  if (learn && I >= 3) rate_phi(a.fit, I, om, a.dT, Phi);
-  const double pk = frac0_at(a, k);
+  double pk = 0.0;
   double phat[kMaxRegions];  // extrapolated fractions (I >= 3), from those of t_k
-  for (int i = 0; i < I; ++i) phat[i] = frac_at(a, k, i);
-
   double change = 0.0;
   int acc = 0, rej = 0;
   bool numeric_bad = false;
-  Macro cur;
-  macro_load(a.rho, cur);  // rho^{k}_0 = R(u0), unchanged
-  for (int n = 0; n < N; ++n) {
-    Macro av;
-    coarse(a, cur, av);
-    const double* b = a.stats + (size_t)n * kStat;
-    double* cache = a.cache + (size_t)n * 2 * kMaxRegions;
-    double* af = a.aff + (size_t)(n + 1) * kMaxRegions * kAff;
-    Macro nx;
-    macro_zero(nx);
-    for (int i = 0; i < kMaxRegions; ++i) set_aff(af + i * kAff, kMatchIdentity, 0.0, 0.0, 0.0);
-    for (int i = 0; i < I; ++i) {
-      const double* bi = b + stat_region(i);
-      const double cnt = bi[0], bm = bi[1], bv = bi[2];
-      const double bmin = bi[3], bmax = bi[4];
-      if (!(fabs(bm) < INFINITY) || !(bv < INFINITY)) numeric_bad = true;
-      if (cnt <= 0.0) {
-        // empty region: carry the coarse prediction, move nothing
-        nx.mean[i] = av.mean[i];
-        nx.var[i] = av.var[i];
-        continue;
-      }
-      // alpha = R(b) + (a - c): a == c returns R(b) exactly (Property 3.3)
-      const double am = bm + (av.mean[i] - cache[2 * i]);
-      const double avv = bv + (av.var[i] - cache[2 * i + 1]);
-      bool accept = avv >= 0.0;
-      double delta = 0.0, sm1 = 0.0;
-      if (accept && bv > 0.0) {
-        delta = am - bm;
-        sm1 = sqrt(avv / bv) - 1.0;
-      }
-      if (accept && a.variant != MMP_UNIMODAL && I > 1) {
-        // Def. 3.2: move a region only if no particle leaves it
-        if (bv == 0.0) {
-          accept = false;
-        } else {
-          accept = stays_in_region(a, i, bmin, bmax, delta, sm1, bm);
-        }
-      }
-      if (accept) {
-        nx.mean[i] = am;
-        nx.var[i] = avv;
-        matching_record(af + i * kAff, cnt, bm, bv, am, avv);
-        ++acc;
-      } else {
-        nx.mean[i] = bm;
-        nx.var[i] = bv;
-        ++rej;
-      }
-    }
-    // fractions come from the fine propagator (Def. 3.2), or from the
-    // learned model beyond the exact slices (Def. 3.4)
-    for (int i = 0; i < I; ++i) nx.frac[i] = b[stat_region(i)] / (double)a.P;
-    if (learn && n + 1 > k) {
-      if (I == 2) {
-        const double p0hat = pk + (pk - beta) * expm1(alpha * (double)(n + 1 - k) * a.dT);
-        nx.frac[0] = p0hat;
-        nx.frac[1] = 1.0 - p0hat;
-      } else {
-        double q[kMaxRegions];
-        mat_vec(I, Phi, phat, q);
-        for (int i = 0; i < I; ++i) {
-          phat[i] = q[i];
-          nx.frac[i] = q[i];
-        }
-      }
-    }
-    if (I < 2) nx.frac[0] = 1.0;
-    for (int i = 0; i < kMaxRegions; ++i) {
-      cache[2 * i] = av.mean[i];
-      cache[2 * i + 1] = av.var[i];
-    }
-    double* rr = a.rho + (size_t)(n + 1) * kMom;
-    const double oldM = rr[kMomM], oldV = rr[kMomV];
-    macro_store(a, rr, nx);
-    change = fmax(change, fmax(fabs(rr[kMomM] - oldM), fabs(rr[kMomV] - oldV)));
-    cur = nx;
+  if (lane == 0) {
+    if (a.variant == MMP_LEARNING && I >= 3 && k >= I) learn = rate_fit(a, I, k, om);
+    if (learn && I >= 3) rate_phi(a.fit, I, om, a.dT, Phi);
+    pk = frac0_at(a, k);
+    for (int i = 0; i < I; ++i) phat[i] = frac_at(a, k, i);
+    macro_load(a.rho, cur);  // rho^{k}_0 = R(u0), unchanged
   }
+  for (int c0 = 0; c0 < N; c0 += kDrvChunk) {
+    const int cn = min(kDrvChunk, N - c0);
+    __syncwarp();
+    for (int idx = lane; idx < cn * kDrvRow; idx += 32) {
+      const int n = c0 + idx / kDrvRow;
+      const int f = idx % kDrvRow;
+      double v;
+      if (f < 5 * kMaxRegions) {
+        v = a.stats[(size_t)n * kStat + stat_region(f / 5) + f % 5];
+      } else if (f < 7 * kMaxRegions) {
+        v = a.cache[(size_t)n * 2 * kMaxRegions + (f - 5 * kMaxRegions)];
+      } else {
+        v = a.rho[(size_t)(n + 1) * kMom + (f == 7 * kMaxRegions ? kMomM : kMomV)];
+      }
+      s_stage[idx] = v;
+    }
+    __syncwarp();
+    if (lane != 0) continue;
+    for (int n = c0; n < c0 + cn; ++n) {
+      const double* row = s_stage + (size_t)(n - c0) * kDrvRow;
+      const double* cache_old = row + 5 * kMaxRegions;
+      Macro av;
+      coarse(a, cur, av);
+      double* cache = a.cache + (size_t)n * 2 * kMaxRegions;
+      double* af = a.aff + (size_t)(n + 1) * kMaxRegions * kAff;
+      Macro nx;
+      macro_zero(nx);
+      for (int i = 0; i < kMaxRegions; ++i) set_aff(af + i * kAff, kMatchIdentity, 0.0, 0.0, 0.0);
+      for (int i = 0; i < I; ++i) {
+        const double* bi = row + 5 * i;
+        const double cnt = bi[0], bm = bi[1], bv = bi[2];
+        const double bmin = bi[3], bmax = bi[4];
+        if (!(fabs(bm) < INFINITY) || !(bv < INFINITY)) numeric_bad = true;
+        if (cnt <= 0.0) {
+          // empty region: carry the coarse prediction, move nothing
+          nx.mean[i] = av.mean[i];
+          nx.var[i] = av.var[i];
+          continue;
+        }
+        // alpha = R(b) + (a - c): a == c returns R(b) exactly (Property 3.3)
+        const double am = bm + (av.mean[i] - cache_old[2 * i]);
+        const double avv = bv + (av.var[i] - cache_old[2 * i + 1]);
+        bool accept = avv >= 0.0;
+        double delta = 0.0, sm1 = 0.0;
+        if (accept && bv > 0.0) {
+          delta = am - bm;
+          sm1 = sqrt(avv / bv) - 1.0;
+        }
+        if (accept && a.variant != MMP_UNIMODAL && I > 1) {
+          // Def. 3.2: move a region only if no particle leaves it
+          if (bv == 0.0) {
+            accept = false;
+          } else {
+            accept = stays_in_region(a, i, bmin, bmax, delta, sm1, bm);
+          }
+        }
+        if (accept) {
+          nx.mean[i] = am;
+          nx.var[i] = avv;
+          matching_record(af + i * kAff, cnt, bm, bv, am, avv);
+          ++acc;
+        } else {
+          nx.mean[i] = bm;
+          nx.var[i] = bv;
+          ++rej;
+        }
+      }
+      // fractions come from the fine propagator (Def. 3.2), or from the
+      // learned model beyond the exact slices (Def. 3.4)
+      for (int i = 0; i < I; ++i) nx.frac[i] = row[5 * i] / (double)a.P;
+      if (learn && n + 1 > k) {
+        if (I == 2) {
+          const double p0hat = pk + (pk - beta) * expm1(alpha * (double)(n + 1 - k) * a.dT);
+          nx.frac[0] = p0hat;
+          nx.frac[1] = 1.0 - p0hat;
+        } else {
+          double q[kMaxRegions];
+          mat_vec(I, Phi, phat, q);
+          for (int i = 0; i < I; ++i) {
+            phat[i] = q[i];
+            nx.frac[i] = q[i];
+          }
+        }
+      }
+      if (I < 2) nx.frac[0] = 1.0;
+      for (int i = 0; i < kMaxRegions; ++i) {
+        cache[2 * i] = av.mean[i];
+        cache[2 * i + 1] = av.var[i];
+      }
+      const double oldM = row[7 * kMaxRegions], oldV = row[7 * kMaxRegions + 1];
+      double M, V;
+      macro_store(a, a.rho + (size_t)(n + 1) * kMom, nx, M, V);
+      change = fmax(change, fmax(fabs(M - oldM), fabs(V - oldV)));
+      cur = nx;
+    }
+  }
+  if (lane != 0) return;
   if (numeric_bad || !(change < INFINITY)) atomicOr(a.status, kStatusNumeric);
   const bool conv = change < a.tol;
   ctl[0] = change;
