@@ -315,9 +315,13 @@ __device__ bool lsq_fit(const DriverArgs& a, int npts, double p0, double& alpha,
 // ---------------------------------------------------------------------------
 constexpr int kMaxRates = kMaxRegions * (kMaxRegions - 1);
 // sweep staging: slices per chunk, doubles per slice (per region count, mean,
-// variance, min, max; the coarse cache; the old global M, V)
+// variance, min, max; the coarse cache; the old global M, V; the fractions)
 constexpr int kDrvChunk = 64;
-constexpr int kDrvRow = 7 * kMaxRegions + 2;
+constexpr int kDrvRow = 8 * kMaxRegions + 2;
+// the chain's record per slice: accepted flags, coarse prediction (mean,
+// variance), new macro state (fraction, mean, variance), per region
+constexpr int kOutAcc = 0, kOutAv = kMaxRegions, kOutNx = 3 * kMaxRegions;
+constexpr int kDrvOut = 6 * kMaxRegions;
 
 // The fit's working arrays live in the problem's scratch block of device
 // memory (DriverArgs::fit, kFitScratch doubles), at fixed offsets, one
@@ -698,14 +702,22 @@ __device__ void driver_body(const DriverArgs& a) {
     const double p0 = frac0_at(a, 0);
     learn = lsq_fit(a, k, p0, alpha, beta);
   }
-  // The warp stages each chunk of kDrvChunk slices' inputs (restriction
-  // records, coarse cache, old global moments) in shared memory with all 32
-  // lanes; lane 0 then runs the sequential sweep over the chunk from there,
-  // so the chain of slices never waits on a global load.
+  // The sweep over a chunk of kDrvChunk slices runs in three phases:
+  //   stage (all lanes): the slices' restriction records, coarse cache, old
+  //     global moments and fractions (count / P, or the learned two-region
+  //     fractions) into shared memory;
+  //   chain (lane 0): slice by slice, only what the next slice depends on:
+  //     the coarse step, alpha = R(b) + (a - c), acceptance and the new
+  //     macro state, recorded per slice;
+  //   finish (one lane per slice): matching records, coarse cache, moment
+  //     rows with the mixture, and the change, reduced by max over lanes.
+  // Each value is the same expression as in a single sequential pass, so
+  // the results are the same bit for bit; the FP64 instructions (slow on this
+  // chip) off the chain no longer wait for it.
   __shared__ double s_stage[kDrvChunk * kDrvRow];
+  __shared__ double s_out[kDrvChunk * kDrvOut];
   Macro cur;
   double Phi[16];
-  double pk = 0.0;
   double phat[kMaxRegions];  // extrapolated fractions (I >= 3), from those of t_k
   double change = 0.0;
   int acc = 0, rej = 0;
@@ -713,10 +725,11 @@ __device__ void driver_body(const DriverArgs& a) {
   if (lane == 0) {
     if (a.variant == MMP_LEARNING && I >= 3 && k >= I) learn = rate_fit(a, I, k, om);
     if (learn && I >= 3) rate_phi(a.fit, I, om, a.dT, Phi);
-    pk = frac0_at(a, k);
     for (int i = 0; i < I; ++i) phat[i] = frac_at(a, k, i);
     macro_load(a.rho, cur);  // rho^{k}_0 = R(u0), unchanged
   }
+  const bool learn2 = learn && I == 2;  // known to every lane (the two-region fit is warp-wide)
+  const double pk = frac0_at(a, k);
   for (int c0 = 0; c0 < N; c0 += kDrvChunk) {
     const int cn = min(kDrvChunk, N - c0);
     __syncwarp();
@@ -728,71 +741,70 @@ __device__ void driver_body(const DriverArgs& a) {
         v = a.stats[(size_t)n * kStat + stat_region(f / 5) + f % 5];
       } else if (f < 7 * kMaxRegions) {
         v = a.cache[(size_t)n * 2 * kMaxRegions + (f - 5 * kMaxRegions)];
-      } else {
+      } else if (f < 7 * kMaxRegions + 2) {
         v = a.rho[(size_t)(n + 1) * kMom + (f == 7 * kMaxRegions ? kMomM : kMomV)];
+      } else {
+        // fractions of slice end n + 1: from the fine propagator (Def. 3.2), or
+        // learned beyond the exact slices (Def. 3.4, two regions)
+        const int i = f - (7 * kMaxRegions + 2);
+        v = a.stats[(size_t)n * kStat + stat_region(i)] / (double)a.P;
+        if (learn2 && n + 1 > k && i < 2) {
+          const double p0hat = pk + (pk - beta) * expm1(alpha * (double)(n + 1 - k) * a.dT);
+          v = i == 0 ? p0hat : 1.0 - p0hat;
+        }
       }
       s_stage[idx] = v;
     }
     __syncwarp();
-    if (lane != 0) continue;
-    for (int n = c0; n < c0 + cn; ++n) {
-      const double* row = s_stage + (size_t)(n - c0) * kDrvRow;
-      const double* cache_old = row + 5 * kMaxRegions;
-      Macro av;
-      coarse(a, cur, av);
-      double* cache = a.cache + (size_t)n * 2 * kMaxRegions;
-      double* af = a.aff + (size_t)(n + 1) * kMaxRegions * kAff;
-      Macro nx;
-      macro_zero(nx);
-      for (int i = 0; i < kMaxRegions; ++i) set_aff(af + i * kAff, kMatchIdentity, 0.0, 0.0, 0.0);
-      for (int i = 0; i < I; ++i) {
-        const double* bi = row + 5 * i;
-        const double cnt = bi[0], bm = bi[1], bv = bi[2];
-        const double bmin = bi[3], bmax = bi[4];
-        if (!(fabs(bm) < INFINITY) || !(bv < INFINITY)) numeric_bad = true;
-        if (cnt <= 0.0) {
-          // empty region: carry the coarse prediction, move nothing
-          nx.mean[i] = av.mean[i];
-          nx.var[i] = av.var[i];
-          continue;
-        }
-        // alpha = R(b) + (a - c): a == c returns R(b) exactly (Property 3.3)
-        const double am = bm + (av.mean[i] - cache_old[2 * i]);
-        const double avv = bv + (av.var[i] - cache_old[2 * i + 1]);
-        bool accept = avv >= 0.0;
-        double delta = 0.0, sm1 = 0.0;
-        if (accept && bv > 0.0) {
-          delta = am - bm;
-          sm1 = sqrt(avv / bv) - 1.0;
-        }
-        if (accept && a.variant != MMP_UNIMODAL && I > 1) {
-          // Def. 3.2: move a region only if no particle leaves it
-          if (bv == 0.0) {
-            accept = false;
+    if (lane == 0) {
+      for (int n = c0; n < c0 + cn; ++n) {
+        const double* row = s_stage + (size_t)(n - c0) * kDrvRow;
+        const double* cache_old = row + 5 * kMaxRegions;
+        const double* frac = row + 7 * kMaxRegions + 2;
+        double* out = s_out + (size_t)(n - c0) * kDrvOut;
+        Macro av;
+        coarse(a, cur, av);
+        Macro nx;
+        macro_zero(nx);
+        for (int i = 0; i < I; ++i) {
+          const double* bi = row + 5 * i;
+          const double cnt = bi[0], bm = bi[1], bv = bi[2];
+          const double bmin = bi[3], bmax = bi[4];
+          out[kOutAcc + i] = 0.0;
+          if (!(fabs(bm) < INFINITY) || !(bv < INFINITY)) numeric_bad = true;
+          if (cnt <= 0.0) {
+            // empty region: carry the coarse prediction, move nothing
+            nx.mean[i] = av.mean[i];
+            nx.var[i] = av.var[i];
+            continue;
+          }
+          // alpha = R(b) + (a - c): a == c returns R(b) exactly (Property 3.3)
+          const double am = bm + (av.mean[i] - cache_old[2 * i]);
+          const double avv = bv + (av.var[i] - cache_old[2 * i + 1]);
+          bool accept = avv >= 0.0;
+          if (accept && a.variant != MMP_UNIMODAL && I > 1) {
+            // Def. 3.2: move a region only if no particle leaves it
+            if (bv == 0.0) {
+              accept = false;
+            } else {
+              const double delta = am - bm;
+              const double sm1 = sqrt(avv / bv) - 1.0;
+              accept = stays_in_region(a, i, bmin, bmax, delta, sm1, bm);
+            }
+          }
+          if (accept) {
+            nx.mean[i] = am;
+            nx.var[i] = avv;
+            out[kOutAcc + i] = 1.0;
+            ++acc;
           } else {
-            accept = stays_in_region(a, i, bmin, bmax, delta, sm1, bm);
+            nx.mean[i] = bm;
+            nx.var[i] = bv;
+            ++rej;
           }
         }
-        if (accept) {
-          nx.mean[i] = am;
-          nx.var[i] = avv;
-          matching_record(af + i * kAff, cnt, bm, bv, am, avv);
-          ++acc;
-        } else {
-          nx.mean[i] = bm;
-          nx.var[i] = bv;
-          ++rej;
-        }
-      }
-      // fractions come from the fine propagator (Def. 3.2), or from the
-      // learned model beyond the exact slices (Def. 3.4)
-      for (int i = 0; i < I; ++i) nx.frac[i] = row[5 * i] / (double)a.P;
-      if (learn && n + 1 > k) {
-        if (I == 2) {
-          const double p0hat = pk + (pk - beta) * expm1(alpha * (double)(n + 1 - k) * a.dT);
-          nx.frac[0] = p0hat;
-          nx.frac[1] = 1.0 - p0hat;
-        } else {
+        for (int i = 0; i < I; ++i) nx.frac[i] = frac[i];
+        if (learn && I >= 3 && n + 1 > k) {
           double q[kMaxRegions];
           mat_vec(I, Phi, phat, q);
           for (int i = 0; i < I; ++i) {
@@ -800,19 +812,49 @@ __device__ void driver_body(const DriverArgs& a) {
             nx.frac[i] = q[i];
           }
         }
+        if (I < 2) nx.frac[0] = 1.0;
+        for (int i = 0; i < kMaxRegions; ++i) {
+          out[kOutAv + 2 * i] = av.mean[i];
+          out[kOutAv + 2 * i + 1] = av.var[i];
+          out[kOutNx + 3 * i] = nx.frac[i];
+          out[kOutNx + 3 * i + 1] = nx.mean[i];
+          out[kOutNx + 3 * i + 2] = nx.var[i];
+        }
+        cur = nx;
       }
-      if (I < 2) nx.frac[0] = 1.0;
+    }
+    __syncwarp();
+    for (int j = lane; j < cn; j += 32) {
+      const int n = c0 + j;
+      const double* row = s_stage + (size_t)j * kDrvRow;
+      const double* out = s_out + (size_t)j * kDrvOut;
+      double* af = a.aff + (size_t)(n + 1) * kMaxRegions * kAff;
       for (int i = 0; i < kMaxRegions; ++i) {
-        cache[2 * i] = av.mean[i];
-        cache[2 * i + 1] = av.var[i];
+        if (i < I && out[kOutAcc + i] != 0.0) {
+          const double* bi = row + 5 * i;
+          matching_record(af + i * kAff, bi[0], bi[1], bi[2], out[kOutNx + 3 * i + 1], out[kOutNx + 3 * i + 2]);
+        } else {
+          set_aff(af + i * kAff, kMatchIdentity, 0.0, 0.0, 0.0);
+        }
+      }
+      double* cache = a.cache + (size_t)n * 2 * kMaxRegions;
+      Macro nx;
+      for (int i = 0; i < kMaxRegions; ++i) {
+        cache[2 * i] = out[kOutAv + 2 * i];
+        cache[2 * i + 1] = out[kOutAv + 2 * i + 1];
+        nx.frac[i] = out[kOutNx + 3 * i];
+        nx.mean[i] = out[kOutNx + 3 * i + 1];
+        nx.var[i] = out[kOutNx + 3 * i + 2];
       }
       const double oldM = row[7 * kMaxRegions], oldV = row[7 * kMaxRegions + 1];
       double M, V;
       macro_store(a, a.rho + (size_t)(n + 1) * kMom, nx, M, V);
       change = fmax(change, fmax(fabs(M - oldM), fabs(V - oldV)));
-      cur = nx;
     }
   }
+  // the change is a maximum over slices: any order gives the same value
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) change = fmax(change, __shfl_xor_sync(0xffffffffu, change, off));
   if (lane != 0) return;
   if (numeric_bad || !(change < INFINITY)) atomicOr(a.status, kStatusNumeric);
   const bool conv = change < a.tol;
