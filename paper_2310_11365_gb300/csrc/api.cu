@@ -1057,24 +1057,34 @@ int mmp_iterate(mmp_ctx* ctx, int n_iter, int* all_converged) {
       any = true;
     }
     if (!any) break;
+    // one host round trip per sweep: the driver leaves the status word in
+    // ctl[15], and a copy to pageable host memory returns only once it (and
+    // so all the stream's earlier work) has completed
+    std::vector<double> ctls;
+    ctls.reserve(16 * ctx->probs.size());
+    for (Prob& p : ctx->probs) {
+      if (p.done) continue;
+      ctls.resize(ctls.size() + 16);
+      MMP_CUDA(cudaMemcpyAsync(ctls.data() + ctls.size() - 16, p.ctl, sizeof(double) * 16, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+    }
     MMP_CUDA(cudaStreamSynchronize(ctx->stream));
     {
       const int trc = collect_timing(ctx);
       if (trc) return trc;
     }
+    size_t slot = 0;
     for (Prob& p : ctx->probs) {
       if (p.done) continue;
-      double ctl[16];
-      unsigned st[4];
-      MMP_CUDA(cudaMemcpy(ctl, p.ctl, sizeof(ctl), cudaMemcpyDeviceToHost));
-      MMP_CUDA(cudaMemcpy(st, p.status, sizeof(st), cudaMemcpyDeviceToHost));
+      const double* ctl = ctls.data() + 16 * slot++;
+      const unsigned st0 = (unsigned)ctl[15];
       const int k = p.sweeps + 1;
       for (int n = k - 1; n < p.d.N; ++n) p.out_buf[n] = k & 1;
       p.sweeps = k;
       p.last_change = ctl[0];
       p.converged = ctl[1] != 0.0 || k == p.d.N;
       p.done = ctl[3] != 0.0;
-      const int err = status_to_error(st[0]);
+      const int err = status_to_error(st0);
       if (err) return err;
     }
   }

@@ -690,6 +690,7 @@ __device__ void driver_body(const DriverArgs& a) {
     ctl[6] = 0.0;  // fit alpha (two regions)
     ctl[7] = 0.0;  // fit beta (two regions)
     ctl[8] = 0.0;  // fit used
+    ctl[15] = 0.0;  // copy of the status word after a sweep
     return;
   }
 
@@ -857,6 +858,7 @@ __device__ void driver_body(const DriverArgs& a) {
   for (int off = 16; off > 0; off >>= 1) change = fmax(change, __shfl_xor_sync(0xffffffffu, change, off));
   if (lane != 0) return;
   if (numeric_bad || !(change < INFINITY)) atomicOr(a.status, kStatusNumeric);
+  ctl[15] = (double)*(volatile unsigned*)a.status;  // the status word, for one read of ctl by the host
   const bool conv = change < a.tol;
   ctl[0] = change;
   ctl[1] = conv ? 1.0 : 0.0;
