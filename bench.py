@@ -359,6 +359,25 @@ def config4_run() -> dict:
            "backward_particle_steps_per_s": J * p.P / (b_ms / 1e3),
            "loss": float(np.sum(gm ** 2 + gv ** 2) / 4.0),
            "grad_c3_c1_kappa_c0_B0_B_BE": [float(x) for x in grad]}
+    # the same gradient with a checkpoint every 8 steps: the segment's states
+    # and draws (2 x 9 rows of P floats) then stay in L2 during the reverse
+    del adj
+    torch.cuda.empty_cache()
+    adj8 = mmp.Adjoint(s, 0, 8)
+    adj8.forward(theta(*W.ADJOINT_EVAL_PARAMS))
+    adj8.backward(gm, gv)
+    ev8 = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev8[0].record()
+    adj8.forward(theta(*W.ADJOINT_EVAL_PARAMS))
+    ev8[1].record()
+    ev8[2].record()
+    grad8 = adj8.backward(gm, gv)
+    ev8[3].record()
+    torch.cuda.synchronize()
+    out["checkpoint_every_8"] = {"forward_ms": ev8[0].elapsed_time(ev8[1]), "backward_ms": ev8[2].elapsed_time(ev8[3]),
+                                 "workspace_gb": adj8.nbytes / 1e9,
+                                 "same_gradient": bool(np.array_equal(grad8, grad))}
+    del adj8
     s.close()
     return out
 
