@@ -235,6 +235,15 @@ int mmp_adjoint_forward(mmp_ctx* ctx, int prob, int ckpt_every, void* ws, size_t
 int mmp_adjoint_backward(mmp_ctx* ctx, int prob, const double* gm, const double* gv, void* ws,
                          size_t ws_bytes, double* grad_out);
 
+/* The loss L = sum_{n=1..N} (M_n - m_tgt[n-1])^2 + (V_n - v_tgt[n-1])^2 of
+ * the serial fine run's slice-end moments and its gradient in one call:
+ * mmp_adjoint_forward, the cotangents 2 (M_n - m_tgt), 2 (V_n - v_tgt) on the
+ * host, then mmp_adjoint_backward.  m_tgt, v_tgt: host, N doubles each;
+ * grad_out: host, MMP_N_THETA doubles; loss: host, may be NULL.  The same
+ * workspace rules and errors as the two calls.  Synchronising. */
+int mmp_adjoint(mmp_ctx* ctx, int prob, const double* m_tgt, const double* v_tgt, int ckpt_every, void* ws,
+                size_t ws_bytes, double* grad_out, double* loss);
+
 /* Device-time accounting.  With timing on, the library records CUDA
  * events on the context stream around every fine-kernel launch and reads
  * them at its synchronisation points.  mmp_timing reports, since the last

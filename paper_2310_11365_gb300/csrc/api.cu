@@ -1324,6 +1324,26 @@ int mmp_adjoint_backward(mmp_ctx* ctx, int prob, const double* gm, const double*
   return status_to_error(stw[0]);
 }
 
+int mmp_adjoint(mmp_ctx* ctx, int prob, const double* m_tgt, const double* v_tgt, int ckpt_every, void* ws,
+                size_t ws_bytes, double* grad_out, double* loss) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  if (m_tgt == nullptr || v_tgt == nullptr || grad_out == nullptr) return MMP_ERR_INVALID_ARG;
+  const int N = ctx->probs[prob].d.N;
+  std::vector<double> mom(2 * (size_t)(N + 1)), gm(N), gv(N);
+  rc = mmp_adjoint_forward(ctx, prob, ckpt_every, ws, ws_bytes, mom.data());
+  if (rc) return rc;
+  double L = 0.0;
+  for (int n = 1; n <= N; ++n) {
+    const double dm = mom[2 * n] - m_tgt[n - 1], dv = mom[2 * n + 1] - v_tgt[n - 1];
+    L += dm * dm + dv * dv;
+    gm[n - 1] = 2.0 * dm;
+    gv[n - 1] = 2.0 * dv;
+  }
+  if (loss) *loss = L;
+  return mmp_adjoint_backward(ctx, prob, gm.data(), gv.data(), ws, ws_bytes, grad_out);
+}
+
 int mmp_set_timing(mmp_ctx* ctx, int on) {
   if (ctx == nullptr) return MMP_ERR_INVALID_ARG;
   ctx->timing = on != 0;

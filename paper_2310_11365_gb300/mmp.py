@@ -47,7 +47,7 @@ EXPORTED = [
     "mmp_destroy", "mmp_set_initial", "mmp_lift", "mmp_iterate", "mmp_run", "mmp_status",
     "mmp_get_moments", "mmp_get_particles", "mmp_fine_serial", "mmp_fine", "mmp_philox",
     "mmp_normals", "mmp_get_plan", "mmp_set_timing", "mmp_timing", "mmp_fine_static",
-    "mmp_set_params", "mmp_adjoint_workspace_size", "mmp_adjoint_forward", "mmp_adjoint_backward",
+    "mmp_set_params", "mmp_adjoint_workspace_size", "mmp_adjoint_forward", "mmp_adjoint_backward", "mmp_adjoint",
     "mmp_batch_info", "mmp_autotune_workspace_size", "mmp_autotune", "mmp_set_tuning", "mmp_set_batch_nq",
     "mmp_state_size", "mmp_get_state", "mmp_set_state",
 ]
@@ -116,6 +116,7 @@ def load():
         "mmp_adjoint_workspace_size": ([vp, i, i, C.POINTER(C.c_size_t)], i),
         "mmp_adjoint_forward": ([vp, i, i, vp, C.c_size_t, d], i),
         "mmp_adjoint_backward": ([vp, i, d, d, vp, C.c_size_t, d], i),
+        "mmp_adjoint": ([vp, i, d, d, i, vp, C.c_size_t, d, d], i),
         "mmp_batch_info": ([vp, C.POINTER(i), C.POINTER(i)], i),
         "mmp_autotune_workspace_size": ([pd, C.POINTER(C.c_size_t)], i),
         "mmp_autotune": ([pd, C.POINTER(i), i, i, vp, C.c_size_t, vp, C.POINTER(i), d], i),
@@ -349,6 +350,19 @@ def mmp_adjoint_backward(ctx, prob: int, gm, gv, ws_ptr: int, ws_bytes: int) -> 
     return grad
 
 
+def mmp_adjoint(ctx, prob: int, m_tgt, v_tgt, ckpt_every: int, ws_ptr: int, ws_bytes: int):
+    """Loss sum (M_n - m*)^2 + (V_n - v*)^2 of the serial fine run and its
+    gradient in (c3, c1, kappa, c0, B0, B, BE), in one call."""
+    mt = np.ascontiguousarray(m_tgt, dtype=np.float64)
+    vt = np.ascontiguousarray(v_tgt, dtype=np.float64)
+    grad = np.empty(N_THETA, np.float64)
+    loss = C.c_double()
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    _check(load().mmp_adjoint(ctx, prob, dp(mt), dp(vt), ckpt_every, C.c_void_p(ws_ptr), ws_bytes, dp(grad),
+                              C.byref(loss)), "mmp_adjoint")
+    return loss.value, grad
+
+
 def mmp_philox(ctr_ptr: int, key, out_ptr: int, n: int, stream=None) -> None:
     k = (C.c_uint * 2)(int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF)
     _check(load().mmp_philox(C.c_void_p(ctr_ptr), k, C.c_void_p(out_ptr), n,
@@ -479,6 +493,12 @@ class Adjoint:
 
     def backward(self, gm, gv) -> np.ndarray:
         return mmp_adjoint_backward(self.solver.ctx, self.prob, gm, gv, self.ws.data_ptr(), self.nbytes)
+
+    def loss_and_grad(self, theta, m_tgt, v_tgt):
+        """Loss against moment targets and its gradient at theta, one call."""
+        mmp_set_params(self.solver.ctx, self.prob, theta)
+        return mmp_adjoint(self.solver.ctx, self.prob, m_tgt, v_tgt, self.ckpt_every, self.ws.data_ptr(),
+                           self.nbytes)
 
 
 def _autograd_function():

@@ -75,6 +75,23 @@ def test_adjoint_fp64_config4_loss_gradient(mmplib, orc):
     assert np.max(np.abs(g - g_ref) / np.maximum(np.abs(g_ref), 1e-12)) < 1e-9
 
 
+def test_one_call_adjoint_loss(mmplib, orc):
+    """mmp_adjoint (forward, loss, backward in one call) against the oracle's
+    loss and gradient, FP64, general diffusion."""
+    from paper_2310_11365_gb300.mmp import Adjoint, Solver
+
+    p = _general(W.double_well(0.25, 0.5, 0.1, 0.7, m0=0.2, s0=0.5, T=1.0, N=4, dt=0.01, P=3001, seed=17,
+                               precision="fp64"))
+    m_tgt, v_tgt = np.full(p.N, 0.1), np.full(p.N, 0.3)
+    L_ref, g_ref = orc.adjoint_loss(p, m_tgt, v_tgt)
+    s = Solver(p)
+    adj = Adjoint(s, 0, 16)
+    L, g = adj.loss_and_grad(_theta(p), m_tgt, v_tgt)
+    s.close()
+    assert abs(L - L_ref) <= 1e-10 * L_ref
+    assert np.max(np.abs(g - g_ref) / np.maximum(np.abs(g_ref), 1e-12)) < 1e-10, (g, g_ref)
+
+
 @pytest.mark.parametrize("general", [False, True])
 def test_adjoint_mixed_close_to_oracle(mmplib, orc, general):
     """FP32 particles, FP64 accumulation: gradient within 1e-3 relative of the
