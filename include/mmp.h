@@ -48,7 +48,11 @@ extern "C" {
 #define MMP_MIXED 1
 
 /* Parareal variant: Def. 3.1 (one region), Def. 3.2 (per region, with the
- * fractions-unchanged test), Def. 3.4 (Def. 3.2 plus learned fractions). */
+ * fractions-unchanged test), Def. 3.4 (Def. 3.2 plus learned fractions:
+ * with two regions the fraction of region 0 follows App. H's
+ * P(t) = beta + (P(0) - beta) e^{alpha t}; with three or four, all fractions
+ * follow dP/dt = A P of Sec. 3.6, the rates fitted by Levenberg-Marquardt on
+ * the exact slice ends t_0..t_k, from sweep k = n_regions on). */
 #define MMP_UNIMODAL 0
 #define MMP_MULTIMODAL 1
 #define MMP_LEARNING 2

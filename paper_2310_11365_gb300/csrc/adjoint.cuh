@@ -26,7 +26,7 @@ struct AdjointArgs {
                                      // additive noise, (m_j, kappa m_j + c0, (BE m_j + B0) sqrt h) otherwise
   void* segx;                        // (c + 1) rows: states of the segment being reversed
   void* segz;                        // c rows: its normal draws
-  const double* mom;                 // [(N+1)][16] restriction records of the serial run
+  const double* mom;                 // [(N+1)][kStat] restriction records of the serial run
   const double* gm;                  // [N] cotangents of the slice-end means (n = 1..N)
   const double* gv;                  // [N] cotangents of the slice-end variances
   double* grad;                      // [kNGrad] out: d/d(c3, c1, kappa, c0, B0, B, BE)
