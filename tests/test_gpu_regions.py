@@ -149,3 +149,40 @@ def test_batch_of_three_and_four_regions(mmplib, orc):
         assert s.status(b)["sweeps"] == ref["sweeps"] and s.status(b)["dev_err"] == 0
         _compare(p, s.moments(b), ref, 1e-10)
     s.close()
+
+
+def test_redraw_branch_with_three_regions(mmplib, orc):
+    """Every initial particle at x = 0 (s0 = 0): the middle region has
+    variance 0, so lifting redraws it from the tag-2 stream of region 1
+    (Eq. multimodal_M's first branch); FP64 against the oracle to 1e-10."""
+    from paper_2310_11365_gb300.mmp import Solver
+
+    p = _well(W.MULTIMODAL, THR3, s0=0.0, max_iter=3)
+    s = Solver(p)
+    s.run()
+    ref = orc.parareal(p)
+    assert s.status()["sweeps"] == ref["sweeps"] and s.status()["dev_err"] == 0
+    _compare(p, s.moments(), ref, 1e-10)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_regions_with_state_dependent_noise(mmplib, orc, prec):
+    """Four regions with b = B x + BE E[X] + B0 (the general-form fine
+    kernel): FP64 to 1e-10, mixed within its bounds."""
+    from paper_2310_11365_gb300.mmp import Solver
+
+    p = _well(W.LEARNING, THR4, precision=prec, max_iter=5, P=8001).scaled(B=0.15, BE=-0.1)
+    s = Solver(p)
+    s.run()
+    mom = s.moments()
+    ref = orc.parareal(p.scaled(precision="fp64"))
+    assert s.status()["sweeps"] == ref["sweeps"] and s.status()["dev_err"] == 0
+    if prec == "fp64":
+        _compare(p, mom, ref, 1e-10)
+    else:
+        for n in range(p.N + 1):
+            M, V = ref["hist"][-1][n]
+            assert abs(mom[n, 6] - M) <= 2e-6 * max(abs(M), np.sqrt(V)), n
+            assert abs(mom[n, 7] - V) <= 1e-5 * V, n
+    s.close()
