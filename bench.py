@@ -319,19 +319,20 @@ def config3_run() -> dict:
     return out
 
 
-def config4_run() -> dict:
+def config4_run(n_slices: int | None = None) -> dict:
     """Config 4 at full size (the adjoint): the double-well model, P = 1e6,
     N = 64, T = 20, n_f = 313 (20032 steps), checkpoints every 64 steps; the
     recording forward and the reverse sweep timed separately (device time),
     loss L = sum_n (M_n - m*_n)^2 + (V_n - v*_n)^2 with targets from a run at
-    the target parameters on the same draws."""
+    the target parameters on the same draws.  n_slices: the same model with
+    fewer slices of the same length (a shorter horizon; profiling runs)."""
     import numpy as np
     import torch
 
     from paper_2310_11365_gb300 import mmp
     from paper_2310_11365_gb300 import workloads as W
 
-    p = W.config4()
+    p = W.config4() if n_slices is None else W.config4(N=n_slices, T=20.0 * n_slices / 64)
     s = mmp.Solver(p)
     adj = mmp.Adjoint(s, 0, W.ADJOINT_CKPT)
 
@@ -352,8 +353,8 @@ def config4_run() -> dict:
     f_ms, b_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
     J = p.N * math.ceil(p.T / p.N / p.dt - 1e-9)
     out = {"workload": "config4: adjoint of the serial fine run, double well (kappa, sigma, a, b) = "
-                       "(0.1, 0.7, 0.25, 0.5), targets at (0.15, 0.65, 0.25, 0.5), P=1e6, N=64, T=20, "
-                       "dt=1e-3 (n_f=313), checkpoint every 64 steps",
+                       "(0.1, 0.7, 0.25, 0.5), targets at (0.15, 0.65, 0.25, 0.5), P=1e6, "
+                       f"N={p.N}, T={p.T:g}, dt=1e-3 (n_f=313), checkpoint every 64 steps",
            "steps": J, "P": p.P, "forward_ms": f_ms, "backward_ms": b_ms,
            "forward_particle_steps_per_s": J * p.P / (f_ms / 1e3),
            "backward_particle_steps_per_s": J * p.P / (b_ms / 1e3),
@@ -435,6 +436,8 @@ def main():
     ap.add_argument("--no-cfg4", action="store_true", help="skip the config-4 adjoint timing")
     ap.add_argument("--no-tune", action="store_true",
                     help="plan config 2 with the cost model instead of measured shapes (profiling runs)")
+    ap.add_argument("--adjoint-only", type=int, default=None, metavar="N",
+                    help="only the config-4 adjoint leg, with N slices of the config's length (profiling runs)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -444,6 +447,9 @@ def main():
     import torch
 
     torch.cuda.set_device(local)
+    if args.adjoint_only is not None:
+        print(json.dumps({"config4_adjoint": config4_run(args.adjoint_only)}))
+        return 0
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
