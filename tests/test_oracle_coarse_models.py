@@ -23,11 +23,17 @@ def _rhs(orc, p, model, frac, mean, var):
     return orc.coarse_rhs(p.scaled(coarse_model=model), frac, mean, var)
 
 
-@pytest.mark.parametrize("regions", [1, 2])
+BOUNDS = dict(threshold=-0.5, threshold2=0.0, threshold3=0.5)
+FRAC = {1: [1.0], 2: [0.4, 0.6], 3: [0.3, 0.3, 0.4], 4: [0.2, 0.3, 0.1, 0.4]}
+MEAN = [-0.7, 0.9, 1.3, -1.1]
+VAR = [0.3, 0.5, 0.2, 0.45]
+
+
+@pytest.mark.parametrize("regions", [1, 2, 3, 4])
 def test_linear_drift_all_models_agree(orc, regions):
-    p = W.Problem(c1=-1.3, kappa=0.4, c0=0.2, B=0.3, BE=0.1, B0=0.5, n_regions=regions, threshold=0.0,
-                  variant=W.MULTIMODAL if regions == 2 else W.UNIMODAL)
-    frac, mean, var = [0.4, 0.6], [-0.7, 0.9], [0.3, 0.5]
+    p = W.Problem(c1=-1.3, kappa=0.4, c0=0.2, B=0.3, BE=0.1, B0=0.5, n_regions=regions,
+                  variant=W.MULTIMODAL if regions > 1 else W.UNIMODAL, **BOUNDS)
+    frac, mean, var = FRAC[regions], MEAN[:regions], VAR[:regions]
     ref = _rhs(orc, p, W.CLOSURE, frac, mean, var)
     for model in MODELS[1:]:
         got = _rhs(orc, p, model, frac, mean, var)
@@ -36,12 +42,12 @@ def test_linear_drift_all_models_agree(orc, regions):
             assert got[1][i] == pytest.approx(ref[1][i], rel=1e-14, abs=1e-15)
 
 
-@pytest.mark.parametrize("regions", [1, 2])
+@pytest.mark.parametrize("regions", [1, 2, 3, 4])
 def test_cubic_drift_closed_form_differences(orc, regions):
     c3 = 0.8
     p = W.Problem(c3=c3, c1=0.6, kappa=0.3, c0=-0.1, B=0.25, BE=-0.2, B0=0.4, n_regions=regions,
-                  threshold=0.0, variant=W.MULTIMODAL if regions == 2 else W.UNIMODAL)
-    frac, mean, var = [0.35, 0.65], [-0.9, 1.1], [0.2, 0.45]
+                  variant=W.MULTIMODAL if regions > 1 else W.UNIMODAL, **BOUNDS)
+    frac, mean, var = FRAC[regions], MEAN[:regions], VAR[:regions]
     cl = _rhs(orc, p, W.CLOSURE, frac, mean, var)
     s3 = _rhs(orc, p, W.SIGMA3, frac, mean, var)
     s2 = _rhs(orc, p, W.SIGMA2, frac, mean, var)

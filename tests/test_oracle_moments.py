@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from paper_2310_11365_gb300 import workloads as W
 
@@ -85,14 +86,17 @@ def test_gaussian_closure_against_quadrature(orc):
         assert abs(dv[0] - dv_q) < 1e-12 * (1 + abs(dv_q))
 
 
-def test_multimodal_region_rhs_uses_global_mean(orc):
+@pytest.mark.parametrize("regions", [2, 3, 4])
+def test_multimodal_region_rhs_uses_global_mean(orc, regions):
     """Per-region model, Eq. (moment_model_Taylor_multimodal): each region's
-    drift feels the mixture mean M = sum P_i m_i through kappa."""
-    p = W.double_well(0.25, 0.5, 0.3, 0.7, n_regions=2)
-    frac, mean, var = [0.3, 0.7], [-0.9, 1.1], [0.05, 0.08]
-    M = 0.3 * -0.9 + 0.7 * 1.1
+    drift feels the mixture mean M = sum P_i m_i through kappa (two to four
+    regions; Gauss-Hermite quadrature of each region's N(m_i, v_i))."""
+    p = W.double_well(0.25, 0.5, 0.3, 0.7, n_regions=regions, threshold=-0.5, threshold2=0.0, threshold3=0.5)
+    frac = {2: [0.3, 0.7], 3: [0.3, 0.3, 0.4], 4: [0.1, 0.2, 0.3, 0.4]}[regions]
+    mean, var = [-0.9, 1.1, 0.2, -0.4][:regions], [0.05, 0.08, 0.12, 0.03][:regions]
+    M = sum(f * m for f, m in zip(frac, mean))
     dm, dv = orc.coarse_rhs(p, frac, mean, var)
-    for i in range(2):
+    for i in range(regions):
         a = lambda x: -p.c3 * x**3 + p.c1 * x + p.kappa * M
         assert abs(dm[i] - _gh_expect(a, mean[i], var[i])) < 1e-12
         dvq = 2 * _gh_expect(lambda x: (x - mean[i]) * a(x), mean[i], var[i]) + p.B0**2
