@@ -1,9 +1,8 @@
-"""The multi-rank path of bench.py on CPU: two gloo ranks on 127.0.0.1
-(the box has one GPU, and the solve does not shard: ranks are independent
-replicas with a barrier and max-over-ranks timing).  Checks the rank
-environment, the barrier, the reductions, the whole-job throughput (units
-of all ranks over the slowest rank's time), and that the reference arm
-does its work on rank 0 only."""
+"""The multi-rank path of bench.py on CPU: two gloo ranks on 127.0.0.1.
+The solve does not shard, so ranks are independent replicas with a barrier
+and max-over-ranks timing.  Checks the rank environment, the barrier, the
+reductions, the whole-job throughput (units of all ranks over the slowest
+rank's time), and that the reference arm does its work on rank 0 only."""
 import os
 import socket
 import sys
