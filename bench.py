@@ -534,6 +534,13 @@ def main():
                "unit": UNIT, "h2d_bytes_per_step": int(p.P * 4),
                "d2h_bytes_per_step": int(out.nbytes)}
 
+    # the converged iterate against the solver's own serial fine run (the run
+    # the iteration reaches exactly at k = N, Property 3.3): the moment
+    # accuracy at which the mixed and FP64 times to tolerance compare
+    ser = solver.serial()
+    accuracy = {"tol": p.tol, "mixed": {"max_abs_dM": float(np.max(np.abs(mom[:, 6] - ser[:, 10]))),
+                                        "max_abs_dV": float(np.max(np.abs(mom[:, 7] - ser[:, 11])))}}
+
     # plain FP64 GPU form: time to the same tolerance (one solve)
     fp64 = None
     if not args.no_fp64:
@@ -550,6 +557,9 @@ def main():
         fp64 = {"time_to_tol_s": t64, "sweeps": k64, "particle_steps_per_s": tm64["fine_particle_steps"] / t64,
                 "max_abs_diff_M_vs_mixed": float(np.max(np.abs(m64[:, 6] - mom[:, 6]))),
                 "max_abs_diff_V_vs_mixed": float(np.max(np.abs(m64[:, 7] - mom[:, 7])))}
+        ser64 = s64.serial()
+        accuracy["fp64"] = {"max_abs_dM": float(np.max(np.abs(m64[:, 6] - ser64[:, 10]))),
+                            "max_abs_dV": float(np.max(np.abs(m64[:, 7] - ser64[:, 11])))}
         s64.close()
 
     batch = None
@@ -588,6 +598,7 @@ def main():
                          "peak_note": "152 SMs x 128 FP32/INT32 lanes x max SM clock (MEASURED_PEAKS sm_max_mhz)"},
             "e2e": e2e,
             "fp64_plain": fp64,
+            "accuracy_vs_own_serial": accuracy,
             "batched_config5": batch,
             "coarse_models_config2": coarse,
             "config3": cfg3,
