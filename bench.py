@@ -43,22 +43,53 @@ PROFILE = os.path.join(ROOT, "profiles", "k_fine_config2_N8_mixed.md")
 PROFILE_SOURCES = ("fine_kernel.cuh", "mmp_internal.cuh", "fine_f32.cu")
 
 
-def _profile_bytes_per_slice():
+def _strip_comments(text: str) -> str:
+    """C/C++ source without comments, trailing blanks and empty lines (string
+    and character literals kept), so that editing a comment does not change
+    the code digest."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = (line.rstrip() for line in "".join(out).splitlines())
+    return "\n".join(line for line in lines if line)
+
+
+def code_digest(names) -> str:
+    """First 16 hex digits of the sha256 of the named csrc files' code."""
     import hashlib
 
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2310_11365_gb300", "csrc", name)) as f:
+            h.update(_strip_comments(f.read()).encode())
+    return h.hexdigest()[:16]
+
+
+def _profile_bytes_per_slice():
     try:
         fields = {}
         with open(PROFILE) as f:
             for line in f:
                 line = line.strip().lstrip("- ")
-                for key in ("source-sha256-16:", "dram-bytes-per-slice:"):
+                for key in ("code-sha256-16:", "dram-bytes-per-slice:"):
                     if line.startswith(key):
                         fields[key] = line[len(key):].split()[0]
-        h = hashlib.sha256()
-        for name in PROFILE_SOURCES:
-            with open(os.path.join(ROOT, "paper_2310_11365_gb300", "csrc", name), "rb") as f:
-                h.update(f.read())
-        if h.hexdigest()[:16] != fields.get("source-sha256-16:"):
+        if code_digest(PROFILE_SOURCES) != fields.get("code-sha256-16:"):
             return None
         return float(fields["dram-bytes-per-slice:"])
     except Exception:

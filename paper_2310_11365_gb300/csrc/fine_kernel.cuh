@@ -5,15 +5,19 @@
 // One slice of the Parareal sweep is one "task".  A task's P particles are
 // split over a group of G co-resident CTAs (the launch is cooperative, so
 // all CTAs are resident and a group barrier cannot deadlock).  Each thread
-// holds up to NQ quads of 4 particles in registers for all n_f steps:
+// keeps its quads of 4 particles on chip for all n_f steps: in shared memory
+// (NQ = 0, the layout the planner uses, a.nq quads per thread) or in
+// registers (NQ quads):
 //
 //   prologue  load u (coalesced 16-byte vectors), apply the matching T of
-//             its region (Eq. multimodal_M), reduce the mean m_0
+//             its region (Eq. multimodal_M), sum the inputs
 //   steps     x += h a(x, m_j) + b(x, m_j) sqrt(h) xi   (Eq. Euler_Maruyama)
-//             with xi from Philox(p/4, j, n, problem) and the mean
-//             m_{j+1} reduced over the whole group (warp shuffles, a shared
-//             memory stage, then a cross-CTA stage through L2: per-CTA
-//             publication slots and epoch flags, read after a bounded spin)
+//             with xi from Philox(p/4, j, n, problem) and the mean m_j
+//             reduced over the whole group (warp shuffles, a shared-memory
+//             stage, then a cross-CTA stage through L2: one tagged 8-byte
+//             word per CTA and step, read after a bounded wait; with
+//             additive noise the exchange runs one step behind, see
+//             fine_task)
 //   epilogue  store x, restriction per region (Eq. multimodal_R): counts,
 //             means, then centred sums, extremes (two passes, FP64)
 //
