@@ -349,7 +349,7 @@ int mmp_normals(const mmp_problem_desc* desc, int tag, unsigned int j, unsigned 
  *
  * No context, no workspace, no allocation: the scratch of the kernel's
  * cross-CTA mean reduction comes from one fixed array inside libmmp.so
- * (about 171 KB of device memory, held on every GPU that loads the library
+ * (about 650 KB of device memory, held on every GPU that loads the library
  * until the process exits), serving at most MMP_STATIC_MAX_CTAS CTAs per
  * slice; larger problems (above roughly 9.9e6 float or 4.9e6 double
  * particles, depending on the launch shape) return MMP_ERR_UNSUPPORTED.
