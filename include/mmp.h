@@ -127,6 +127,11 @@ typedef struct mmp_ctx mmp_ctx;
 #define MMP_STAT_REGION(i) ((i) < 2 ? 5 * (i) : 5 * (i) + 6)
 
 const char* mmp_strerror(int code);
+/* Version of the C-ABI: 101 adds up to four regions (threshold2, threshold3;
+ * 16-double moment rows, 32-double restriction records), seven-coefficient
+ * adjoints (mmp_set_params' n_theta, mmp_adjoint).  Checkpoints (mmp_get_state)
+ * restore only into the same version. */
+#define MMP_VERSION 101
 int mmp_version(void);
 /* Last CUDA error code seen by the library in this process (0 if none). */
 int mmp_last_cuda_error(void);

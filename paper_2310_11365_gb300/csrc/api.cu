@@ -855,7 +855,7 @@ const char* mmp_strerror(int code) {
   }
 }
 
-int mmp_version(void) { return 100; }
+int mmp_version(void) { return MMP_VERSION; }
 
 int mmp_last_cuda_error(void) { return g_last_cuda_error; }
 

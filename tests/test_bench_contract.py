@@ -26,3 +26,19 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("config2")
+
+
+def test_code_digest_ignores_comments_only():
+    """The profile summary is tied to the kernel's code by a digest that
+    ignores comments and blank lines but not code (string literals kept)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    a = 'int f(int x) {  // one\n  /* two\n lines */ return x + 1;\n}\nconst char* s = "// kept";\n'
+    b = '// a header\nint f(int x) {\n\n  return x + 1;   \n}\nconst char* s = "// kept";\n'
+    c = 'int f(int x) {\n  return x + 2;\n}\nconst char* s = "// kept";\n'
+    d = 'int f(int x) {\n  return x + 1;\n}\nconst char* s = "// changed";\n'
+    sa, sb = bench._strip_comments(a), bench._strip_comments(b)
+    assert sa.replace(" ", "") == sb.replace(" ", "")
+    assert bench._strip_comments(c) != sb and bench._strip_comments(d) != sb
+    assert len(bench.code_digest(bench.PROFILE_SOURCES)) == 16
