@@ -3,6 +3,7 @@ The solve does not shard, so ranks are independent replicas with a barrier
 and max-over-ranks timing.  Checks the rank environment, the barrier, the
 reductions, the whole-job throughput (units of all ranks over the slowest
 rank's time), and that the reference arm does its work on rank 0 only."""
+import json
 import os
 import socket
 import sys
@@ -39,8 +40,8 @@ def _rank_main(rank: int, world: int, port: int, out_dir: str):
     }
     bench.barrier(w)
     dist.destroy_process_group()
-    with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
-        f.write(repr(res))
+    with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as f:
+        json.dump(res, f)
 
 
 def test_two_gloo_replicas(tmp_path):
@@ -49,7 +50,7 @@ def test_two_gloo_replicas(tmp_path):
     port = _free_port()
     mp.spawn(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
     for rank in range(2):
-        res = eval(open(tmp_path / f"rank{rank}.txt").read())
+        res = json.loads((tmp_path / f"rank{rank}.json").read_text())
         assert res["world"] == 2 and res["rank"] == rank and res["local"] == rank
         assert res["max"] == 3.0
         assert res["sum"] == 3000.0
