@@ -14,8 +14,11 @@
  *    names it.  Arguments are checked on the host before any launch.
  *  - memory: the library allocates no device memory.  The caller passes one
  *    device workspace (size from mmp_workspace_size) and owns it; the
- *    context only records pointers.  Host pointers passed in are read or
- *    written before the call returns.
+ *    context only records pointers.  Every device workspace (context,
+ *    adjoint, autotune) starts on a 256-byte boundary, as cudaMalloc's and
+ *    PyTorch's allocations do; a NULL, misaligned or too small workspace is
+ *    MMP_ERR_WORKSPACE, returned before any device work.  Host pointers
+ *    passed in are read or written before the call returns.
  *  - streams: `stream` is a cudaStream_t (passed as void*); all device work
  *    of a context is issued on it, in order.  Calls documented as
  *    "synchronising" wait for that stream before they return.

@@ -1240,7 +1240,8 @@ int mmp_adjoint_workspace_size(mmp_ctx* ctx, int prob, int ckpt_every, size_t* b
 int mmp_adjoint_forward(mmp_ctx* ctx, int prob, int ckpt_every, void* ws, size_t ws_bytes, double* moments_out) {
   int rc = check_prob(ctx, prob);
   if (rc) return rc;
-  if (ws == nullptr || ((uintptr_t)ws % kAlign) != 0 || ckpt_every < 1) return MMP_ERR_INVALID_ARG;
+  if (ckpt_every < 1) return MMP_ERR_INVALID_ARG;
+  if (ws == nullptr || ((uintptr_t)ws % kAlign) != 0) return MMP_ERR_WORKSPACE;
   Prob& p = ctx->probs[prob];
   AdjLayout L;
   rc = adjoint_layout(ctx, p, ckpt_every, (char*)ws, L);
@@ -1291,7 +1292,8 @@ int mmp_adjoint_backward(mmp_ctx* ctx, int prob, const double* gm, const double*
                          double* grad_out) {
   int rc = check_prob(ctx, prob);
   if (rc) return rc;
-  if (gm == nullptr || gv == nullptr || grad_out == nullptr || ws == nullptr) return MMP_ERR_INVALID_ARG;
+  if (gm == nullptr || gv == nullptr || grad_out == nullptr) return MMP_ERR_INVALID_ARG;
+  if (ws == nullptr || ((uintptr_t)ws % kAlign) != 0) return MMP_ERR_WORKSPACE;
   Prob& p = ctx->probs[prob];
   if (!p.adj_ready || p.adj_ws != ws) return MMP_ERR_STATE;
   AdjLayout L;
@@ -1591,8 +1593,9 @@ extern "C" int mmp_autotune_workspace_size(const mmp_problem_desc* desc, size_t*
 
 extern "C" int mmp_autotune(const mmp_problem_desc* desc, const int* candidates, int n_candidates, int probe_steps,
                             void* workspace, size_t bytes, void* stream, int* best_nq, double* rates) {
-  if (desc == nullptr || workspace == nullptr || best_nq == nullptr) return MMP_ERR_INVALID_ARG;
+  if (desc == nullptr || best_nq == nullptr) return MMP_ERR_INVALID_ARG;
   if (candidates != nullptr && n_candidates < 1) return MMP_ERR_INVALID_ARG;
+  if (workspace == nullptr || ((uintptr_t)workspace % kAlign) != 0) return MMP_ERR_WORKSPACE;
   int rc = validate(*desc);
   if (rc) return rc;
   Prob p;

@@ -79,3 +79,27 @@ def test_set_params_arity(mmplib):
     lib = mmplib.load()
     theta = (C.c_double * 7)(*([0.0] * 7))
     assert lib.mmp_set_params(None, 0, theta, 7) == -1
+
+
+def test_workspace_checked_before_any_device_work(mmplib):
+    """A NULL or misaligned device workspace is MMP_ERR_WORKSPACE (-2), for
+    the context, the adjoint and the autotuner, before any CUDA call (so it
+    holds without a GPU); a missing context is MMP_ERR_INVALID_ARG."""
+    lib = mmplib.load()
+    d = mmplib.desc(W.config1())
+    ctx = C.c_void_p()
+    for ws in (None, 8, 4096 + 16):
+        assert lib.mmp_create(C.byref(ctx), C.byref(d), 1, ws, 1 << 20, None) == -2
+        assert not ctx.value
+    best = C.c_int()
+    assert lib.mmp_autotune(C.byref(d), None, 0, 0, 8, 1 << 20, None, C.byref(best), None) == -2
+    assert lib.mmp_autotune(None, None, 0, 0, 4096, 1 << 20, None, C.byref(best), None) == -1
+    assert lib.mmp_autotune(C.byref(d), None, 0, 0, 4096, 1 << 20, None, None, None) == -1
+    n = C.c_size_t()
+    v = (C.c_double * 8)()
+    assert lib.mmp_adjoint_workspace_size(None, 0, 8, C.byref(n)) == -1
+    assert lib.mmp_adjoint_forward(None, 0, 8, 4096, 1 << 20, v) == -1
+    assert lib.mmp_adjoint_backward(None, 0, v, v, 4096, 1 << 20, v) == -1
+    assert lib.mmp_adjoint(None, 0, v, v, 8, 4096, 1 << 20, v, v) == -1
+    assert lib.mmp_iterate(None, 1, None) == -1
+    assert lib.mmp_get_moments(None, 0, v) == -1
