@@ -72,8 +72,21 @@ double orc_normal(const orc_problem* pr, int tag, uint32_t j, uint32_t n, long l
   return z[p % 4];
 }
 
+/* The plane rotator's shift modulo 2 pi into [0, 2 pi] (Sec. 5, Example
+ * "Unimodal plane rotator": applied to every particle in each time step).
+ * reading: the initial ensemble is shifted as well, so that every slice end,
+ * t_0 included, holds particles in [0, 2 pi]. */
+static const double TWO_PI = 6.283185307179586476925286766559;
+
+double orc_wrap(double x) {
+  return x - TWO_PI * floor(x / TWO_PI);
+}
+
 void orc_initial(const orc_problem* pr, double* u0) {
-  for (long long p = 0; p < pr->P; ++p) u0[p] = pr->m0 + pr->s0 * orc_normal(pr, 1, 0, 0, p);
+  for (long long p = 0; p < pr->P; ++p) {
+    u0[p] = pr->m0 + pr->s0 * orc_normal(pr, 1, 0, 0, p);
+    if (pr->family == ORC_FAMILY_ROTATOR) u0[p] = orc_wrap(u0[p]);
+  }
 }
 
 /* ------------------------------------------------------------------------
@@ -109,6 +122,23 @@ static double ensemble_mean(const double* u, long long P) {
   return s / (double)P;
 }
 
+/* Plane rotator: (K/P) sum_q sin(X_q - x) = K (S cos x - C sin x) by the
+ * difference formula for the sine, with S, C the ensemble means of sin X and
+ * cos X; the pinning term -g sin x. */
+static double rotator_drift(const orc_problem* pr, double x, double S, double C) {
+  return pr->K * (S * cos(x) - C * sin(x)) - pr->g * sin(x);
+}
+
+static void ensemble_sin_cos(const double* u, long long P, double* S, double* C) {
+  double s = 0.0, c = 0.0;
+  for (long long p = 0; p < P; ++p) {
+    s += sin(u[p]);
+    c += cos(u[p]);
+  }
+  *S = s / (double)P;
+  *C = c / (double)P;
+}
+
 void orc_fine(const orc_problem* pr, int n, const double* u_in, double* u_out, double* means) {
   const long long P = pr->P;
   const int nf = orc_fine_steps(pr);
@@ -117,15 +147,22 @@ void orc_fine(const orc_problem* pr, int n, const double* u_in, double* u_out, d
   double* x = (double*)malloc(sizeof(double) * (size_t)P);
   double* y = (double*)malloc(sizeof(double) * (size_t)P);
   memcpy(x, u_in, sizeof(double) * (size_t)P);
+  const int rotator = pr->family == ORC_FAMILY_ROTATOR;
   for (int j = 0; j < nf; ++j) {
     double m = ensemble_mean(x, P);
     if (means) means[j] = m;
+    double S = 0.0, C = 0.0;
+    if (rotator) ensemble_sin_cos(x, P, &S, &C);
     for (long long q = 0; 4 * q < P; ++q) {
       double z[4];
       normals4(pr, 0, (uint32_t)j, (uint32_t)n, (uint32_t)q, z);
       for (int w = 0; w < 4 && 4 * q + w < P; ++w) {
         long long p = 4 * q + w;
-        y[p] = x[p] + drift(pr, x[p], m) * h + diffusion(pr, x[p], m) * sqrt_h * z[w];
+        if (rotator) {
+          y[p] = orc_wrap(x[p] + rotator_drift(pr, x[p], S, C) * h + pr->B0 * sqrt_h * z[w]);
+        } else {
+          y[p] = x[p] + drift(pr, x[p], m) * h + diffusion(pr, x[p], m) * sqrt_h * z[w];
+        }
       }
     }
     double* t = x; x = y; y = t;
@@ -265,10 +302,80 @@ int orc_coarse_steps(const orc_problem* pr) {
  *   Taylor:  dm = a(m) + a_XX(m) v / 2, dv = (2 a_X(m) + b_X^2) v + b(m)^2
  *            (Eq. moment_model_class_1; the same model without its Sigma^2
  *            term for this drift);
+ *   Taylor1: the Taylor model without its Sigma term in the mean,
+ *            dm = a(m);
  *   sigma-point: the expectations of Eq. Gaussian_model_McK_V_SDE by a
  *            k-point rule on N(m, v): k = 2: m -+ sqrt(v), weights 1/2;
  *            k = 3: m, m -+ sqrt(3 v), weights 2/3, 1/6, 1/6. */
+static void sigma_points(int model, double m, double v, double* xs, double* ws, int* k) {
+  if (model == ORC_COARSE_SIGMA2) {
+    double d = sqrt(v > 0.0 ? v : 0.0);
+    xs[0] = m - d; xs[1] = m + d;
+    ws[0] = 0.5; ws[1] = 0.5;
+    *k = 2;
+  } else {
+    double d = sqrt(3.0 * (v > 0.0 ? v : 0.0));
+    xs[0] = m; xs[1] = m - d; xs[2] = m + d;
+    ws[0] = 2.0 / 3.0; ws[1] = 1.0 / 6.0; ws[2] = 1.0 / 6.0;
+    *k = 3;
+  }
+}
+
+/* Coarse moment ODE of the plane rotator (one region), the mean-field means
+ * S = E[sin X], C = E[cos X] taken under each model's own law:
+ *   closure: X ~ N(m, v): E sin X = sin m e^{-v/2}, E cos X = cos m e^{-v/2};
+ *            dm = E[a] = K (S C - C S) - g S, and by Stein's lemma
+ *            E[(X - m) f(X)] = v E[f'(X)]:
+ *            dv = 2 v E[a_X] + B0^2 = 2 v (-K (S^2 + C^2) - g C) + B0^2;
+ *   Taylor:  the point mass at m (S = sin m, C = cos m) and the derivatives
+ *            of a at m: dm = a(m) + a_XX(m) v / 2 = -g sin m + g sin m v / 2,
+ *            dv = 2 a_X(m) v + B0^2 = 2 (-K - g cos m) v + B0^2, which is
+ *            Eq. plane_rotator_third_order for g = 1;
+ *            reading: that equation's variance line prints
+ *            -2 (-K - cos M) Sigma, a growing variance; Eq.
+ *            moment_model_class_1 gives +2 a_X Sigma with a_X = -K - cos M;
+ *   Taylor1: the same without the Sigma term of the mean (the paper's first
+ *            coarse solver of this example);
+ *   sigma-point: the k-point rule for every expectation, S and C included. */
+static void rotator_rhs(const orc_problem* pr, double m, double v, double* dm, double* dv) {
+  const double b2 = pr->B0 * pr->B0;
+  if (pr->coarse_model == ORC_COARSE_TAYLOR || pr->coarse_model == ORC_COARSE_TAYLOR1) {
+    const double S = sin(m), C = cos(m);
+    const double a = rotator_drift(pr, m, S, C);
+    const double ax = pr->K * (-S * sin(m) - C * cos(m)) - pr->g * cos(m);
+    const double axx = pr->K * (-S * cos(m) + C * sin(m)) + pr->g * sin(m);
+    *dm = pr->coarse_model == ORC_COARSE_TAYLOR ? a + 0.5 * axx * v : a;
+    *dv = 2.0 * ax * v + b2;
+  } else if (pr->coarse_model == ORC_COARSE_SIGMA2 || pr->coarse_model == ORC_COARSE_SIGMA3) {
+    double xs[3], ws[3];
+    int k;
+    sigma_points(pr->coarse_model, m, v, xs, ws, &k);
+    double S = 0.0, C = 0.0;
+    for (int s = 0; s < k; ++s) {
+      S += ws[s] * sin(xs[s]);
+      C += ws[s] * cos(xs[s]);
+    }
+    double ea = 0.0, exa = 0.0;
+    for (int s = 0; s < k; ++s) {
+      const double a = rotator_drift(pr, xs[s], S, C);
+      ea += ws[s] * a;
+      exa += ws[s] * (xs[s] - m) * a;
+    }
+    *dm = ea;
+    *dv = 2.0 * exa + b2;
+  } else {
+    const double e = exp(-0.5 * v);
+    const double S = sin(m) * e, C = cos(m) * e;
+    *dm = pr->K * (S * C - C * S) - pr->g * S;
+    *dv = 2.0 * v * (-pr->K * (S * S + C * C) - pr->g * C) + b2;
+  }
+}
+
 void orc_coarse_rhs(const orc_problem* pr, const orc_macro* r, double* dm, double* dv) {
+  if (pr->family == ORC_FAMILY_ROTATOR) {
+    rotator_rhs(pr, r->mean[0], r->var[0], &dm[0], &dv[0]);
+    return;
+  }
   const int I = pr->n_regions < 2 ? 1 : pr->n_regions;
   double M = 0.0;
   if (I == 1) {
@@ -278,26 +385,16 @@ void orc_coarse_rhs(const orc_problem* pr, const orc_macro* r, double* dm, doubl
   }
   for (int i = 0; i < I; ++i) {
     double m = r->mean[i], v = r->var[i];
-    if (pr->coarse_model == ORC_COARSE_TAYLOR) {
+    if (pr->coarse_model == ORC_COARSE_TAYLOR || pr->coarse_model == ORC_COARSE_TAYLOR1) {
       double ax = -3.0 * pr->c3 * m * m + pr->c1;
       double axx = -6.0 * pr->c3 * m;
       double b = diffusion(pr, m, M);
-      dm[i] = drift(pr, m, M) + 0.5 * axx * v;
+      dm[i] = drift(pr, m, M) + (pr->coarse_model == ORC_COARSE_TAYLOR ? 0.5 * axx * v : 0.0);
       dv[i] = (2.0 * ax + pr->B * pr->B) * v + b * b;
     } else if (pr->coarse_model == ORC_COARSE_SIGMA2 || pr->coarse_model == ORC_COARSE_SIGMA3) {
       double xs[3], ws[3];
       int k;
-      if (pr->coarse_model == ORC_COARSE_SIGMA2) {
-        double d = sqrt(v > 0.0 ? v : 0.0);
-        xs[0] = m - d; xs[1] = m + d;
-        ws[0] = 0.5; ws[1] = 0.5;
-        k = 2;
-      } else {
-        double d = sqrt(3.0 * (v > 0.0 ? v : 0.0));
-        xs[0] = m; xs[1] = m - d; xs[2] = m + d;
-        ws[0] = 2.0 / 3.0; ws[1] = 1.0 / 6.0; ws[2] = 1.0 / 6.0;
-        k = 3;
-      }
+      sigma_points(pr->coarse_model, m, v, xs, ws, &k);
       double ea = 0.0, exa = 0.0, eb2 = 0.0;
       for (int s = 0; s < k; ++s) {
         double a = drift(pr, xs[s], M);
@@ -824,6 +921,7 @@ int orc_parareal(const orc_problem* pr, const double* u0_in, double* hist, orc_m
   const double dT = pr->T / N;
   int K = pr->max_iter < N ? pr->max_iter : N;
   if (K < 1) K = 1;
+  if (pr->family == ORC_FAMILY_ROTATOR && I > 1) return -1;
 
   double* u0 = (double*)malloc(sizeof(double) * (size_t)P);
   if (u0_in) memcpy(u0, u0_in, sizeof(double) * (size_t)P);
@@ -1023,6 +1121,7 @@ void orc_fine_serial(const orc_problem* pr, const double* u0_in, orc_stats* stat
  * ---------------------------------------------------------------------- */
 int orc_adjoint(const orc_problem* pr, const double* u0_in, const double* gm, const double* gv,
                 double grad[ORC_N_THETA], double* moments) {
+  if (pr->family == ORC_FAMILY_ROTATOR) return -1;
   const long long P = pr->P;
   const int N = pr->N;
   const int nf = orc_fine_steps(pr);
@@ -1098,6 +1197,7 @@ int orc_adjoint(const orc_problem* pr, const double* u0_in, const double* gm, co
 
 int orc_adjoint_loss(const orc_problem* pr, const double* u0_in, const double* m_tgt,
                      const double* v_tgt, double grad[ORC_N_THETA], double* loss) {
+  if (pr->family == ORC_FAMILY_ROTATOR) return -1;
   const int N = pr->N;
   double* mom = (double*)malloc(sizeof(double) * 2 * (size_t)(N + 1));
   double* gm = (double*)calloc((size_t)N, sizeof(double));

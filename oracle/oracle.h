@@ -17,6 +17,15 @@
  * Lemma 2.1 is c3 = 0; the cubic and double-well drifts of Sec. 5.3 are
  * c3 > 0 with additive noise (B = BE = 0).
  *
+ * A second family, the plane rotator of Sec. 5 (Example "Unimodal plane
+ * rotator", Eq. SDE_plane_rotator), has the drift
+ *   a(x) = (K/P) sum_q sin(X_q - x) - g sin x = K (S cos x - C sin x) - g sin x
+ * with S, C the ensemble means of sin X and cos X (the particle itself
+ * included, sin 0 = 0), g = 1 in the paper, additive noise b = B0 =
+ * sqrt(2 k_B T), and every particle shifted modulo 2 pi into [0, 2 pi]
+ * (x - 2 pi floor(x / 2 pi)) after each Euler-Maruyama step and in the
+ * initial ensemble.  It has one region and no adjoint here.
+ *
  * Random numbers (Property 3.3 needs the same draws in every iteration):
  * Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with
  *   key     = (seed mod 2^32, seed div 2^32)
@@ -40,6 +49,7 @@ extern "C" {
 #define ORC_MAX_REGIONS 4
 
 enum { ORC_UNIMODAL = 0, ORC_MULTIMODAL = 1, ORC_LEARNING = 2 };
+enum { ORC_FAMILY_POLY = 0, ORC_FAMILY_ROTATOR = 1 };
 
 typedef struct {
   double c3, c1, kappa, c0;   /* drift coefficients */
@@ -59,6 +69,8 @@ typedef struct {
   int max_iter;               /* at most this many fine sweeps (<= N) */
   int coarse_model;           /* ORC_COARSE_CLOSURE / _TAYLOR / _SIGMA2 / _SIGMA3 */
   double threshold2, threshold3;  /* t_2, t_3 (n_regions 3, 4): D_2 = {t_2 <= x (< t_3)}, D_3 = {x >= t_3} */
+  int family;                 /* ORC_FAMILY_POLY / ORC_FAMILY_ROTATOR */
+  double K, g;                /* plane rotator: coupling K, pinning g (c3..c0, B, BE unused) */
 } orc_problem;
 
 /* Coarse moment models (Sec. 2): the Gaussian closure (expectations of the
@@ -69,6 +81,9 @@ typedef struct {
 #define ORC_COARSE_TAYLOR 1
 #define ORC_COARSE_SIGMA2 2
 #define ORC_COARSE_SIGMA3 3
+/* The Taylor model without the Sigma term of the mean, dM = a(M) (the first
+ * coarse model of the plane-rotator example). */
+#define ORC_COARSE_TAYLOR1 4
 
 /* Restriction of one ensemble (Eq. multimodal_R plus the extremes needed by
  * the "fractions unchanged" test of Def. 3.2). */
@@ -95,6 +110,9 @@ double orc_uniform(uint32_t word);
 double orc_normal(const orc_problem* pr, int tag, uint32_t j, uint32_t n, long long p);
 /* X0 = m0 + s0 z, tag 1 */
 void orc_initial(const orc_problem* pr, double* u0);
+
+/* x shifted modulo 2 pi into [0, 2 pi] (plane rotator) */
+double orc_wrap(double x);
 
 /* -- fine propagator (Eq. Euler_Maruyama) -------------------------------- */
 int orc_fine_steps(const orc_problem* pr);
@@ -164,6 +182,7 @@ typedef struct {
  *   u0_in    optional user initial ensemble (NULL: tag-1 Philox draws) */
 int orc_parareal(const orc_problem* pr, const double* u0_in, double* hist, orc_macro* macro,
                  double* parts, orc_result* res);
+/* orc_parareal returns 0, or -1 for a plane rotator with more than one region. */
 
 /* Serial reference u_{n+1} = F_n(u_n): stats[n] = R(u_n), n = 0..N;
  * parts (optional) [(N+1) * P]. */
@@ -177,7 +196,7 @@ void orc_fine_serial(const orc_problem* pr, const double* u0_in, orc_stats* stat
  * adjoint of the Euler-Maruyama recursion on the same draws (additive,
  * state-proportional and mean-field diffusion alike).  Stores the whole
  * trajectory (P (N n_f + 1) doubles).  moments (optional) receives
- * (M_n, V_n), n = 0..N.  Returns 0. */
+ * (M_n, V_n), n = 0..N.  Returns 0, or -1 for the plane rotator. */
 int orc_adjoint(const orc_problem* pr, const double* u0_in, const double* gm, const double* gv,
                 double grad[ORC_N_THETA], double* moments);
 /* L = sum_n (M_n - m_tgt[n-1])^2 + (V_n - v_tgt[n-1])^2 and its gradient. */

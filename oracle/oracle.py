@@ -20,6 +20,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 UNIMODAL, MULTIMODAL, LEARNING = 0, 1, 2
 MAX_REGIONS = 4
+POLY, ROTATOR = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -46,6 +47,7 @@ class OrcProblem(C.Structure):
         ("variant", C.c_int), ("seed", C.c_uint64), ("problem_tag", C.c_uint32),
         ("tol", C.c_double), ("max_iter", C.c_int), ("coarse_model", C.c_int),
         ("threshold2", C.c_double), ("threshold3", C.c_double),
+        ("family", C.c_int), ("K", C.c_double), ("g", C.c_double),
     ]
 
 
@@ -91,6 +93,8 @@ def lib():
         _lib.orc_fine_h.argtypes = [pp]
         _lib.orc_fine_h.restype = C.c_double
         _lib.orc_fine.argtypes = [pp, C.c_int, d, d, d]
+        _lib.orc_wrap.argtypes = [C.c_double]
+        _lib.orc_wrap.restype = C.c_double
         _lib.orc_region.argtypes = [pp, C.c_double]
         _lib.orc_restrict.argtypes = [pp, d, C.POINTER(OrcStats)]
         _lib.orc_mixture.argtypes = [pp, C.POINTER(OrcMacro), d, d]
@@ -135,7 +139,7 @@ def problem(p) -> OrcProblem:
     return OrcProblem(
         p.c3, p.c1, p.kappa, p.c0, p.B, p.BE, p.B0, p.m0, p.s0, p.T, p.N, p.dt, p.P,
         p.coarse_h, p.n_regions, p.threshold, p.variant, p.seed, p.problem_tag, p.tol, max_iter,
-        p.coarse_model, p.threshold2, p.threshold3,
+        p.coarse_model, p.threshold2, p.threshold3, p.family, p.K, p.g,
     )
 
 
@@ -161,6 +165,11 @@ def initial(p) -> np.ndarray:
     u = np.empty(p.P, np.float64)
     lib().orc_initial(C.byref(pr), _dp(u))
     return u
+
+
+def wrap(x: float) -> float:
+    """The plane rotator's shift of x modulo 2 pi into [0, 2 pi]."""
+    return lib().orc_wrap(float(x))
 
 
 def fine_steps(p) -> int:
@@ -316,7 +325,9 @@ def parareal(p, u0: np.ndarray | None = None, want_parts: bool = False) -> dict:
     parts = np.empty((N + 1) * p.P) if want_parts else None
     res = OrcResult()
     u0a = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64)
-    lib().orc_parareal(C.byref(pr), _dp(u0a), _dp(hist.reshape(-1)), mac, _dp(parts), C.byref(res))
+    rc = lib().orc_parareal(C.byref(pr), _dp(u0a), _dp(hist.reshape(-1)), mac, _dp(parts), C.byref(res))
+    if rc != 0:
+        raise ValueError(f"orc_parareal returned {rc}")
     out = {
         "hist": hist[: res.sweeps + 1],
         "frac": np.array([list(m.frac) for m in mac]),

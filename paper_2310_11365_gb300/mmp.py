@@ -140,6 +140,9 @@ def _check(rc: int, where: str):
 
 
 def desc(p: workloads.Problem) -> ProblemDesc:
+    if p.family != workloads.POLY:
+        # the library's kernels propagate the polynomial drift family only
+        raise MMPError(-3, "desc")
     prec = MMP_MIXED if p.precision == "mixed" else MMP_FP64
     return ProblemDesc(p.c3, p.c1, p.kappa, p.c0, p.B, p.BE, p.B0, p.m0, p.s0, p.T, p.N, p.dt, p.P,
                        p.coarse_h, p.n_regions, p.threshold, p.variant, prec, p.seed, p.problem_tag,

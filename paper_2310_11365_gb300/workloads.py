@@ -15,6 +15,12 @@ which covers the linear SDE of Lemma 2.1 (c3 = 0), the cubic drift and the
 double well V(x) = a x^4 - b x^2 of Sec. 5.3 Eq. (SDE_bimodal_first_time)
 (c3 = 4a, the x coefficient 2b, plus the mean-field term kappa (E[X] - x)).
 
+A second family (family = ROTATOR) is the plane rotator of Sec. 5 (Example
+"Unimodal plane rotator", Eq. SDE_plane_rotator): drift
+(K/P) sum_q sin(X_q - x) - g sin x, additive noise B0 = sqrt(2 k_B T), the
+particles shifted modulo 2 pi into [0, 2 pi].  Only the oracle propagates it
+so far; the CUDA library refuses it.
+
 The paper runs on synthetic SDEs only (no dataset, Sec. 5); the five
 workloads below take the shapes of its unimodal and bimodal examples at the
 sizes the project measures.
@@ -27,7 +33,8 @@ from dataclasses import dataclass, replace
 import numpy as np
 
 UNIMODAL, MULTIMODAL, LEARNING = 0, 1, 2
-CLOSURE, TAYLOR, SIGMA2, SIGMA3 = 0, 1, 2, 3  # coarse moment models
+CLOSURE, TAYLOR, SIGMA2, SIGMA3, TAYLOR1 = 0, 1, 2, 3, 4  # coarse moment models
+POLY, ROTATOR = 0, 1  # drift families
 SEED_BASE = 0x231011365
 
 
@@ -58,6 +65,9 @@ class Problem:
     coarse_model: int = 0      # CLOSURE, TAYLOR, SIGMA2 or SIGMA3
     threshold2: float = 0.0    # region boundaries t_2 < t_3 for n_regions 3 and 4
     threshold3: float = 0.0
+    family: int = POLY         # POLY (the polynomial drift above) or ROTATOR
+    K: float = 0.0             # plane rotator: coupling K and pinning g
+    g: float = 0.0
 
     def scaled(self, **kw) -> "Problem":
         return replace(copy.copy(self), **kw)
@@ -88,6 +98,17 @@ def gbm(**kw) -> Problem:
     p = Problem(c3=0.0, c1=-0.5, kappa=0.8, c0=1.0 / 3.0, B=s, BE=s, B0=1.0 / 6.0, m0=1.0, s0=0.5,
                 T=1.0, N=10, dt=1e-3, P=100_000, coarse_h=0.25, seed=SEED_BASE + 6, tol=1e-8,
                 precision="fp64")
+    return p.scaled(**kw) if kw else p
+
+
+def plane_rotator(K: float = 1.0, kT: float = 0.25, g: float = 1.0, **kw) -> Problem:
+    """The unimodal plane rotator of Sec. 5: T = 10, dt = 1e-3, P = 1e5 and
+    X0 ~ N(pi/4, 3 pi/4) (read as mean and variance) as in the paper; the
+    coupling K and temperature k_B T are not given there (K = 1, k_B T = 1/4
+    here, so B0 = sqrt(2 k_B T)), nor is N (10 slices here)."""
+    p = Problem(family=ROTATOR, K=K, g=g, B0=float(np.sqrt(2.0 * kT)), m0=np.pi / 4,
+                s0=float(np.sqrt(3.0 * np.pi / 4)), T=10.0, N=10, dt=1e-3, P=100_000, coarse_h=0.25,
+                seed=SEED_BASE + 7, tol=1e-6, precision="fp64")
     return p.scaled(**kw) if kw else p
 
 

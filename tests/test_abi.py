@@ -103,3 +103,11 @@ def test_workspace_checked_before_any_device_work(mmplib):
     assert lib.mmp_adjoint(None, 0, v, v, 8, 4096, 1 << 20, v, v) == -1
     assert lib.mmp_iterate(None, 1, None) == -1
     assert lib.mmp_get_moments(None, 0, v) == -1
+
+
+def test_plane_rotator_is_refused_by_the_library(mmplib):
+    """The plane rotator (a drift family only the oracle propagates) never
+    reaches the library as a polynomial problem: the binding refuses it."""
+    with pytest.raises(mmplib.MMPError) as e:
+        mmplib.mmp_workspace_size([W.plane_rotator(P=1000)])
+    assert e.value.code == -3
