@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -48,12 +49,12 @@ using namespace mmp;
 
 namespace {
 
-
-int g_last_cuda_error = 0;
+// written by any thread that sees a CUDA call fail
+std::atomic<int> g_last_cuda_error{0};
 
 // Records a failed CUDA call; MMP_DEBUG=1 also names it on stderr.
 int cuda_fail(cudaError_t e, const char* what, int line) {
-  g_last_cuda_error = (int)e;
+  g_last_cuda_error.store((int)e, std::memory_order_relaxed);
   static const bool debug = [] {
     const char* v = std::getenv("MMP_DEBUG");
     return v != nullptr && v[0] == '1';
@@ -857,7 +858,7 @@ const char* mmp_strerror(int code) {
 
 int mmp_version(void) { return MMP_VERSION; }
 
-int mmp_last_cuda_error(void) { return g_last_cuda_error; }
+int mmp_last_cuda_error(void) { return g_last_cuda_error.load(std::memory_order_relaxed); }
 
 int mmp_workspace_size(const mmp_problem_desc* descs, int n_problems, size_t* bytes) {
   if (bytes == nullptr) return MMP_ERR_INVALID_ARG;
