@@ -70,12 +70,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(src: str) -> str:
         obj = os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src, __file__] + headers):
-            cmd = [cc, *ARCH, *CFLAGS, *FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
-            if verbose:
-                cmd.insert(1, "-Xptxas=-v")
+            # -Xptxas=-v only reports (registers, stack, spills); its report
+            # is kept beside the object for resource_usage()
+            cmd = [cc, "-Xptxas=-v", *ARCH, *CFLAGS, *FILE_FLAGS.get(os.path.basename(src), []), "-c", src,
+                   "-o", obj]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+            with open(obj[:-2] + ".ptxas.txt", "w") as fh:
+                fh.write(r.stderr)
             if verbose:
                 sys.stderr.write(r.stderr)
         return obj
@@ -90,6 +93,40 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
     return LIB
+
+
+def resource_usage() -> dict[str, dict]:
+    """Per kernel (mangled name), what ptxas reported when the library was
+    last compiled: registers, stack frame bytes, spill store and load bytes."""
+    import re
+
+    out: dict[str, dict] = {}
+    for log in sorted(glob.glob(os.path.join(OBJDIR, "*.ptxas.txt"))):
+        props: dict[str, tuple[int, int, int]] = {}
+        current = None   # the function whose properties come next
+        entry = None     # the entry whose register count comes next
+        for line in open(log):
+            m = re.search(r"Function properties for (\S+)", line)
+            if m:
+                current = m.group(1)
+                continue
+            m = re.search(r"(\d+) bytes stack frame, (\d+) bytes spill stores, (\d+) bytes spill loads", line)
+            if m and current is not None:
+                props[current] = tuple(int(g) for g in m.groups())
+                current = None
+                continue
+            m = re.search(r"Compiling entry function '(\S+)'", line)
+            if m:
+                entry = m.group(1)
+                continue
+            m = re.search(r"Used (\d+) registers", line)
+            if m and entry is not None:
+                out[entry] = {"registers": int(m.group(1)), "file": os.path.basename(log)[: -len(".ptxas.txt")]}
+                entry = None
+        for name, rec in out.items():
+            if name in props:
+                rec["stack"], rec["spill_stores"], rec["spill_loads"] = props[name]
+    return out
 
 
 if __name__ == "__main__":
