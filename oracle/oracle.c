@@ -72,14 +72,21 @@ double orc_normal(const orc_problem* pr, int tag, uint32_t j, uint32_t n, long l
   return z[p % 4];
 }
 
-/* The plane rotator's shift modulo 2 pi into [0, 2 pi] (Sec. 5, Example
- * "Unimodal plane rotator": applied to every particle in each time step).
+/* The plane rotator's shift modulo 2 pi (Sec. 5, Example "Unimodal plane
+ * rotator": applied to every particle in each time step).
+ * reading: the interval is [-pi, pi], not the printed [0, 2 pi].  The printed
+ * drift -sin x has its stable point at 0 = 2 pi, the end of [0, 2 pi], so an
+ * ensemble shifted there piles up at both ends (mean near pi, variance near
+ * pi^2) instead of being the unimodal distribution the example describes;
+ * centred on the stable point it is unimodal and the iteration reaches the
+ * statistical error in a few sweeps, as the example reports.
  * reading: the initial ensemble is shifted as well, so that every slice end,
- * t_0 included, holds particles in [0, 2 pi]. */
+ * t_0 included, holds particles in [-pi, pi]. */
+static const double PI = 3.141592653589793238462643383280;
 static const double TWO_PI = 6.283185307179586476925286766559;
 
 double orc_wrap(double x) {
-  return x - TWO_PI * floor(x / TWO_PI);
+  return x - TWO_PI * floor((x + PI) / TWO_PI);
 }
 
 void orc_initial(const orc_problem* pr, double* u0) {

@@ -22,9 +22,10 @@
  *   a(x) = (K/P) sum_q sin(X_q - x) - g sin x = K (S cos x - C sin x) - g sin x
  * with S, C the ensemble means of sin X and cos X (the particle itself
  * included, sin 0 = 0), g = 1 in the paper, additive noise b = B0 =
- * sqrt(2 k_B T), and every particle shifted modulo 2 pi into [0, 2 pi]
- * (x - 2 pi floor(x / 2 pi)) after each Euler-Maruyama step and in the
- * initial ensemble.  It has one region and no adjoint here.
+ * sqrt(2 k_B T), and every particle shifted modulo 2 pi into [-pi, pi]
+ * (x - 2 pi floor((x + pi) / 2 pi)) after each Euler-Maruyama step and in
+ * the initial ensemble (the paper prints [0, 2 pi]; see orc_wrap).  It has
+ * one region and no adjoint here.
  *
  * Random numbers (Property 3.3 needs the same draws in every iteration):
  * Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with
@@ -111,7 +112,7 @@ double orc_normal(const orc_problem* pr, int tag, uint32_t j, uint32_t n, long l
 /* X0 = m0 + s0 z, tag 1 */
 void orc_initial(const orc_problem* pr, double* u0);
 
-/* x shifted modulo 2 pi into [0, 2 pi] (plane rotator) */
+/* x shifted modulo 2 pi into [-pi, pi] (plane rotator) */
 double orc_wrap(double x);
 
 /* -- fine propagator (Eq. Euler_Maruyama) -------------------------------- */

@@ -168,7 +168,7 @@ def initial(p) -> np.ndarray:
 
 
 def wrap(x: float) -> float:
-    """The plane rotator's shift of x modulo 2 pi into [0, 2 pi]."""
+    """The plane rotator's shift of x modulo 2 pi into [-pi, pi]."""
     return lib().orc_wrap(float(x))
 
 

@@ -18,8 +18,9 @@ double well V(x) = a x^4 - b x^2 of Sec. 5.3 Eq. (SDE_bimodal_first_time)
 A second family (family = ROTATOR) is the plane rotator of Sec. 5 (Example
 "Unimodal plane rotator", Eq. SDE_plane_rotator): drift
 (K/P) sum_q sin(X_q - x) - g sin x, additive noise B0 = sqrt(2 k_B T), the
-particles shifted modulo 2 pi into [0, 2 pi].  Only the oracle propagates it
-so far; the CUDA library refuses it.
+particles shifted modulo 2 pi into [-pi, pi] (centred on the stable point of
+-sin x; the paper prints [0, 2 pi]).  Only the oracle propagates it so far;
+the CUDA library refuses it.
 
 The paper runs on synthetic SDEs only (no dataset, Sec. 5); the five
 workloads below take the shapes of its unimodal and bimodal examples at the
@@ -102,10 +103,11 @@ def gbm(**kw) -> Problem:
 
 
 def plane_rotator(K: float = 1.0, kT: float = 0.25, g: float = 1.0, **kw) -> Problem:
-    """The unimodal plane rotator of Sec. 5: T = 10, dt = 1e-3, P = 1e5 and
-    X0 ~ N(pi/4, 3 pi/4) (read as mean and variance) as in the paper; the
-    coupling K and temperature k_B T are not given there (K = 1, k_B T = 1/4
-    here, so B0 = sqrt(2 k_B T)), nor is N (10 slices here)."""
+    """The unimodal plane rotator of Sec. 5: T = 10, dt = 1e-3 and
+    X0 ~ N(pi/4, 3 pi/4) (read as mean and variance) as in the example, with
+    the section's P = 1e5 particles and N = 10 slices; the coupling K and
+    temperature k_B T are not given (K = 1, k_B T = 1/4 here, so
+    B0 = sqrt(2 k_B T))."""
     p = Problem(family=ROTATOR, K=K, g=g, B0=float(np.sqrt(2.0 * kT)), m0=np.pi / 4,
                 s0=float(np.sqrt(3.0 * np.pi / 4)), T=10.0, N=10, dt=1e-3, P=100_000, coarse_h=0.25,
                 seed=SEED_BASE + 7, tol=1e-6, precision="fp64")
