@@ -10,6 +10,15 @@
  * Everything is written for clarity, not speed: one thread, double
  * precision, no blocking or fusion beyond what the paper states.
  *
+ * Pins (tests/test_oracle_*.py): every function here is checked against
+ * something other than itself -- closed forms, exact sample-path
+ * identities, quadrature, brute force on tiny ensembles, invariants such as
+ * Lemma 3.1 and Property 3.3, the classical Parareal recursion, and the
+ * outcomes the paper states for its setups.  Parity unpinned: the values of
+ * whole nonlinear runs (orc_parareal on the cubic, double-well and rotator
+ * models at full size), for which the paper prints no numbers (its figures
+ * are not in the text); they rest on the pinned parts and the invariants.
+ *
  * The model family (Sec. 2.1, Eq. SDE_class_1 with f(x) = x):
  *   drift      a(x, m) = -c3 x^3 + c1 x + kappa m + c0
  *   diffusion  b(x, m) = B x + BE m + B0
