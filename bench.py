@@ -92,7 +92,7 @@ def _profile_bytes_per_slice():
         if code_digest(PROFILE_SOURCES) != fields.get("code-sha256-16:"):
             return None
         return float(fields["dram-bytes-per-slice:"])
-    except Exception:
+    except (OSError, KeyError, ValueError):
         return None
 
 
@@ -100,7 +100,7 @@ def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)
-    except Exception:
+    except (OSError, ValueError):
         return {}
 
 
@@ -122,7 +122,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except Exception:
+        except OSError:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
@@ -140,7 +140,7 @@ class ClockSampler:
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
-        except Exception:
+        except subprocess.TimeoutExpired:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
