@@ -39,6 +39,8 @@ def test_strerror_and_version(mmplib):
     dict(tol=-1.0), dict(n_regions=3, threshold=0.5, threshold2=0.5),
     dict(n_regions=4, threshold=-1.0, threshold2=0.0, threshold3=-0.5),
     dict(n_regions=3, threshold=0.0, threshold2=float("inf")),
+    dict(P=2**31), dict(N=1, T=1e3, dt=1e-7), dict(N=1, T=1.0, coarse_h=1e-9), dict(coarse_model=5),
+    dict(B0=float("inf")), dict(precision="fp64", m0=float("nan")),
 ])
 def test_invalid_descriptor_rejected_on_host(mmplib, bad):
     p = W.config1(**bad)
