@@ -82,7 +82,7 @@ typedef struct {
   double T;                  /* horizon, > 0                                  */
   int N;                     /* slices, 1..65535                              */
   double dt;                 /* requested fine step, > 0                      */
-  long long P;               /* particles, 1..2^31                            */
+  long long P;               /* particles, 1 .. 2^31 - 8                      */
   double coarse_h;           /* largest coarse step, > 0                      */
   int n_regions;             /* 1 .. MMP_MAX_REGIONS                          */
   double threshold;          /* t_1, the first region boundary (n_regions > 1)  */
@@ -272,12 +272,14 @@ int mmp_timing(mmp_ctx* ctx, int reset, double* fine_ms, long long* fine_launche
  * view of the iteration (sweeps done, finished, last change, which buffer
  * holds each slice's latest output).  mmp_state_size gives its bytes;
  * mmp_get_state writes it to host memory `dst` (caller-owned, that many
- * bytes); mmp_set_state restores it into a context created with the same
+ * bytes); mmp_set_state restores it from host memory `src` (that many bytes)
+ * into a context created with the same
  * problem descriptions and the same launch plans, at any workspace address:
  * the next mmp_iterate continues exactly as the saved context would have,
  * bit for bit.  Adjoint recordings are not part of the state.  Both
  * synchronise.  Errors: MMP_ERR_INVALID_ARG (NULL), MMP_ERR_STATE (the blob
- * belongs to other problems, plans or library version), MMP_ERR_CUDA.  The
+ * belongs to other problems, plans or library version, or holds an iteration
+ * state no run reaches; the context is then left unchanged), MMP_ERR_CUDA.  The
  * paper has no counterpart (a property of this library). */
 int mmp_state_size(mmp_ctx* ctx, size_t* bytes);
 int mmp_get_state(mmp_ctx* ctx, void* dst);

@@ -1816,6 +1816,23 @@ extern "C" int mmp_set_state(mmp_ctx* ctx, const void* src) {
   if (hd.magic != kStateMagic || hd.version != mmp_version() || hd.n != (int)ctx->probs.size() ||
       hd.digest != state_digest(ctx) || hd.ws_used != ctx->ws_used)
     return MMP_ERR_STATE;
+  // every host view must be one this context could have reached (the output
+  // buffer indices select device buffers) before anything is changed
+  const char* j = i;
+  for (const Prob& p : ctx->probs) {
+    ProbState ps;
+    std::memcpy(&ps, j, sizeof(ps));
+    j += sizeof(ps);
+    if (ps.sweeps < 0 || ps.sweeps > p.d.N || (unsigned)ps.lifted > 1u || (unsigned)ps.done > 1u ||
+        (unsigned)ps.converged > 1u)
+      return MMP_ERR_STATE;
+    for (int n = 0; n < p.d.N; ++n) {
+      int b;
+      std::memcpy(&b, j + sizeof(int) * (size_t)n, sizeof(b));
+      if (b < -1 || b > 1) return MMP_ERR_STATE;
+    }
+    j += sizeof(int) * (size_t)p.d.N;
+  }
   for (Prob& p : ctx->probs) {
     ProbState ps;
     std::memcpy(&ps, i, sizeof(ps));
