@@ -345,8 +345,9 @@ int mmp_philox(const unsigned int* ctr, const unsigned int* key, unsigned int* o
                void* stream);
 
 /* The normals the fine propagator uses for (tag, step j, slice n):
- * out[p] for p < count (device, double or float per `precision`).
- * Asynchronous on `stream`. */
+ * out[p] for p < count (device, double or float per `precision`, aligned
+ * to its element; count <= 2^34; tag < 256; n < 2^24, else
+ * MMP_ERR_INVALID_ARG).  Asynchronous on `stream`. */
 int mmp_normals(const mmp_problem_desc* desc, int tag, unsigned int j, unsigned int n,
                 long long count, void* out, void* stream);
 

@@ -1420,6 +1420,9 @@ int mmp_normals(const mmp_problem_desc* desc, int tag, unsigned int j, unsigned 
   if (desc == nullptr || out == nullptr || count < 0 || tag < 0 || tag > 255 || n >= (1u << 24))
     return MMP_ERR_INVALID_ARG;
   if (desc->precision != MMP_FP64 && desc->precision != MMP_MIXED) return MMP_ERR_INVALID_ARG;
+  // element-aligned output; particle quads are counted in 32 bits
+  if ((uintptr_t)out % (desc->precision == MMP_MIXED ? sizeof(float) : sizeof(double)) != 0) return MMP_ERR_INVALID_ARG;
+  if (count > (4LL << 32)) return MMP_ERR_INVALID_ARG;
   if (count == 0) return MMP_OK;
   MMP_CUDA(launch_normals(desc->precision, out, count, (uint32_t)tag, j, n, (uint32_t)(desc->seed & 0xffffffffull),
                           (uint32_t)(desc->seed >> 32), desc->problem_tag, (cudaStream_t)stream));

@@ -113,3 +113,15 @@ def test_plane_rotator_is_refused_by_the_library(mmplib):
     with pytest.raises(mmplib.MMPError) as e:
         mmplib.mmp_workspace_size([W.plane_rotator(P=1000)])
     assert e.value.code == -3
+
+
+def test_normals_arguments_checked_on_the_host(mmplib):
+    """mmp_normals refuses a misaligned output, an oversized count, a tag
+    past 8 bits and a slice past 24 bits before any launch."""
+    lib = mmplib.load()
+    d = mmplib.desc(W.config1())
+    assert lib.mmp_normals(C.byref(d), 0, 0, 0, 16, 4096 + 4, None) == -1   # FP64 needs 8-byte alignment
+    assert lib.mmp_normals(C.byref(d), 0, 0, 0, (4 << 32) + 1, 4096, None) == -1
+    assert lib.mmp_normals(C.byref(d), 256, 0, 0, 16, 4096, None) == -1
+    assert lib.mmp_normals(C.byref(d), 0, 0, 1 << 24, 16, 4096, None) == -1
+    assert lib.mmp_normals(C.byref(d), 0, 0, 0, 0, 4096, None) == 0        # nothing to do
