@@ -83,3 +83,25 @@ def test_models_change_the_iterates(orc):
     assert np.allclose(first[W.SIGMA3], first[W.CLOSURE], rtol=1e-12, atol=1e-14)
     assert not np.allclose(first[W.SIGMA2], first[W.CLOSURE], rtol=1e-9)
     assert not np.allclose(first[W.TAYLOR], first[W.CLOSURE], rtol=1e-9)
+
+
+def test_gbm_every_model_the_same_and_one_sweep_reaches_the_mc_level(orc):
+    """The modified geometric Brownian motion (Sec. 5.1) has drift and
+    diffusion linear in X and E[X], state- and mean-dependent noise
+    included, so every coarse model is the same moment ODE (Lemma 2.1) and
+    gives the same iterates; with that model one sweep brings the iterate to
+    the Monte Carlo level of the serial fine run (within two statistical
+    units, sqrt(V/P) for the mean and V sqrt(2/P) for the variance)."""
+    hists = {}
+    for model in MODELS:
+        p = W.gbm(P=2000, dt=1e-2, coarse_model=model, tol=0.0)
+        hists[model] = orc.parareal(p.scaled(max_iter=2))["hist"]
+    for model in MODELS[1:]:
+        assert np.allclose(hists[model], hists[W.CLOSURE], rtol=1e-12, atol=1e-14), model
+    p = W.gbm(P=2000, dt=1e-2, tol=0.0)
+    ser = orc.fine_serial(p)
+    M, V = ser["gmean"], ser["gvar"]
+    sm, sv = np.sqrt(V.max() / p.P), V.max() * np.sqrt(2.0 / p.P)
+    h = hists[W.CLOSURE][1]
+    assert np.max(np.abs(h[:, 0] - M)) < 2 * sm
+    assert np.max(np.abs(h[:, 1] - V)) < 2 * sv
