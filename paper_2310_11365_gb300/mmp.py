@@ -54,6 +54,7 @@ EXPORTED = [
 
 
 class MMPError(RuntimeError):
+    """A negative MMP_* return code (.code) with the call that returned it."""
     def __init__(self, code: int, where: str):
         name = ERRORS.get(code, str(code))
         msg = _lib.mmp_strerror(code).decode() if _lib is not None else name
@@ -65,6 +66,7 @@ class MMPError(RuntimeError):
 
 
 class ProblemDesc(C.Structure):
+    """ctypes mirror of mmp_problem_desc (field order and types as in include/mmp.h)."""
     _fields_ = [
         ("c3", C.c_double), ("c1", C.c_double), ("kappa", C.c_double), ("c0", C.c_double),
         ("B", C.c_double), ("BE", C.c_double), ("B0", C.c_double),
@@ -140,6 +142,7 @@ def _check(rc: int, where: str):
 
 
 def desc(p: workloads.Problem) -> ProblemDesc:
+    """The C descriptor of a problem record; refuses drift families the kernels do not run."""
     if p.family != workloads.POLY:
         # the library's kernels propagate the polynomial drift family only
         raise MMPError(-3, "desc")
@@ -166,14 +169,17 @@ def _stream_handle(stream) -> int:
 # ---- one Python function per C entry point --------------------------------
 
 def mmp_strerror(code: int) -> str:
+    """Name of a return code."""
     return load().mmp_strerror(code).decode()
 
 
 def mmp_version() -> int:
+    """C-ABI version of the loaded library (MMP_VERSION)."""
     return load().mmp_version()
 
 
 def mmp_workspace_size(problems) -> int:
+    """Bytes of device workspace a context over these problems needs."""
     arr = _descs(problems)
     n = C.c_size_t()
     _check(load().mmp_workspace_size(arr, len(problems), C.byref(n)), "mmp_workspace_size")
@@ -181,6 +187,7 @@ def mmp_workspace_size(problems) -> int:
 
 
 def mmp_create(problems, workspace_ptr: int, workspace_bytes: int, stream=None) -> C.c_void_p:
+    """A context over caller-owned device workspace (256-byte aligned); draws the initial ensembles."""
     arr = _descs(problems)
     ctx = C.c_void_p()
     _check(load().mmp_create(C.byref(ctx), arr, len(problems), C.c_void_p(workspace_ptr), workspace_bytes,
@@ -189,30 +196,36 @@ def mmp_create(problems, workspace_ptr: int, workspace_bytes: int, stream=None) 
 
 
 def mmp_destroy(ctx) -> None:
+    """Frees the context (a host object); the workspace stays the caller's."""
     _check(load().mmp_destroy(ctx), "mmp_destroy")
 
 
 def mmp_set_initial(ctx, prob: int, u0_ptr: int, from_host: bool) -> None:
+    """Replaces problem prob's initial ensemble by P values at u0_ptr (host or device)."""
     _check(load().mmp_set_initial(ctx, prob, C.c_void_p(u0_ptr), int(from_host)), "mmp_set_initial")
 
 
 def mmp_lift(ctx) -> None:
+    """Iteration k = 0: restriction of u0, sequential coarse sweep, lifting records."""
     _check(load().mmp_lift(ctx), "mmp_lift")
 
 
 def mmp_iterate(ctx, n_iter: int) -> bool:
+    """Up to n_iter fine + coarse sweeps (Eq. mM_parareal_other_k_NEW); True when every problem stopped."""
     done = C.c_int()
     _check(load().mmp_iterate(ctx, n_iter, C.byref(done)), "mmp_iterate")
     return bool(done.value)
 
 
 def mmp_run(ctx) -> int:
+    """Lift, then sweep until every problem stops; returns the largest sweep count."""
     k = C.c_int()
     _check(load().mmp_run(ctx, C.byref(k)), "mmp_run")
     return k.value
 
 
 def mmp_status(ctx, prob: int) -> dict:
+    """Sweeps done, converged, last change and device error code of problem prob."""
     s, c, e = C.c_int(), C.c_int(), C.c_int()
     ch = C.c_double()
     _check(load().mmp_status(ctx, prob, C.byref(s), C.byref(c), C.byref(ch), C.byref(e)), "mmp_status")
@@ -220,16 +233,19 @@ def mmp_status(ctx, prob: int) -> dict:
 
 
 def mmp_get_moments(ctx, prob: int, N: int) -> np.ndarray:
+    """Macro states rho_n, n = 0..N, as an [(N+1), MOMENT_STRIDE] array."""
     out = np.empty((N + 1) * MOMENT_STRIDE, np.float64)
     _check(load().mmp_get_moments(ctx, prob, out.ctypes.data_as(C.POINTER(C.c_double))), "mmp_get_moments")
     return out.reshape(N + 1, MOMENT_STRIDE)
 
 
 def mmp_get_particles(ctx, prob: int, n: int, dst_ptr: int, to_host: bool) -> None:
+    """Slice-end particles u_n (n = 0..N) of problem prob, copied to dst_ptr."""
     _check(load().mmp_get_particles(ctx, prob, n, C.c_void_p(dst_ptr), int(to_host)), "mmp_get_particles")
 
 
 def mmp_fine_serial(ctx, prob: int, n_end: int, parts_ptr: int | None = None) -> np.ndarray:
+    """Restriction records of the serial fine run u_0..u_{n_end} ([(n_end+1), STAT_STRIDE])."""
     out = np.empty((n_end + 1) * STAT_STRIDE, np.float64)
     _check(load().mmp_fine_serial(ctx, prob, n_end, out.ctypes.data_as(C.POINTER(C.c_double)),
                                   C.c_void_p(parts_ptr or 0)), "mmp_fine_serial")
@@ -237,6 +253,7 @@ def mmp_fine_serial(ctx, prob: int, n_end: int, parts_ptr: int | None = None) ->
 
 
 def mmp_fine(ctx, prob: int, n: int, u_in_ptr: int, u_out_ptr: int) -> np.ndarray:
+    """One fine propagation F_n of the ensemble at u_in_ptr into u_out_ptr; its restriction record."""
     out = np.empty(STAT_STRIDE, np.float64)
     _check(load().mmp_fine(ctx, prob, n, C.c_void_p(u_in_ptr), C.c_void_p(u_out_ptr),
                            out.ctypes.data_as(C.POINTER(C.c_double))), "mmp_fine")
@@ -244,6 +261,7 @@ def mmp_fine(ctx, prob: int, n: int, u_in_ptr: int, u_out_ptr: int) -> np.ndarra
 
 
 def mmp_get_plan(ctx, prob: int) -> dict:
+    """Launch shape of problem prob's fine kernel (quads per thread, CTAs per slice, ...)."""
     a, b, c, e = C.c_int(), C.c_int(), C.c_int(), C.c_int()
     _check(load().mmp_get_plan(ctx, prob, C.byref(a), C.byref(b), C.byref(c), C.byref(e)), "mmp_get_plan")
     return {"quads_per_thread": a.value, "ctas_per_slice": b.value, "max_concurrent_slices": c.value,
@@ -251,10 +269,12 @@ def mmp_get_plan(ctx, prob: int) -> dict:
 
 
 def mmp_set_timing(ctx, on: bool) -> None:
+    """Switches CUDA-event timing of every fine launch on or off."""
     _check(load().mmp_set_timing(ctx, int(on)), "mmp_set_timing")
 
 
 def mmp_timing(ctx, reset: bool = False) -> dict:
+    """Fine-kernel milliseconds, launches and particle-steps, other launches (since the last reset)."""
     ms, steps = C.c_double(), C.c_double()
     fl, ol = C.c_longlong(), C.c_longlong()
     _check(load().mmp_timing(ctx, int(reset), C.byref(ms), C.byref(fl), C.byref(steps), C.byref(ol)),
@@ -264,6 +284,7 @@ def mmp_timing(ctx, reset: bool = False) -> dict:
 
 
 def mmp_batch_info(ctx) -> dict:
+    """Whether the context batches its problems and replays its sweeps from a CUDA graph."""
     b, g = C.c_int(), C.c_int()
     _check(load().mmp_batch_info(ctx, C.byref(b), C.byref(g)), "mmp_batch_info")
     return {"batched": bool(b.value), "graph": bool(g.value)}
@@ -291,11 +312,13 @@ def mmp_autotune(p: workloads.Problem, candidates=None, probe_steps: int = 0, st
 
 
 def mmp_set_tuning(precision: str, p_lo: int, p_hi: int, quads_per_thread: int) -> None:
+    """Registers quads per thread for problems of a precision with p_lo <= P <= p_hi."""
     prec = MMP_MIXED if precision == "mixed" else MMP_FP64
     _check(load().mmp_set_tuning(prec, int(p_lo), int(p_hi), int(quads_per_thread)), "mmp_set_tuning")
 
 
 def mmp_set_batch_nq(precision: str, quads_per_thread: int) -> None:
+    """Cap on quads per thread of batched contexts of a precision created afterwards."""
     prec = MMP_MIXED if precision == "mixed" else MMP_FP64
     _check(load().mmp_set_batch_nq(prec, int(quads_per_thread)), "mmp_set_batch_nq")
 
@@ -310,6 +333,7 @@ def mmp_get_state(ctx) -> bytes:
 
 
 def mmp_set_state(ctx, blob: bytes) -> None:
+    """Restores a checkpoint taken by mmp_get_state into a context over the same problems."""
     buf = C.create_string_buffer(blob, len(blob))
     _check(load().mmp_set_state(ctx, buf), "mmp_set_state")
 
@@ -331,12 +355,14 @@ def mmp_set_params(ctx, prob: int, theta) -> None:
 
 
 def mmp_adjoint_workspace_size(ctx, prob: int, ckpt_every: int) -> int:
+    """Bytes of adjoint workspace for a checkpoint every ckpt_every fine steps."""
     n = C.c_size_t()
     _check(load().mmp_adjoint_workspace_size(ctx, prob, ckpt_every, C.byref(n)), "mmp_adjoint_workspace_size")
     return n.value
 
 
 def mmp_adjoint_forward(ctx, prob: int, ckpt_every: int, ws_ptr: int, ws_bytes: int, N: int) -> np.ndarray:
+    """Recording serial fine run; slice-end (M_n, V_n), n = 0..N, as an [(N+1), 2] array."""
     mom = np.empty(2 * (N + 1), np.float64)
     _check(load().mmp_adjoint_forward(ctx, prob, ckpt_every, C.c_void_p(ws_ptr), ws_bytes,
                                       mom.ctypes.data_as(C.POINTER(C.c_double))), "mmp_adjoint_forward")
@@ -344,6 +370,7 @@ def mmp_adjoint_forward(ctx, prob: int, ckpt_every: int, ws_ptr: int, ws_bytes: 
 
 
 def mmp_adjoint_backward(ctx, prob: int, gm, gv, ws_ptr: int, ws_bytes: int) -> np.ndarray:
+    """Gradient of sum gm M_n + gv V_n in (c3, c1, kappa, c0, B0, B, BE) after a forward run."""
     gma = np.ascontiguousarray(gm, dtype=np.float64)
     gva = np.ascontiguousarray(gv, dtype=np.float64)
     grad = np.empty(N_THETA, np.float64)
@@ -367,12 +394,14 @@ def mmp_adjoint(ctx, prob: int, m_tgt, v_tgt, ckpt_every: int, ws_ptr: int, ws_b
 
 
 def mmp_philox(ctr_ptr: int, key, out_ptr: int, n: int, stream=None) -> None:
+    """Philox-4x32-10 of n counters at ctr_ptr under key into out_ptr (device, 16-byte aligned)."""
     k = (C.c_uint * 2)(int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF)
     _check(load().mmp_philox(C.c_void_p(ctr_ptr), k, C.c_void_p(out_ptr), n,
                              C.c_void_p(_stream_handle(stream))), "mmp_philox")
 
 
 def mmp_normals(p: workloads.Problem, tag: int, j: int, n: int, count: int, out_ptr: int, stream=None) -> None:
+    """The normals the fine propagator draws for (tag, step j, slice n), count of them, into out_ptr."""
     dsc = desc(p)
     _check(load().mmp_normals(C.byref(dsc), tag, j, n, count, C.c_void_p(out_ptr),
                               C.c_void_p(_stream_handle(stream))), "mmp_normals")
