@@ -747,14 +747,60 @@ static int spd_solve(int n, const double* M, const double* b, double* x) {
   return 0;
 }
 
+/* The rates are non-negative (they are transition rates between regions),
+ * and a rate far above 1 / dT is indistinguishable from a faster one: a
+ * region left at rate omega keeps a share e^{-omega dT} of its mass over one
+ * slice, below 2e-9 once omega dT >= 20, so the slice-end fractions cannot
+ * tell such rates apart and the cost is flat there.  The fit is therefore
+ * the least-squares minimiser of rate_cost over the box
+ * 0 <= omega <= omega_max = 20 / dT, found by Levenberg-Marquardt on omega
+ * with the bounds kept by projection: in every iteration a rate is held when
+ * it sits at a bound and the cost would fall only if it crossed it (J^T r
+ * pointing out of the box); the other ("free") rates take the damped
+ * Gauss-Newton step (J^T J + mu I) d = J^T r, and the new point is the step
+ * clipped to the box.  The damping mu follows the gain
+ * ratio rho = (actual decrease) / (decrease predicted by the linear model):
+ * after a step with rho > 0 it is multiplied by max(1/3, 1 - (2 rho - 1)^3),
+ * after a failed one by nu, which doubles with every failure in a row
+ * (Madsen, Nielsen and Tingleff, "Methods for non-linear least squares
+ * problems", 2004, Sec. 3.2). */
+static int rate_free_step(int np, const double* om, double om_max, const double* JtJ, const double* g,
+                          double mu, double* step, double* pred) {
+  int fr_idx[12], nf = 0;
+  for (int p = 0; p < np; ++p) {
+    step[p] = 0.0;
+    const int held = (om[p] == 0.0 && !(g[p] > 0.0)) || (om[p] == om_max && !(g[p] < 0.0));
+    if (!held) fr_idx[nf++] = p;
+  }
+  *pred = 0.0;
+  if (nf == 0) return 0;
+  double M[144], b[12], x[12];
+  for (int a = 0; a < nf; ++a) {
+    for (int c = 0; c < nf; ++c) M[a * nf + c] = JtJ[fr_idx[a] * np + fr_idx[c]];
+    M[a * nf + a] = M[a * nf + a] + mu;
+    b[a] = g[fr_idx[a]];
+  }
+  if (spd_solve(nf, M, b, x) != 0) return -1;
+  /* predicted decrease of the cost: d^T (mu d + g) over the free rates */
+  double s = 0.0;
+  for (int a = 0; a < nf; ++a) {
+    step[fr_idx[a]] = x[a];
+    s += x[a] * (mu * x[a] + b[a]);
+  }
+  *pred = s;
+  return nf;
+}
+
 int orc_rate_fit(int I, int k, const double* fr, double dT, double* om) {
   const int np = I * (I - 1);
   if (I < 2 || I > 4 || k < I) return -1;
-  double th[12], nth[12], nw[12];
   /* initial rates: the one-step regression P_n ~ Phi0 P_{n-1} (least squares
    * over n = 1..k), Phi0 ~ I + A dT, so omega_ij ~ Phi0_ji / dT, floored at
-   * a small positive rate; equal rates 1 / (I k dT) if the regression is
-   * singular */
+   * a small positive rate and capped at 1 / dT (a start among much faster
+   * rates lies where the cost is flat and leaves the iteration nothing to
+   * follow); equal rates 1 / (I k dT) if the regression is singular */
+  const double floor_rate = 1e-3 / ((double)k * dT);
+  const double om_max = 20.0 / dT;
   {
     double Sxx[16] = {0.0}, Syx[16] = {0.0};
     for (int n = 1; n <= k; ++n)
@@ -763,7 +809,6 @@ int orc_rate_fit(int I, int k, const double* fr, double dT, double* om) {
           Sxx[a * I + b] += fr[(n - 1) * I + a] * fr[(n - 1) * I + b];
           Syx[a * I + b] += fr[n * I + a] * fr[(n - 1) * I + b];
         }
-    const double floor_rate = 1e-3 / ((double)k * dT);
     int ok = 1;
     double Phi0[16];
     for (int a = 0; a < I && ok; ++a) {
@@ -780,73 +825,50 @@ int orc_rate_fit(int I, int k, const double* fr, double dT, double* om) {
       for (int j = 0; j < I; ++j) {
         if (j == i) continue;
         const double w = ok ? Phi0[j * I + i] / dT : 1.0 / ((double)I * (double)k * dT);
-        th[i * (I - 1) + (j < i ? j : j - 1)] = sqrt(isfinite(w) && w > floor_rate ? w : floor_rate);
+        om[i * (I - 1) + (j < i ? j : j - 1)] = isfinite(w) && w > floor_rate ? fmin(w, 1.0 / dT) : floor_rate;
       }
   }
-  const double th_floor = sqrt(1e-3 / ((double)k * dT));
-  for (int p = 0; p < np; ++p) om[p] = th[p] * th[p];
-  double lambda = 1e-3;
+  double JtJ[144], g[12], st[12], nw[12];
   double cost = rate_cost(I, k, fr, dT, om);
-  double JtJ[144], g[12], M[144], st[12];
-  /* normal equations in theta: J_theta = J_omega diag(2 theta) */
-  for (int it = 0; it < 100; ++it) {
-    rate_normal(I, k, fr, dT, om, JtJ, g);
-    for (int p = 0; p < np; ++p) {
-      g[p] *= 2.0 * th[p];
-      for (int q = 0; q < np; ++q) JtJ[p * np + q] *= (2.0 * th[p]) * (2.0 * th[q]);
+  rate_normal(I, k, fr, dT, om, JtJ, g);
+  double mu = 0.0, nu = 2.0;
+  for (int p = 0; p < np; ++p) mu = fmax(mu, JtJ[p * np + p]);
+  mu = 1e-3 * mu;
+  int converged = cost == 0.0;
+  for (int it = 0; it < ORC_RATE_FIT_MAX_ITER && !converged; ++it) {
+    double pred;
+    const int nf = rate_free_step(np, om, om_max, JtJ, g, mu, st, &pred);
+    if (nf == 0) { /* every rate held at a bound: a stationary point */
+      converged = 1;
+      break;
     }
-    for (int r = 0; r < np * np; ++r) M[r] = JtJ[r];
-    for (int p = 0; p < np; ++p) M[p * np + p] = JtJ[p * np + p] * (1.0 + lambda);
-    if (spd_solve(np, M, g, st) != 0) {
-      lambda *= 10.0;
-      if (lambda > 1e12) break;
-      continue;
+    double ncost = 0.0;
+    if (nf > 0) {
+      for (int p = 0; p < np; ++p) nw[p] = fmin(fmax(om[p] + st[p], 0.0), om_max);
+      ncost = rate_cost(I, k, fr, dT, nw);
     }
-    for (int p = 0; p < np; ++p) {
-      /* a step changes theta by at most twice its size (or the floor's) */
-      const double cap = 2.0 * fmax(fabs(th[p]), th_floor);
-      nth[p] = th[p] + fmax(-cap, fmin(cap, st[p]));
-      nw[p] = nth[p] * nth[p];
-    }
-    const double ncost = rate_cost(I, k, fr, dT, nw);
-    if (isfinite(ncost) && ncost < cost) {
-      double rel = 0.0;
-      for (int p = 0; p < np; ++p) {
-        th[p] = nth[p];
-        om[p] = nw[p];
-        rel = fmax(rel, fabs(st[p]) / (fabs(th[p]) + 1e-300));
-      }
+    if (nf > 0 && pred > 0.0 && isfinite(ncost) && ncost < cost) {
+      const double rho = (cost - ncost) / pred;
+      const double t = 2.0 * rho - 1.0;
+      for (int p = 0; p < np; ++p) om[p] = nw[p];
       cost = ncost;
-      lambda /= 10.0;
-      if (rel < 1e-15) break;
+      rate_normal(I, k, fr, dT, om, JtJ, g);
+      mu = mu * fmax(1.0 / 3.0, 1.0 - t * t * t);
+      nu = 2.0;
+      if (pred < 1e-15 * cost || cost == 0.0) converged = 1; /* the model promises nothing more */
     } else {
-      lambda *= 10.0;
-      if (lambda > 1e12) break;
+      if (nf > 0 && !(pred > 0.0)) { /* no descent left on the free rates */
+        converged = 1;
+        break;
+      }
+      mu = mu * nu;
+      nu = 2.0 * nu;
+      if (nu > 1e18) break;
     }
-  }
-  /* Gauss-Newton refinement, each step kept only if the cost does not rise */
-  for (int it = 0; it < 3; ++it) {
-    rate_normal(I, k, fr, dT, om, JtJ, g);
-    for (int p = 0; p < np; ++p) {
-      g[p] *= 2.0 * th[p];
-      for (int q = 0; q < np; ++q) JtJ[p * np + q] *= (2.0 * th[p]) * (2.0 * th[q]);
-    }
-    if (spd_solve(np, JtJ, g, st) != 0) break;
-    for (int p = 0; p < np; ++p) {
-      nth[p] = th[p] + st[p];
-      nw[p] = nth[p] * nth[p];
-    }
-    const double ncost = rate_cost(I, k, fr, dT, nw);
-    if (!(isfinite(ncost) && ncost <= cost)) break;
-    for (int p = 0; p < np; ++p) {
-      th[p] = nth[p];
-      om[p] = nw[p];
-    }
-    cost = ncost;
   }
   for (int p = 0; p < np; ++p)
     if (!isfinite(om[p]) || !(om[p] >= 0.0)) return -2;
-  return 0;
+  return converged ? 0 : 1;
 }
 
 void orc_rate_propagate(int I, const double* om, double dT, const double* p_in, int m, double* p_out) {
@@ -978,7 +1000,7 @@ int orc_parareal(const orc_problem* pr, const double* u0_in, double* hist, orc_m
       double om[12];
       for (int n = 0; n <= k; ++n)
         for (int i = 0; i < I; ++i) frk[n * I + i] = fr[n * ORC_MAX_REGIONS + i];
-      if (orc_rate_fit(I, k, frk, dT, om) == 0) {
+      if (orc_rate_fit(I, k, frk, dT, om) >= 0) {
         for (int n = k + 1; n <= N; ++n)
           orc_rate_propagate(I, om, dT, fr + (size_t)(n - 1) * ORC_MAX_REGIONS, 1, fr + (size_t)n * ORC_MAX_REGIONS);
       }

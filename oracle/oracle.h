@@ -163,8 +163,14 @@ void orc_rate_generator(int I, const double* omega, double* A);
  * derivative of that computation in the direction dX. */
 void orc_expm(int n, const double* X, const double* dX, double* E, double* dE);
 /* Fit omega to the fractions fr[n I + i] at t_n = n dT, n = 0..k (fr at
- * t_0 fixed) by Levenberg-Marquardt on theta, omega = theta^2; returns 0 if the fit is
- * usable (every rate finite), -1 if k < I, -2 otherwise. */
+ * t_0 fixed): a least-squares minimiser over the box 0 <= omega <= 20 / dT,
+ * by Levenberg-Marquardt on omega with the bounds kept by projection, from
+ * the one-step regression (see oracle.c).  Returns 0 when the iteration
+ * converged, 1 when it stopped after ORC_RATE_FIT_MAX_ITER iterations or
+ * could not reduce the damping further (the rates are then a point of lower
+ * cost than the start, still used), -1 if k < I, -2 if a rate is not
+ * finite. */
+#define ORC_RATE_FIT_MAX_ITER 2000
 int orc_rate_fit(int I, int k, const double* fr, double dT, double* omega);
 /* p_out = expm(A m dT) p_in as m steps of Phi = expm(A dT). */
 void orc_rate_propagate(int I, const double* omega, double dT, const double* p_in, int m, double* p_out);
