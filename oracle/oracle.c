@@ -115,8 +115,10 @@ double orc_fine_h(const orc_problem* pr) {
   return (pr->T / pr->N) / orc_fine_steps(pr);
 }
 
-static double drift(const orc_problem* pr, double x, double m) {
-  return -pr->c3 * x * x * x + pr->c1 * x + pr->kappa * m + pr->c0;
+/* a(x, m, s) with s = E[X^2]; the term -q2 x s is the second-moment
+ * coupling of the polynomial-drift example (App. C), zero elsewhere */
+static double drift(const orc_problem* pr, double x, double m, double s) {
+  return -pr->c3 * x * x * x + (pr->c1 - pr->q2 * s) * x + pr->kappa * m + pr->c0;
 }
 
 static double diffusion(const orc_problem* pr, double x, double m) {
@@ -126,6 +128,13 @@ static double diffusion(const orc_problem* pr, double x, double m) {
 static double ensemble_mean(const double* u, long long P) {
   double s = 0.0;
   for (long long p = 0; p < P; ++p) s += u[p];
+  return s / (double)P;
+}
+
+/* E[X^2] of the ensemble (the second raw moment) */
+static double ensemble_second_moment(const double* u, long long P) {
+  double s = 0.0;
+  for (long long p = 0; p < P; ++p) s += u[p] * u[p];
   return s / (double)P;
 }
 
@@ -160,6 +169,7 @@ void orc_fine(const orc_problem* pr, int n, const double* u_in, double* u_out, d
     if (means) means[j] = m;
     double S = 0.0, C = 0.0;
     if (rotator) ensemble_sin_cos(x, P, &S, &C);
+    const double s2 = pr->q2 != 0.0 ? ensemble_second_moment(x, P) : 0.0;
     for (long long q = 0; 4 * q < P; ++q) {
       double z[4];
       normals4(pr, 0, (uint32_t)j, (uint32_t)n, (uint32_t)q, z);
@@ -168,7 +178,7 @@ void orc_fine(const orc_problem* pr, int n, const double* u_in, double* u_out, d
         if (rotator) {
           y[p] = orc_wrap(x[p] + rotator_drift(pr, x[p], S, C) * h + pr->B0 * sqrt_h * z[w]);
         } else {
-          y[p] = x[p] + drift(pr, x[p], m) * h + diffusion(pr, x[p], m) * sqrt_h * z[w];
+          y[p] = x[p] + drift(pr, x[p], m, s2) * h + diffusion(pr, x[p], m) * sqrt_h * z[w];
         }
       }
     }
@@ -384,19 +394,28 @@ void orc_coarse_rhs(const orc_problem* pr, const orc_macro* r, double* dm, doubl
     return;
   }
   const int I = pr->n_regions < 2 ? 1 : pr->n_regions;
-  double M = 0.0;
+  /* the mean field: the mixture mean M, and (second-moment coupling only)
+   * the mixture second moment S2 = sum_i P_i (M_i^2 + Sigma_i) */
+  double M = 0.0, S2 = 0.0;
   if (I == 1) {
     M = r->mean[0];
+    S2 = r->mean[0] * r->mean[0] + r->var[0];
   } else {
-    for (int i = 0; i < I; ++i) M += r->frac[i] * r->mean[i];
+    for (int i = 0; i < I; ++i) {
+      M += r->frac[i] * r->mean[i];
+      S2 += r->frac[i] * (r->mean[i] * r->mean[i] + r->var[i]);
+    }
   }
+  if (pr->q2 == 0.0) S2 = 0.0;
+  /* with the coupling the drift is linear in x with coefficient c1 - q2 S2 */
+  const double c1e = pr->c1 - pr->q2 * S2;
   for (int i = 0; i < I; ++i) {
     double m = r->mean[i], v = r->var[i];
     if (pr->coarse_model == ORC_COARSE_TAYLOR || pr->coarse_model == ORC_COARSE_TAYLOR1) {
-      double ax = -3.0 * pr->c3 * m * m + pr->c1;
+      double ax = -3.0 * pr->c3 * m * m + c1e;
       double axx = -6.0 * pr->c3 * m;
       double b = diffusion(pr, m, M);
-      dm[i] = drift(pr, m, M) + (pr->coarse_model == ORC_COARSE_TAYLOR ? 0.5 * axx * v : 0.0);
+      dm[i] = drift(pr, m, M, S2) + (pr->coarse_model == ORC_COARSE_TAYLOR ? 0.5 * axx * v : 0.0);
       dv[i] = (2.0 * ax + pr->B * pr->B) * v + b * b;
     } else if (pr->coarse_model == ORC_COARSE_SIGMA2 || pr->coarse_model == ORC_COARSE_SIGMA3) {
       double xs[3], ws[3];
@@ -404,7 +423,7 @@ void orc_coarse_rhs(const orc_problem* pr, const orc_macro* r, double* dm, doubl
       sigma_points(pr->coarse_model, m, v, xs, ws, &k);
       double ea = 0.0, exa = 0.0, eb2 = 0.0;
       for (int s = 0; s < k; ++s) {
-        double a = drift(pr, xs[s], M);
+        double a = drift(pr, xs[s], M, S2);
         double b = diffusion(pr, xs[s], M);
         ea += ws[s] * a;
         exa += ws[s] * (xs[s] - m) * a;
@@ -416,8 +435,8 @@ void orc_coarse_rhs(const orc_problem* pr, const orc_macro* r, double* dm, doubl
       double ex3 = m * m * m + 3.0 * m * v;
       double cov3 = 3.0 * v * (m * m + v);
       double eb = pr->B * m + pr->BE * M + pr->B0;
-      dm[i] = -pr->c3 * ex3 + pr->c1 * m + pr->kappa * M + pr->c0;
-      dv[i] = 2.0 * (-pr->c3 * cov3 + pr->c1 * v) + pr->B * pr->B * v + eb * eb;
+      dm[i] = -pr->c3 * ex3 + c1e * m + pr->kappa * M + pr->c0;
+      dv[i] = 2.0 * (-pr->c3 * cov3 + c1e * v) + pr->B * pr->B * v + eb * eb;
     }
   }
 }
@@ -1150,7 +1169,7 @@ void orc_fine_serial(const orc_problem* pr, const double* u0_in, orc_stats* stat
  * ---------------------------------------------------------------------- */
 int orc_adjoint(const orc_problem* pr, const double* u0_in, const double* gm, const double* gv,
                 double grad[ORC_N_THETA], double* moments) {
-  if (pr->family == ORC_FAMILY_ROTATOR) return -1;
+  if (pr->family == ORC_FAMILY_ROTATOR || pr->q2 != 0.0) return -1;
   const long long P = pr->P;
   const int N = pr->N;
   const int nf = orc_fine_steps(pr);
@@ -1172,7 +1191,7 @@ int orc_adjoint(const orc_problem* pr, const double* u0_in, const double* gm, co
     const int n = (int)(j / nf), js = (int)(j % nf);
     for (long long p = 0; p < P; ++p) {
       double xi = orc_normal(pr, 0, (uint32_t)js, (uint32_t)n, p);
-      y[p] = x[p] + drift(pr, x[p], m[j]) * h + diffusion(pr, x[p], m[j]) * sqrt_h * xi;
+      y[p] = x[p] + drift(pr, x[p], m[j], 0.0) * h + diffusion(pr, x[p], m[j]) * sqrt_h * xi;
     }
   }
   m[J] = ensemble_mean(X + (size_t)J * P, P);

@@ -24,7 +24,12 @@
  *   diffusion  b(x, m) = B x + BE m + B0
  * where m = E[X] is the ensemble mean.  The linear McKean-Vlasov SDE of
  * Lemma 2.1 is c3 = 0; the cubic and double-well drifts of Sec. 5.3 are
- * c3 > 0 with additive noise (B = BE = 0).
+ * c3 > 0 with additive noise (B = BE = 0).  One more term, -q2 x E[X^2]
+ * (q2 = 0 otherwise), couples the drift to the ensemble's second moment:
+ * the polynomial-drift example of App. C, dX = (alpha X + E[X] - X E[X^2]) dt
+ * + X dW, is c1 = alpha, kappa = 1, q2 = 1, B = 1.  In every coarse model the
+ * term acts as the linear coefficient c1 - q2 S with S = V + M^2 of the
+ * law (the mixture's with several regions).  The adjoint does not take it.
  *
  * A second family, the plane rotator of Sec. 5 (Example "Unimodal plane
  * rotator", Eq. SDE_plane_rotator), has the drift
@@ -81,6 +86,7 @@ typedef struct {
   double threshold2, threshold3;  /* t_2, t_3 (n_regions 3, 4): D_2 = {t_2 <= x (< t_3)}, D_3 = {x >= t_3} */
   int family;                 /* ORC_FAMILY_POLY / ORC_FAMILY_ROTATOR */
   double K, g;                /* plane rotator: coupling K, pinning g (c3..c0, B, BE unused) */
+  double q2;                  /* second-moment coupling: the drift gets -q2 x E[X^2] (App. C) */
 } orc_problem;
 
 /* Coarse moment models (Sec. 2): the Gaussian closure (expectations of the

@@ -47,7 +47,7 @@ class OrcProblem(C.Structure):
         ("variant", C.c_int), ("seed", C.c_uint64), ("problem_tag", C.c_uint32),
         ("tol", C.c_double), ("max_iter", C.c_int), ("coarse_model", C.c_int),
         ("threshold2", C.c_double), ("threshold3", C.c_double),
-        ("family", C.c_int), ("K", C.c_double), ("g", C.c_double),
+        ("family", C.c_int), ("K", C.c_double), ("g", C.c_double), ("q2", C.c_double),
     ]
 
 
@@ -139,7 +139,7 @@ def problem(p) -> OrcProblem:
     return OrcProblem(
         p.c3, p.c1, p.kappa, p.c0, p.B, p.BE, p.B0, p.m0, p.s0, p.T, p.N, p.dt, p.P,
         p.coarse_h, p.n_regions, p.threshold, p.variant, p.seed, p.problem_tag, p.tol, max_iter,
-        p.coarse_model, p.threshold2, p.threshold3, p.family, p.K, p.g,
+        p.coarse_model, p.threshold2, p.threshold3, p.family, p.K, p.g, p.q2,
     )
 
 

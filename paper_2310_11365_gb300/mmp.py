@@ -143,8 +143,9 @@ def _check(rc: int, where: str):
 
 def desc(p: workloads.Problem) -> ProblemDesc:
     """The C descriptor of a problem record; refuses drift families the kernels do not run."""
-    if p.family != workloads.POLY:
-        # the library's kernels propagate the polynomial drift family only
+    if p.family != workloads.POLY or p.q2 != 0.0:
+        # the library's kernels propagate the polynomial drift family without
+        # the second-moment coupling only
         raise MMPError(-3, "desc")
     prec = MMP_MIXED if p.precision == "mixed" else MMP_FP64
     return ProblemDesc(p.c3, p.c1, p.kappa, p.c0, p.B, p.BE, p.B0, p.m0, p.s0, p.T, p.N, p.dt, p.P,

@@ -69,6 +69,7 @@ class Problem:
     family: int = POLY         # POLY (the polynomial drift above) or ROTATOR
     K: float = 0.0             # plane rotator: coupling K and pinning g
     g: float = 0.0
+    q2: float = 0.0            # second-moment coupling: the drift gets -q2 x E[X^2]
 
     def scaled(self, **kw) -> "Problem":
         return replace(copy.copy(self), **kw)
@@ -111,6 +112,17 @@ def plane_rotator(K: float = 1.0, kT: float = 0.25, g: float = 1.0, **kw) -> Pro
     p = Problem(family=ROTATOR, K=K, g=g, B0=float(np.sqrt(2.0 * kT)), m0=np.pi / 4,
                 s0=float(np.sqrt(3.0 * np.pi / 4)), T=10.0, N=10, dt=1e-3, P=100_000, coarse_h=0.25,
                 seed=SEED_BASE + 7, tol=1e-6, precision="fp64")
+    return p.scaled(**kw) if kw else p
+
+
+def polynomial_drift(alpha: float = -0.5, **kw) -> Problem:
+    """The polynomial-drift example of App. C (after Son Doan et al.):
+    dX = (alpha X + E[X] - X E[X^2]) dt + X dW, X(0) = 1, whose Taylor
+    moment model is the exact moment system.  alpha is not given there
+    (alpha = -1/2 here, as in the paper's linear example); T = 1, N = 10,
+    dt = 1e-3 and P = 1e5 are chosen here."""
+    p = Problem(c1=alpha, kappa=1.0, q2=1.0, B=1.0, m0=1.0, s0=0.0, T=1.0, N=10, dt=1e-3, P=100_000,
+                coarse_h=0.25, coarse_model=TAYLOR, seed=SEED_BASE + 8, tol=1e-8, precision="fp64")
     return p.scaled(**kw) if kw else p
 
 
