@@ -300,20 +300,36 @@ __device__ bool lsq_fit(const DriverArgs& a, int npts, double p0, double& alpha,
 // Learning with I >= 3 regions: the rate model of the fractions (Sec. 3.6,
 // Eq. generalised_model_multimodal_PFs), dP/dt = A P with rates
 // omega_ij >= 0 from D_i to D_j (A_ji = omega_ij, A_ii = -sum_j omega_ij),
-// P(t_{n+1}) = Phi P(t_n), Phi = expm(A dT).  Fitted by Levenberg-Marquardt
-// on theta with omega = theta^2 to the exact fractions of t_0..t_k (k >= I):
-// start from the one-step regression P_n ~ Phi0 P_{n-1} (omega_ij ~
-// Phi0_ji / dT, floored at 1e-3 / (k dT)); the Jacobian is the derivative
-// of the computed expm (degree-16 Taylor polynomial after scaling to norm
-// <= 1/2, then squarings) in each rate's direction; damping 1e-3 scaled by
-// diag(J^T J), /10 on success, x10 on failure, at most 100 iterations, each
-// step of theta capped at twice max(|theta|, sqrt(floor)), stop on a
-// relative step below 1e-15 or damping above 1e12; then up to three
-// Gauss-Newton steps kept only if the cost does not rise.  One lane runs
-// the fit in IEEE arithmetic and sqrt only, step for step in a fixed order,
-// so that it is reproducible bit for bit.
+// P(t_{n+1}) = Phi P(t_n), Phi = expm(A dT), fitted by least squares to the
+// exact fractions of t_0..t_k (k >= I) over the box 0 <= omega <= 20 / dT
+// (non-negative rates; beyond omega dT = 20 a region keeps < 2e-9 of its
+// mass over a slice, so the slice-end fractions cannot tell faster rates
+// apart).  Levenberg-Marquardt on omega with the bounds kept by projection:
+// a rate at a bound whose gradient points out of the box is held, the
+// others solve (J^T J + mu I) d = J^T r, the new point is the step clipped
+// to the box; mu starts at 1e-3 max diag(J^T J) and follows the gain ratio
+// rho of actual to predicted decrease (x max(1/3, 1 - (2 rho - 1)^3) after
+// a success, x nu after a failure, nu doubling with every failure in a row;
+// Madsen, Nielsen and Tingleff 2004, Sec. 3.2).  Converged when the
+// predicted decrease is below 1e-15 of the cost, no rate is free or no
+// descent is left; otherwise it stops after kRateFitMaxIter iterations or
+// 60 failures in a row (the rates, of lower cost than the start, are still
+// used).  Start: the one-step regression P_n ~ Phi0 P_{n-1}, omega_ij ~
+// Phi0_ji / dT, floored at 1e-3 / (k dT) and capped at 1 / dT.  The
+// Jacobian is the derivative of the computed expm (degree-16 Taylor
+// polynomial after scaling to norm <= 1/2, then squarings) in each rate's
+// direction.
+//
+// The whole warp runs the fit: lane p computes the directional derivative
+// of expm in the direction of rate p, the derivative S_p of every modelled
+// fraction, J^T r at p and row p of J^T J, each accumulated over (n, i) in
+// the same order as a single pass would; lane 0 runs the sequential parts
+// (costs, the damped solve, the decisions).  Everything is IEEE arithmetic
+// and sqrt on working arrays in shared memory, in a fixed order, so the fit
+// is reproducible bit for bit.
 // ---------------------------------------------------------------------------
 constexpr int kMaxRates = kMaxRegions * (kMaxRegions - 1);
+constexpr int kRateFitMaxIter = 2000;
 // sweep staging: slices per chunk, doubles per slice (per region count, mean,
 // variance, min, max; the coarse cache; the old global M, V; the fractions)
 constexpr int kDrvChunk = 64;
@@ -323,24 +339,25 @@ constexpr int kDrvRow = 8 * kMaxRegions + 2;
 constexpr int kOutAcc = 0, kOutAv = kMaxRegions, kOutNx = 3 * kMaxRegions;
 constexpr int kDrvOut = 6 * kMaxRegions;
 
-// The fit's working arrays live in the problem's scratch block of device
-// memory (DriverArgs::fit, kFitScratch doubles), at fixed offsets, one
-// region per function so that no callee overwrites a caller's live data.
-// (With these arrays on the thread's stack, about 7 KB, some builds of the
-// driver kernels computed different fits from the same inputs; in global
-// memory every build reproduces the oracle's fit bit for bit.)
-enum FitOffsets : int {
-  kFitTh = 0, kFitNth = 12, kFitNw = 24, kFitJtJ = 36, kFitG = 180, kFitM = 192, kFitSt = 336,   // rate_fit
-  kFitSxx = 348, kFitSyx = 364, kFitPhi0 = 380, kFitRhs = 396, kFitX = 400,                     // regression
-  kFitL = 404, kFitY = 548,                                                                     // spd_solve
-  kFitNA = 560, kFitNPhi = 576, kFitDPhi = 592, kFitE = 784, kFitDA = 796, kFitP = 812,        // rate_normal
-  kFitQ = 816, kFitS = 820, kFitS2 = 868, kFitS3 = 872,
-  kFitCPhi = 880, kFitCp = 896, kFitCq = 900,                                                   // rate_cost
-  kFitEx = 904,                                                                                 // expm_dir: 7 x 16
-  kFitGA = 1016,                                                                                // rate_phi
-  kFitEnd = 1032
+// Working arrays of an expm with its directional derivative: Y, dY, T, dT,
+// W, dW, U (16 doubles each); the results are left in T and dT.
+constexpr int kExpmWork = 7 * 16;
+// Per-rate block: the expm work, then A, dA, the unit vector e, P, Q, S2, S3.
+constexpr int kFitLane = kExpmWork + 16 + 16 + kMaxRates + 16;
+
+struct FitShared {
+  double lane[kMaxRates][kFitLane];
+  double cw[kExpmWork + 16];  // lane 0's expm without derivative, then A
+  double S[kMaxRates][4];     // S_p at the current slice end
+  double JtJ[kMaxRates * kMaxRates];
+  double g[kMaxRates];
+  double M[kMaxRates * kMaxRates], L[kMaxRates * kMaxRates];
+  double y[kMaxRates], x[kMaxRates], b[kMaxRates];
+  double st[kMaxRates], nw[kMaxRates], om[kMaxRates];
+  double cp[4], cq[4];
+  double Sxx[16], Syx[16], Phi0[16], rhs[4], xr[4];
+  int fidx[kMaxRates];
 };
-static_assert(kFitEnd <= kFitScratch, "fit scratch");
 
 __device__ double frac_at(const DriverArgs& a, int n, int i) {
   const double* st = n == 0 ? a.stats_u0 : a.stats + (size_t)(n - 1) * kStat;
@@ -377,16 +394,17 @@ __device__ void mat_vec(int n, const double* M, const double* x, double* y) {
   }
 }
 
-// E = expm(X) (n <= 4) and, if dX is not null, dE = its derivative in the
-// direction dX, through the same scaling, Horner and squaring steps.
-__device__ void expm_dir(double* ws, int n, const double* X, const double* dX, double* E, double* dE) {
-  double* Y = ws + kFitEx;
-  double* dY = Y + 16;
-  double* T = Y + 32;
-  double* dT = Y + 48;
-  double* W = Y + 64;
-  double* dW = Y + 80;
-  double* U = Y + 96;
+// expm(X) (n <= 4) into w + 32 and, if dX is not null, its derivative in
+// the direction dX into w + 48, through the same scaling, Horner and
+// squaring steps.
+__device__ void expm_work(double* w, int n, const double* X, const double* dX) {
+  double* Y = w;
+  double* dY = w + 16;
+  double* T = w + 32;
+  double* dT = w + 48;
+  double* W = w + 64;
+  double* dW = w + 80;
+  double* U = w + 96;
   double norm = 0.0;
   for (int j = 0; j < n; ++j) {
     double c = 0.0;
@@ -425,24 +443,22 @@ __device__ void expm_dir(double* ws, int n, const double* X, const double* dX, d
     mat_mul(n, T, T, W);
     for (int r = 0; r < n * n; ++r) T[r] = W[r];
   }
-  for (int r = 0; r < n * n; ++r) {
-    E[r] = T[r];
-    if (dE) dE[r] = dT[r];
-  }
 }
 
-__device__ void rate_phi(double* ws, int I, const double* om, double dT, double* Phi) {
-  double* A = ws + kFitGA;
+// Phi = expm(A(omega) dT) into w + 32 (w: kExpmWork + 16 doubles).
+__device__ const double* rate_phi(double* w, int I, const double* om, double dT) {
+  double* A = w + kExpmWork;
   rate_generator(I, om, A);
   for (int r = 0; r < I * I; ++r) A[r] *= dT;
-  expm_dir(ws, I, A, nullptr, Phi, nullptr);
+  expm_work(w, I, A, nullptr);
+  return w + 32;
 }
 
-__device__ double rate_cost(const DriverArgs& a, double* ws, int I, int k, const double* om) {
-  double* Phi = ws + kFitCPhi;
-  double* p = ws + kFitCp;
-  double* q = ws + kFitCq;
-  rate_phi(ws, I, om, a.dT, Phi);
+// One lane: the cost sum_n sum_i (fr_{n,i} - (Phi^n P_0)_i)^2 at omega.
+__device__ double rate_cost(const DriverArgs& a, FitShared& F, int I, int k, const double* om) {
+  const double* Phi = rate_phi(F.cw, I, om, a.dT);
+  double* p = F.cp;
+  double* q = F.cq;
   for (int i = 0; i < I; ++i) p[i] = frac_at(a, 0, i);
   double s = 0.0;
   for (int n = 1; n <= k; ++n) {
@@ -456,188 +472,199 @@ __device__ double rate_cost(const DriverArgs& a, double* ws, int I, int k, const
   return s;
 }
 
-// J^T J and J^T r at omega (J = d model / d omega, r = data - model)
-__device__ void rate_normal(const DriverArgs& a, double* ws, int I, int k, const double* om, double* JtJ,
-                            double* g) {
+// Whole warp: J^T J (F.JtJ) and J^T r (F.g) at omega = F.om, with
+// J = d model / d omega and r = data - model.  Lane p < I (I - 1) owns rate p.
+__device__ void rate_normal_warp(const DriverArgs& a, FitShared& F, int I, int k) {
   const int np = I * (I - 1);
-  double* A = ws + kFitNA;
-  double* Phi = ws + kFitNPhi;
-  double* dPhi = ws + kFitDPhi;  // [np][16]
-  double* e = ws + kFitE;
-  double* dA = ws + kFitDA;
-  double* P = ws + kFitP;
-  double* Q = ws + kFitQ;
-  double* S = ws + kFitS;        // [np][4]
-  double* S2 = ws + kFitS2;
-  double* S3 = ws + kFitS3;
-  rate_generator(I, om, A);
-  for (int r = 0; r < I * I; ++r) A[r] *= a.dT;
-  for (int p = 0; p < np; ++p) {
+  const int p = threadIdx.x & 31;
+  const bool own = p < np;
+  double* w = F.lane[own ? p : 0];
+  double* A = w + kExpmWork;
+  double* dA = A + 16;
+  double* e = dA + 16;
+  double* P = e + kMaxRates;
+  double* Q = P + 4;
+  double* S2 = Q + 4;
+  double* S3 = S2 + 4;
+  const double* Phi = w + 32;
+  const double* dPhi = w + 48;
+  __syncwarp();
+  if (own) {
+    rate_generator(I, F.om, A);
+    for (int r = 0; r < I * I; ++r) A[r] *= a.dT;
     for (int q = 0; q < kMaxRates; ++q) e[q] = 0.0;
     e[p] = 1.0;
     rate_generator(I, e, dA);
     for (int r = 0; r < I * I; ++r) dA[r] *= a.dT;
-    expm_dir(ws, I, A, dA, Phi, dPhi + 16 * p);
-  }
-  for (int r = 0; r < np * np; ++r) JtJ[r] = 0.0;
-  for (int p = 0; p < np; ++p) g[p] = 0.0;
-  for (int i = 0; i < I; ++i) P[i] = frac_at(a, 0, i);
-  for (int p = 0; p < np; ++p)
-    for (int i = 0; i < I; ++i) S[4 * p + i] = 0.0;
-  for (int n = 1; n <= k; ++n) {
-    for (int p = 0; p < np; ++p) {
-      mat_vec(I, dPhi + 16 * p, P, S2);
-      mat_vec(I, Phi, S + 4 * p, S3);
-      for (int i = 0; i < I; ++i) S[4 * p + i] = S2[i] + S3[i];
-    }
-    mat_vec(I, Phi, P, Q);
-    for (int i = 0; i < I; ++i) P[i] = Q[i];
+    expm_work(w, I, A, dA);
+    for (int q = 0; q < np; ++q) F.JtJ[p * np + q] = 0.0;
+    F.g[p] = 0.0;
     for (int i = 0; i < I; ++i) {
-      const double r = frac_at(a, n, i) - P[i];
-      for (int p = 0; p < np; ++p) {
-        g[p] += S[4 * p + i] * r;
-        for (int q = 0; q < np; ++q) JtJ[p * np + q] += S[4 * p + i] * S[4 * q + i];
+      P[i] = frac_at(a, 0, i);
+      F.S[p][i] = 0.0;
+    }
+  }
+  for (int n = 1; n <= k; ++n) {
+    if (own) {
+      // S_p <- dPhi_p P + Phi S_p (the derivative of P_n), then P <- Phi P
+      mat_vec(I, dPhi, P, S2);
+      mat_vec(I, Phi, F.S[p], S3);
+      for (int i = 0; i < I; ++i) F.S[p][i] = S2[i] + S3[i];
+      mat_vec(I, Phi, P, Q);
+      for (int i = 0; i < I; ++i) P[i] = Q[i];
+    }
+    __syncwarp();
+    if (own) {
+      for (int i = 0; i < I; ++i) {
+        const double r = frac_at(a, n, i) - P[i];
+        const double sp = F.S[p][i];
+        F.g[p] += sp * r;
+        for (int q = 0; q < np; ++q) F.JtJ[p * np + q] += sp * F.S[q][i];
       }
     }
+    __syncwarp();
   }
 }
 
-// M x = b for symmetric positive definite M (Cholesky); false if not SPD
-__device__ bool spd_solve(double* ws, int n, const double* M, const double* b, double* x) {
-  double* L = ws + kFitL;
-  double* y = ws + kFitY;
+// M x = b for symmetric positive definite M (Cholesky, factor in Lf); false if not SPD
+__device__ bool spd_solve(double* Lf, double* y, int n, const double* M, const double* b, double* x) {
   for (int i = 0; i < n; ++i) {
     for (int j = 0; j <= i; ++j) {
       double s = M[i * n + j];
-      for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+      for (int k = 0; k < j; ++k) s -= Lf[i * n + k] * Lf[j * n + k];
       if (i == j) {
         if (!(s > 0.0) || !isfinite(s)) return false;
-        L[i * n + i] = sqrt(s);
+        Lf[i * n + i] = sqrt(s);
       } else {
-        L[i * n + j] = s / L[j * n + j];
+        Lf[i * n + j] = s / Lf[j * n + j];
       }
     }
   }
   for (int i = 0; i < n; ++i) {
     double s = b[i];
-    for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
-    y[i] = s / L[i * n + i];
+    for (int k = 0; k < i; ++k) s -= Lf[i * n + k] * y[k];
+    y[i] = s / Lf[i * n + i];
   }
   for (int i = n - 1; i >= 0; --i) {
     double s = y[i];
-    for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
-    x[i] = s / L[i * n + i];
+    for (int k = i + 1; k < n; ++k) s -= Lf[k * n + i] * x[k];
+    x[i] = s / Lf[i * n + i];
   }
   return true;
 }
 
-// normal equations in theta: J_theta = J_omega diag(2 theta)
-__device__ void to_theta(int np, const double* th, double* JtJ, double* g) {
+// One lane: the damped step on the free rates (F.st) and its predicted
+// decrease; returns the number of free rates, or -1 if the system is not SPD.
+__device__ int rate_free_step(FitShared& F, int np, double om_max, double mu, double& pred) {
+  int nf = 0;
   for (int p = 0; p < np; ++p) {
-    g[p] *= 2.0 * th[p];
-    for (int q = 0; q < np; ++q) JtJ[p * np + q] *= (2.0 * th[p]) * (2.0 * th[q]);
+    F.st[p] = 0.0;
+    const bool held = (F.om[p] == 0.0 && !(F.g[p] > 0.0)) || (F.om[p] == om_max && !(F.g[p] < 0.0));
+    if (!held) F.fidx[nf++] = p;
   }
+  pred = 0.0;
+  if (nf == 0) return 0;
+  for (int r = 0; r < nf; ++r) {
+    for (int c = 0; c < nf; ++c) F.M[r * nf + c] = F.JtJ[F.fidx[r] * np + F.fidx[c]];
+    F.M[r * nf + r] = F.M[r * nf + r] + mu;
+    F.b[r] = F.g[F.fidx[r]];
+  }
+  if (!spd_solve(F.L, F.y, nf, F.M, F.b, F.x)) return -1;
+  double s = 0.0;
+  for (int r = 0; r < nf; ++r) {
+    F.st[F.fidx[r]] = F.x[r];
+    s += F.x[r] * (mu * F.x[r] + F.b[r]);
+  }
+  pred = s;
+  return nf;
 }
 
-__device__ bool rate_fit(const DriverArgs& a, int I, int k, double* om) {
+// Whole warp.  Returns 0 (converged), 1 (stopped; rates still used), -1 (k < I)
+// or -2 (a rate not finite); the rates are left in F.om.
+__device__ int rate_fit(const DriverArgs& a, FitShared& F, int I, int k) {
   const int np = I * (I - 1);
-  if (I < 2 || I > kMaxRegions || k < I || a.fit == nullptr) return false;
-  double* ws = a.fit;
+  const int lane = threadIdx.x & 31;
+  if (I < 2 || I > kMaxRegions || k < I) return -1;
   const double dT = a.dT;
-  double* th = ws + kFitTh;
-  double* nth = ws + kFitNth;
-  double* nw = ws + kFitNw;
-  {
-    double* Sxx = ws + kFitSxx;
-    double* Syx = ws + kFitSyx;
-    double* Phi0 = ws + kFitPhi0;
-    double* rhs = ws + kFitRhs;
-    double* x = ws + kFitX;
+  const double floor_rate = 1e-3 / ((double)k * dT);
+  const double om_max = 20.0 / dT;
+  double cost = 0.0, mu = 0.0, nu = 2.0;
+  if (lane == 0) {
     for (int r = 0; r < 16; ++r) {
-      Sxx[r] = 0.0;
-      Syx[r] = 0.0;
+      F.Sxx[r] = 0.0;
+      F.Syx[r] = 0.0;
     }
     for (int n = 1; n <= k; ++n)
       for (int p = 0; p < I; ++p)
         for (int q = 0; q < I; ++q) {
-          Sxx[p * I + q] += frac_at(a, n - 1, p) * frac_at(a, n - 1, q);
-          Syx[p * I + q] += frac_at(a, n, p) * frac_at(a, n - 1, q);
+          F.Sxx[p * I + q] += frac_at(a, n - 1, p) * frac_at(a, n - 1, q);
+          F.Syx[p * I + q] += frac_at(a, n, p) * frac_at(a, n - 1, q);
         }
-    const double floor_rate = 1e-3 / ((double)k * dT);
     bool ok = true;
     for (int p = 0; p < I && ok; ++p) {
-      for (int q = 0; q < I; ++q) rhs[q] = Syx[p * I + q];
-      if (!spd_solve(ws, I, Sxx, rhs, x)) {
+      for (int q = 0; q < I; ++q) F.rhs[q] = F.Syx[p * I + q];
+      if (!spd_solve(F.L, F.y, I, F.Sxx, F.rhs, F.xr)) {
         ok = false;
       } else {
-        for (int q = 0; q < I; ++q) Phi0[p * I + q] = x[q];
+        for (int q = 0; q < I; ++q) F.Phi0[p * I + q] = F.xr[q];
       }
     }
     for (int i = 0; i < I; ++i)
       for (int j = 0; j < I; ++j) {
         if (j == i) continue;
-        const double w = ok ? Phi0[j * I + i] / dT : 1.0 / ((double)I * (double)k * dT);
-        th[i * (I - 1) + (j < i ? j : j - 1)] = sqrt(isfinite(w) && w > floor_rate ? w : floor_rate);
+        const double w = ok ? F.Phi0[j * I + i] / dT : 1.0 / ((double)I * (double)k * dT);
+        F.om[i * (I - 1) + (j < i ? j : j - 1)] = isfinite(w) && w > floor_rate ? fmin(w, 1.0 / dT) : floor_rate;
       }
+    cost = rate_cost(a, F, I, k, F.om);
   }
-  const double th_floor = sqrt(1e-3 / ((double)k * dT));
-  for (int p = 0; p < np; ++p) om[p] = th[p] * th[p];
-  double lambda = 1e-3;
-  double cost = rate_cost(a, ws, I, k, om);
-  double* JtJ = ws + kFitJtJ;
-  double* g = ws + kFitG;
-  double* M = ws + kFitM;
-  double* st = ws + kFitSt;
-  for (int it = 0; it < 100; ++it) {
-    rate_normal(a, ws, I, k, om, JtJ, g);
-    to_theta(np, th, JtJ, g);
-    for (int r = 0; r < np * np; ++r) M[r] = JtJ[r];
-    for (int p = 0; p < np; ++p) M[p * np + p] = JtJ[p * np + p] * (1.0 + lambda);
-    if (!spd_solve(ws, np, M, g, st)) {
-      lambda *= 10.0;
-      if (lambda > 1e12) break;
-      continue;
-    }
-    for (int p = 0; p < np; ++p) {
-      const double cap = 2.0 * fmax(fabs(th[p]), th_floor);
-      nth[p] = th[p] + fmax(-cap, fmin(cap, st[p]));
-      nw[p] = nth[p] * nth[p];
-    }
-    const double ncost = rate_cost(a, ws, I, k, nw);
-    if (isfinite(ncost) && ncost < cost) {
-      double rel = 0.0;
-      for (int p = 0; p < np; ++p) {
-        th[p] = nth[p];
-        om[p] = nw[p];
-        rel = fmax(rel, fabs(st[p]) / (fabs(th[p]) + 1e-300));
+  rate_normal_warp(a, F, I, k);
+  if (lane == 0) {
+    for (int p = 0; p < np; ++p) mu = fmax(mu, F.JtJ[p * np + p]);
+    mu = 1e-3 * mu;
+  }
+  // lane 0 decides; 0 = go on, 1 = accepted (new J^T J needed), 2 = converged, 3 = stopped
+  int state = __shfl_sync(0xffffffffu, cost == 0.0 ? 2 : 0, 0);
+  for (int it = 0; it < kRateFitMaxIter && state < 2; ++it) {
+    int act = 0;
+    if (lane == 0) {
+      double pred;
+      const int nf = rate_free_step(F, np, om_max, mu, pred);
+      if (nf == 0) {
+        act = 2;  // every rate held at a bound: a stationary point
+      } else {
+        double ncost = 0.0;
+        if (nf > 0) {
+          for (int p = 0; p < np; ++p) F.nw[p] = fmin(fmax(F.om[p] + F.st[p], 0.0), om_max);
+          ncost = rate_cost(a, F, I, k, F.nw);
+        }
+        if (nf > 0 && pred > 0.0 && isfinite(ncost) && ncost < cost) {
+          const double rho = (cost - ncost) / pred;
+          const double t = 2.0 * rho - 1.0;
+          for (int p = 0; p < np; ++p) F.om[p] = F.nw[p];
+          cost = ncost;
+          mu = mu * fmax(1.0 / 3.0, 1.0 - t * t * t);
+          nu = 2.0;
+          act = (pred < 1e-15 * cost || cost == 0.0) ? 2 : 1;
+        } else if (nf > 0 && !(pred > 0.0)) {
+          act = 2;  // no descent left on the free rates
+        } else {
+          mu = mu * nu;
+          nu = 2.0 * nu;
+          act = nu > 1e18 ? 3 : 0;
+        }
       }
-      cost = ncost;
-      lambda /= 10.0;
-      if (rel < 1e-15) break;
-    } else {
-      lambda *= 10.0;
-      if (lambda > 1e12) break;
     }
+    act = __shfl_sync(0xffffffffu, act, 0);
+    if (act == 1) rate_normal_warp(a, F, I, k);
+    if (act >= 2) state = act;
   }
-  for (int it = 0; it < 3; ++it) {
-    rate_normal(a, ws, I, k, om, JtJ, g);
-    to_theta(np, th, JtJ, g);
-    if (!spd_solve(ws, np, JtJ, g, st)) break;
-    for (int p = 0; p < np; ++p) {
-      nth[p] = th[p] + st[p];
-      nw[p] = nth[p] * nth[p];
-    }
-    const double ncost = rate_cost(a, ws, I, k, nw);
-    if (!(isfinite(ncost) && ncost <= cost)) break;
-    for (int p = 0; p < np; ++p) {
-      th[p] = nth[p];
-      om[p] = nw[p];
-    }
-    cost = ncost;
+  __syncwarp();
+  int rc = state == 2 ? 0 : 1;
+  if (lane == 0) {
+    for (int p = 0; p < np; ++p)
+      if (!isfinite(F.om[p]) || !(F.om[p] >= 0.0)) rc = -2;
   }
-  for (int p = 0; p < np; ++p)
-    if (!isfinite(om[p]) || !(om[p] >= 0.0)) return false;
-  return true;
+  return __shfl_sync(0xffffffffu, rc, 0);
 }
 
 }  // namespace
@@ -698,7 +725,6 @@ __device__ void driver_body(const DriverArgs& a) {
   // Def. 3.4: fit the fractions of the exact slice ends t_0..t_k
   bool learn = false;
   double alpha = 0.0, beta = 0.0;
-  double om[kMaxRates];
   if (a.variant == MMP_LEARNING && I == 2 && k >= 2) {
     const double p0 = frac0_at(a, 0);
     learn = lsq_fit(a, k, p0, alpha, beta);
@@ -715,17 +741,29 @@ __device__ void driver_body(const DriverArgs& a) {
   // Each value is the same expression as in a single sequential pass, so
   // the results are the same bit for bit; the FP64 instructions (slow on this
   // chip) off the chain no longer wait for it.
-  __shared__ double s_stage[kDrvChunk * kDrvRow];
-  __shared__ double s_out[kDrvChunk * kDrvOut];
+  // The staging arrays double as the rate fit's working memory: the fit
+  // ends before the staging starts.
+  __shared__ __align__(16) double s_work[kDrvChunk * (kDrvRow + kDrvOut)];
+  static_assert(sizeof(FitShared) <= sizeof(s_work), "fit working memory");
+  double* s_stage = s_work;
+  double* s_out = s_work + kDrvChunk * kDrvRow;
   Macro cur;
   double Phi[16];
   double phat[kMaxRegions];  // extrapolated fractions (I >= 3), from those of t_k
   double change = 0.0;
   int acc = 0, rej = 0;
   bool numeric_bad = false;
+  if (a.variant == MMP_LEARNING && I >= 3 && k >= I) {
+    // the whole warp fits; lane 0 keeps Phi = expm(A dT) of the fitted rates
+    FitShared& F = *reinterpret_cast<FitShared*>(s_work);
+    learn = rate_fit(a, F, I, k) >= 0;
+    if (learn && lane == 0) {
+      const double* ph = rate_phi(F.cw, I, F.om, a.dT);
+      for (int r = 0; r < I * I; ++r) Phi[r] = ph[r];
+    }
+    __syncwarp();
+  }
   if (lane == 0) {
-    if (a.variant == MMP_LEARNING && I >= 3 && k >= I) learn = rate_fit(a, I, k, om);
-    if (learn && I >= 3) rate_phi(a.fit, I, om, a.dT, Phi);
     for (int i = 0; i < I; ++i) phat[i] = frac_at(a, k, i);
     macro_load(a.rho, cur);  // rho^{k}_0 = R(u0), unchanged
   }

@@ -5,8 +5,6 @@
 
 namespace mmp {
 
-constexpr int kFitScratch = 1088;  // doubles of fit scratch per problem (rate model, I >= 3)
-
 struct DriverArgs {
   double nc3, c1, kappa, c0, B, BE, B0;  // model (nc3 = -c3)
   int N, I, variant, precision;
@@ -23,7 +21,6 @@ struct DriverArgs {
   double* cache;           // [N][2 kMaxRegions] C_n(rho^{k-1}_n): (mean_i, var_i) per region
   double* aff;             // [N+1][kMaxRegions][kAff] matching records for the inputs u^k_n
   double* ctl;             // control block (see k_driver)
-  double* fit;             // [kFitScratch] working arrays of the rate-model fit
   unsigned* status;
   int sweep;               // 0 = lifting, k >= 1 = after fine sweep k
 };
