@@ -101,7 +101,6 @@ struct Prob {
   char* S[2] = {nullptr, nullptr};
   double *stats = nullptr, *stats_u0 = nullptr, *ser_stats = nullptr, *tmp_stats = nullptr;
   double *rho = nullptr, *cache = nullptr, *aff = nullptr, *ctl = nullptr, *partials = nullptr;
-  double* fit = nullptr;  // rate-model fit scratch (learning with three or more regions)
   unsigned *flags = nullptr, *status = nullptr;
   unsigned long long* tags = nullptr;  // followed by flags: one block, cleared per launch
   // host view of the iteration
@@ -330,7 +329,6 @@ size_t layout(Prob& p, char* base, size_t start) {
   p.cache = (double*)ptr(sizeof(double) * 2 * kMaxRegions * N);
   p.aff = (double*)ptr(sizeof(double) * kMaxRegions * kAff * (N + 1));
   p.ctl = (double*)ptr(sizeof(double) * 16);
-  p.fit = p.I >= 3 && p.d.variant == MMP_LEARNING ? (double*)ptr(sizeof(double) * kFitScratch) : nullptr;
   p.partials = (double*)ptr(sizeof(double) * kSeatDoubles * (size_t)p.slots_max * p.G);
   p.tags = (unsigned long long*)ptr(sync_bytes(p));
   p.flags = base ? (unsigned*)(p.tags + (size_t)p.slots_max * kSlots * p.G) : nullptr;
@@ -469,7 +467,7 @@ DriverArgs make_driver_args(const Prob& p, int sweep) {
   a.thr = d.threshold; a.thr2 = d.threshold2; a.thr3 = d.threshold3;
   a.tol = d.tol; a.max_sweeps = p.max_sweeps;
   a.stats = p.stats; a.stats_u0 = p.stats_u0; a.rho = p.rho; a.cache = p.cache; a.aff = p.aff;
-  a.ctl = p.ctl; a.fit = p.fit; a.status = p.status; a.sweep = sweep;
+  a.ctl = p.ctl; a.status = p.status; a.sweep = sweep;
   return a;
 }
 
@@ -1510,24 +1508,15 @@ extern "C" int mmp_fine_static(const mmp_problem_desc* desc, int n, const void* 
   cudaStream_t s = (cudaStream_t)stream;
   // every call shares the array: clear what must start at zero
   MMP_CUDA(cudaMemsetAsync(tags, 0, kStaticCtlDoubles * sizeof(double), s));
-  FineArgs a;
-  const mmp_problem_desc& d = p.d;
-  a.nc3 = -d.c3; a.c1 = d.c1; a.kappa = d.kappa; a.c0 = d.c0;
-  a.B = d.B; a.BE = d.BE; a.B0 = d.B0;
-  a.h = p.h; a.sqrt_h = p.sqrt_h; a.nf = p.nf;
-  a.P = d.P; a.Q = p.Q; a.pitch = p.pitch;
-  a.n_regions = p.I; a.thr = d.threshold; a.thr2 = d.threshold2; a.thr3 = d.threshold3;
-  a.key0 = p.key0; a.key1 = p.key1; a.ptag = d.problem_tag;
+  // the problem's own arguments; only the buffers and the one task differ
+  FineArgs a = fine_args_of(p, wait_limit_ns());
   a.slice_begin = n; a.n_tasks = 1;
   a.src0 = u_in; a.src = nullptr; a.dst = u_out; a.dst_fixed = 1;
   a.aff = nullptr; a.aff_fixed = 0;
   a.stats = stats; a.stats_fixed = 1;
-  a.G = p.G;
-  a.nq = p.nq;
   a.partials = base; a.flags = flags; a.tags = tags; a.status = status;
-  a.wait_limit_ns = wait_limit_ns();
   a.tight_polls = p.G <= dev.sms ? kTightPolls : 0;
-  MMP_CUDA(launch_fine(d.precision, p.layout, p.nq, p.mult, p.G, a, s));
+  MMP_CUDA(launch_fine(p.d.precision, p.layout, p.nq, p.mult, p.G, a, s));
   if (stats_dev != nullptr) {
     k_status_to_stats<<<1, 1, 0, s>>>(status, stats_dev);
     MMP_CUDA(cudaGetLastError());
