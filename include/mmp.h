@@ -65,6 +65,15 @@ extern "C" {
  *   dX = a(X, E[X]) dt + b(X, E[X]) dW,  X(0) ~ N(m0, s0^2)
  *   a(x, m) = -c3 x^3 + c1 x + kappa m + c0
  *   b(x, m) = B x + BE m + B0
+ * (family MMP_FAMILY_POLY), or the plane rotator of Sec. 5 (Example
+ * "Unimodal plane rotator", Eq. SDE_plane_rotator; family
+ * MMP_FAMILY_ROTATOR):
+ *   a(x) = (K/P) sum_q sin(X_q - x) - g sin x = K (S cos x - C sin x) - g sin x,
+ *   b = B0,
+ * with S, C the ensemble means of sin X and cos X, every particle shifted
+ * modulo 2 pi into [-pi, pi] (x - 2 pi floor((x + pi) / (2 pi))) after each
+ * Euler-Maruyama step and in the initial ensemble; c3, c1, kappa, c0 are
+ * unused and B, BE must be 0; one region.
  * on [0, T] cut into N Parareal slices; each slice takes
  * n_f = ceil(T/(N dt) - 1e-9) Euler-Maruyama steps of h = T/(N n_f).
  * The coarse propagator is the Gaussian-closure moment ODE per region
@@ -95,7 +104,13 @@ typedef struct {
   int coarse_model;          /* MMP_COARSE_CLOSURE (0) / _TAYLOR / _SIGMA2 / _SIGMA3 */
   double threshold2;         /* t_2 (n_regions >= 3), > t_1                   */
   double threshold3;         /* t_3 (n_regions = 4), > t_2                    */
+  int family;                /* MMP_FAMILY_POLY (0) / MMP_FAMILY_ROTATOR      */
+  double K, g;               /* plane rotator: coupling K, pinning g          */
 } mmp_problem_desc;
+
+/* Drift families. */
+#define MMP_FAMILY_POLY 0
+#define MMP_FAMILY_ROTATOR 1
 
 /* Largest n_regions. */
 #define MMP_MAX_REGIONS 4
@@ -107,11 +122,20 @@ typedef struct {
  *   TAYLOR:  the Taylor-expansion model, Eq. moment_model_class_1
  *            (dM = a(M) + a_XX(M) Sigma / 2, dSigma = (2 a_X + b_X^2) Sigma + b^2);
  *   SIGMA2 / SIGMA3: Gaussian-assumed density, Eq. Gaussian_model_McK_V_SDE,
- *            with a 2- or 3-point sigma-point rule. */
+ *            with a 2- or 3-point sigma-point rule;
+ *   TAYLOR1: the Taylor model without the Sigma term of the mean,
+ *            dM = a(M) (the plane-rotator example's first coarse solver).
+ * For the plane rotator the closure takes S = sin M e^{-Sigma/2},
+ * C = cos M e^{-Sigma/2} under N(M, Sigma) and Stein's lemma for the
+ * variance (dM = -g S, dSigma = 2 Sigma (-K (S^2 + C^2) - g C) + B0^2);
+ * the Taylor models take the point mass at M (a_X(M) = -K - g cos M); the
+ * sigma-point rules take every expectation, S and C included, from their
+ * points. */
 #define MMP_COARSE_CLOSURE 0
 #define MMP_COARSE_TAYLOR 1
 #define MMP_COARSE_SIGMA2 2
 #define MMP_COARSE_SIGMA3 3
+#define MMP_COARSE_TAYLOR1 4
 
 typedef struct mmp_ctx mmp_ctx;
 
@@ -132,9 +156,10 @@ typedef struct mmp_ctx mmp_ctx;
 const char* mmp_strerror(int code);
 /* Version of the C-ABI: 101 adds up to four regions (threshold2, threshold3;
  * 16-double moment rows, 32-double restriction records), seven-coefficient
- * adjoints (mmp_set_params' n_theta, mmp_adjoint).  Checkpoints (mmp_get_state)
- * restore only into the same version. */
-#define MMP_VERSION 101
+ * adjoints (mmp_set_params' n_theta, mmp_adjoint); 102 adds the drift
+ * family (family, K, g: the plane rotator) and MMP_COARSE_TAYLOR1.
+ * Checkpoints (mmp_get_state) restore only into the same version. */
+#define MMP_VERSION 102
 int mmp_version(void);
 /* Last CUDA error code seen by the library in this process (0 if none). */
 int mmp_last_cuda_error(void);
@@ -351,21 +376,45 @@ int mmp_philox(const unsigned int* ctr, const unsigned int* key, unsigned int* o
 int mmp_normals(const mmp_problem_desc* desc, int tag, unsigned int j, unsigned int n,
                 long long count, void* out, void* stream);
 
+/* Self-test of the failure detection of the fine kernel's group exchange
+ * (the paper has no counterpart; a property of the library).  Launches one
+ * CTA of a group of G CTAs on `stream`; it runs the kernel's own group
+ * reduction (channel 0: records behind release/acquire epoch flags, as the
+ * restriction and FP64 particles use; channel 1: the tagged 8-byte step
+ * words of float particles), but no peer ever publishes, so with G >= 2
+ * every bounded wait runs out after limit_ms milliseconds, sets the timeout
+ * bit (1) of the status word and lets the kernel return; nothing faults or
+ * hangs, and the device stays usable.  ws: device scratch, 256-byte
+ * aligned, at least G * 548 + 4 bytes (publication slots, step words, epoch
+ * flags, status word), caller-owned.  Synchronising.  *status_out (may be
+ * NULL) receives the status word.  Returns MMP_ERR_TIMEOUT when the wait ran
+ * out (G >= 2), MMP_OK when nothing had to be waited for (G = 1);
+ * MMP_ERR_INVALID_ARG for a channel other than 0 or 1, G outside 1..1024 or
+ * limit_ms outside [1, 10000]; MMP_ERR_WORKSPACE for a NULL, misaligned or
+ * short ws. */
+int mmp_probe_wait(int channel, int G, double limit_ms, void* ws, size_t ws_bytes, void* stream,
+                   unsigned* status_out);
+
 /* One fine propagation F_n of an explicit ensemble, like mmp_fine, for
- * callers that cannot allocate device memory where they need it: work
- * issued while a stream is being captured into a CUDA graph (allocation is
- * not allowed inside a capture), hosts whose device pool belongs to another
- * allocator, latency-bound loops where an allocation could stall.  The
- * paper has no counterpart; this is a property of the library.
+ * callers that cannot allocate device memory where they call it: code
+ * inside a host application or framework that owns the GPU's memory through
+ * its own allocator and gives plugins no way to reserve more, and
+ * latency-bound loops in which a cudaMalloc or cudaFree (which can
+ * synchronise the whole device) is not acceptable.  They own their
+ * ensembles; what they cannot provide is the scratch of the kernel's
+ * cross-CTA mean reduction.  The paper has no counterpart; this is a
+ * property of the library.
  *
- * No context, no workspace, no allocation: the scratch of the kernel's
- * cross-CTA mean reduction comes from one fixed array inside libmmp.so
- * (about 650 KB of device memory, held on every GPU that loads the library
- * until the process exits), serving at most MMP_STATIC_MAX_CTAS CTAs per
- * slice; larger problems (above roughly 9.9e6 float or 4.9e6 double
- * particles, depending on the launch shape) return MMP_ERR_UNSUPPORTED.
- * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.
+ * No context, no workspace, no allocation: that scratch is one fixed array
+ * inside libmmp.so (about 650 KB of device memory, held on every GPU that
+ * loads the library until the process exits), serving at most
+ * MMP_STATIC_MAX_CTAS CTAs per slice; larger problems (above roughly 9.9e6
+ * float or 4.9e6 double particles, depending on the launch shape) return
+ * MMP_ERR_UNSUPPORTED before any device work.  The first call on a device
+ * looks up the array's device address (once per device, kept for the life
+ * of the process); make that first call before any stream capture.  After a
+ * cudaDeviceReset the kept address is stale: resetting a device while this
+ * entry point is in use is not supported.
  *
  * desc      problem (only one slice is propagated; n in 0..N-1 selects the
  *           draws)
@@ -373,7 +422,10 @@ int mmp_normals(const mmp_problem_desc* desc, int tag, unsigned int j, unsigned 
  *           16-byte aligned; u_out device, P values, must not alias u_in
  * stats_dev device, MMP_STAT_STRIDE doubles or NULL: the restriction of
  *           F_n(u_in); element 14 receives the device status bits
- *           (0 = ok, 1 = a bounded wait gave up, 2 = non-finite result)
+ *           (0 = ok, 1 = a bounded wait gave up, 2 = non-finite result).
+ *           This is the only place device-side errors are reported: with
+ *           stats_dev NULL a timed-out or non-finite propagation is not
+ *           seen by the caller.
  * stream    cudaStream_t; asynchronous.
  * Every call shares the array and leaves its contents behind: the call
  * clears what must start at zero, and calls that overlap on the GPU (on

@@ -20,13 +20,15 @@
 static_assert(mmp::kNGrad == MMP_N_THETA, "adjoint gradient length");
 
 namespace mmp {
-const void* fine_kernel_f32(int nq, bool mult);
-const void* fine_kernel_f64(int nq, bool mult);
+cudaError_t launch_wait_probe(double* partials, unsigned* flags, unsigned long long* tags, unsigned* status, int G,
+                              unsigned long long limit_ns, int channel, cudaStream_t stream);
+const void* fine_kernel_f32(int nq, bool mult, int family);
+const void* fine_kernel_f64(int nq, bool mult, int family);
 
-const void* fine_kernel(int precision, int layout, int nq, bool mult) {
+const void* fine_kernel(int precision, int layout, int nq, bool mult, int family) {
   const int t = layout == kLayoutSmem ? 0 : nq;
   if (layout != kLayoutSmem && nq < 1) return nullptr;
-  return precision == MMP_MIXED ? fine_kernel_f32(t, mult) : fine_kernel_f64(t, mult);
+  return precision == MMP_MIXED ? fine_kernel_f32(t, mult, family) : fine_kernel_f64(t, mult, family);
 }
 
 size_t fine_smem_bytes(int precision, int layout, int nq) {
@@ -35,8 +37,8 @@ size_t fine_smem_bytes(int precision, int layout, int nq) {
 }
 
 cudaError_t launch_fine(int precision, int layout, int nq, bool mult, int grid, const FineArgs& args,
-                        cudaStream_t stream) {
-  const void* fn = fine_kernel(precision, layout, nq, mult);
+                        cudaStream_t stream, int family) {
+  const void* fn = fine_kernel(precision, layout, nq, mult, family);
   if (fn == nullptr) return cudaErrorInvalidValue;
   FineArgs copy = args;
   void* params[] = {&copy};
@@ -125,8 +127,8 @@ int query_device(Device& d) {
 }
 
 bool finite_all(const mmp_problem_desc& d) {
-  const double v[] = {d.c3, d.c1, d.kappa, d.c0, d.B, d.BE, d.B0, d.m0, d.s0,
-                      d.T, d.dt, d.coarse_h, d.threshold, d.threshold2, d.threshold3, d.tol};
+  const double v[] = {d.c3, d.c1, d.kappa, d.c0, d.B, d.BE, d.B0, d.m0, d.s0, d.T, d.dt,
+                      d.coarse_h, d.threshold, d.threshold2, d.threshold3, d.tol, d.K, d.g};
   for (double x : v)
     if (!std::isfinite(x)) return false;
   return true;
@@ -142,7 +144,13 @@ int validate(const mmp_problem_desc& d) {
   if (d.n_regions >= 4 && !(d.threshold3 > d.threshold2)) return MMP_ERR_INVALID_ARG;
   if (d.variant < MMP_UNIMODAL || d.variant > MMP_LEARNING) return MMP_ERR_INVALID_ARG;
   if (d.precision != MMP_FP64 && d.precision != MMP_MIXED) return MMP_ERR_INVALID_ARG;
-  if (d.coarse_model < MMP_COARSE_CLOSURE || d.coarse_model > MMP_COARSE_SIGMA3) return MMP_ERR_INVALID_ARG;
+  if (d.coarse_model < MMP_COARSE_CLOSURE || d.coarse_model > MMP_COARSE_TAYLOR1) return MMP_ERR_INVALID_ARG;
+  if (d.family != MMP_FAMILY_POLY && d.family != MMP_FAMILY_ROTATOR) return MMP_ERR_INVALID_ARG;
+  if (d.family == MMP_FAMILY_ROTATOR) {
+    // the plane rotator: additive noise, one region (Sec. 5's unimodal example)
+    if (d.B != 0.0 || d.BE != 0.0) return MMP_ERR_INVALID_ARG;
+    if (d.n_regions != 1) return MMP_ERR_UNSUPPORTED;
+  }
   const double steps = std::ceil((d.T / d.N) / d.dt - 1e-9);
   if (!(steps >= 1) || steps > 2e9) return MMP_ERR_INVALID_ARG;
   const double csteps = std::ceil((d.T / d.N) / d.coarse_h - 1e-9);
@@ -162,7 +170,7 @@ void derive(Prob& p) {
   p.Q = (int)((d.P + 3) / 4);
   p.pitch = 4LL * p.Q;
   p.esz = d.precision == MMP_MIXED ? 4 : 8;
-  p.mult = d.B != 0.0 || d.BE != 0.0;
+  p.mult = d.family == MMP_FAMILY_POLY && (d.B != 0.0 || d.BE != 0.0);
   p.key0 = (uint32_t)(d.seed & 0xffffffffull);
   p.key1 = (uint32_t)(d.seed >> 32);
   const int mi = d.max_iter > 0 ? d.max_iter : d.N;
@@ -208,7 +216,7 @@ int plan(Prob& p, const Device& dev, int batch_nq = 0) {
     p.G = (int)(((long long)p.Q + (long long)p.nq * kTPB - 1) / ((long long)p.nq * kTPB));
     p.slots_max = 1;
     // the per-problem kernel still serves lifting and serial runs
-    const void* fn = fine_kernel(p.d.precision, kLayoutSmem, p.nq, p.mult);
+    const void* fn = fine_kernel(p.d.precision, kLayoutSmem, p.nq, p.mult, p.d.family);
     size_t limit = 0;
     const int rc = allow_dynamic_smem(fn, dev.dev, &limit);
     if (rc) return rc;
@@ -220,14 +228,15 @@ int plan(Prob& p, const Device& dev, int batch_nq = 0) {
     return MMP_OK;
   }
   const char* env = std::getenv("MMP_FINE_LAYOUT");
-  const int layout = (env != nullptr && std::strcmp(env, "regs") == 0) ? kLayoutRegs : kLayoutSmem;
+  const int layout = (env != nullptr && std::strcmp(env, "regs") == 0 && p.d.family == MMP_FAMILY_POLY)
+                         ? kLayoutRegs : kLayoutSmem;
   const char* env_nq = std::getenv("MMP_FINE_NQ");
   const int max_nq_l = layout == kLayoutSmem ? (p.esz == 4 ? 32 : 16) : (p.esz == 4 ? 8 : 4);
   if (tuned > 0 && (layout != kLayoutSmem || tuned > max_nq_l)) tuned = 0;
   if (tuned > 0) {
     // a measured shape is a saturated-throughput optimum: use it only if the
     // problem's slices fill the resident CTAs at that shape
-    const void* fn = fine_kernel(p.d.precision, layout, tuned, p.mult);
+    const void* fn = fine_kernel(p.d.precision, layout, tuned, p.mult, p.d.family);
     size_t limit = 0;
     int occ = 0;
     const size_t smem = fine_smem_bytes(p.d.precision, layout, tuned);
@@ -242,7 +251,7 @@ int plan(Prob& p, const Device& dev, int batch_nq = 0) {
   int occ_of[33] = {0};
   for (int nq = 1; nq <= max_nq; ++nq) {
     int occ = 0;
-    const void* fn = fine_kernel(p.d.precision, layout, nq, p.mult);
+    const void* fn = fine_kernel(p.d.precision, layout, nq, p.mult, p.d.family);
     if (fn == nullptr) return MMP_ERR_UNSUPPORTED;
     const size_t smem = fine_smem_bytes(p.d.precision, layout, nq);
     if (layout == kLayoutSmem) {
@@ -254,7 +263,8 @@ int plan(Prob& p, const Device& dev, int batch_nq = 0) {
     MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, smem));
     occ_of[nq] = occ;
   }
-  const double quad_rate = p.esz == 4 ? 0.8 : 0.02;  // quad-steps per cycle per SM
+  // quad-steps per cycle per SM (the rotator evaluates two sine-cosine pairs per particle-step)
+  const double quad_rate = (p.esz == 4 ? 0.8 : 0.02) * (p.d.family == MMP_FAMILY_ROTATOR ? 0.4 : 1.0);
   double best = INFINITY;
   int best_nq = 0, best_G = 0, best_slots = 0;
   const int N = p.d.N;
@@ -439,6 +449,7 @@ FineArgs fine_args_of(const Prob& p, unsigned long long limit_ns) {
   const mmp_problem_desc& d = p.d;
   a.nc3 = -d.c3; a.c1 = d.c1; a.kappa = d.kappa; a.c0 = d.c0;
   a.B = d.B; a.BE = d.BE; a.B0 = d.B0;
+  a.K = d.K; a.gpin = d.g;
   a.h = p.h; a.sqrt_h = p.sqrt_h; a.nf = p.nf;
   a.P = d.P; a.Q = p.Q; a.pitch = p.pitch;
   a.n_regions = p.I; a.thr = d.threshold; a.thr2 = d.threshold2; a.thr3 = d.threshold3;
@@ -461,6 +472,7 @@ DriverArgs make_driver_args(const Prob& p, int sweep) {
   const mmp_problem_desc& d = p.d;
   a.nc3 = -d.c3; a.c1 = d.c1; a.kappa = d.kappa; a.c0 = d.c0;
   a.B = d.B; a.BE = d.BE; a.B0 = d.B0;
+  a.family = d.family; a.K = d.K; a.g = d.g;
   a.N = d.N; a.I = p.I; a.variant = d.variant; a.precision = d.precision;
   a.coarse_model = d.coarse_model;
   a.dT = p.dT; a.hc = p.hc; a.nc = p.nc; a.P = d.P;
@@ -488,7 +500,8 @@ int batch_plan(const std::vector<Prob>& probs, const Device& dev, BatchLayout& B
   const char* e = std::getenv("MMP_BATCH");
   if (e != nullptr && std::strcmp(e, "0") == 0) return MMP_OK;
   for (const Prob& p : probs)
-    if (p.d.precision != probs[0].d.precision || p.mult != probs[0].mult) return MMP_OK;
+    if (p.d.precision != probs[0].d.precision || p.mult != probs[0].mult || p.d.family != MMP_FAMILY_POLY)
+      return MMP_OK;
   int nq_max = 1;
   for (const Prob& p : probs) {
     nq_max = std::max(nq_max, p.nq);
@@ -588,7 +601,7 @@ int run_fine(mmp_ctx* c, Prob& p, int slice_begin, int n_tasks, int nf, const vo
     }
     MMP_CUDA(cudaEventRecord(e0, c->stream));
   }
-  MMP_CUDA(launch_fine(d.precision, p.layout, p.nq, p.mult, slots * p.G, a, c->stream));
+  MMP_CUDA(launch_fine(d.precision, p.layout, p.nq, p.mult, slots * p.G, a, c->stream, d.family));
   if (c->timing) {
     MMP_CUDA(cudaEventRecord(e1, c->stream));
     c->pending.emplace_back(e0, e1);
@@ -766,6 +779,7 @@ struct AdjLayout {
 };
 
 int adjoint_layout(mmp_ctx* c, Prob& p, int ckpt_every, char* base, AdjLayout& L) {
+  if (p.d.family != MMP_FAMILY_POLY) return MMP_ERR_UNSUPPORTED;  // the adjoint is the polynomial drift's
   const long long J = (long long)p.d.N * p.nf;
   L.n_seg = (int)((J + ckpt_every - 1) / ckpt_every);
   const void* fn = adjoint_kernel(p.d.precision, p.mult);
@@ -793,7 +807,7 @@ int adjoint_layout(mmp_ctx* c, Prob& p, int ckpt_every, char* base, AdjLayout& L
   // too little work per step for the cross-CTA exchange they add.
   L.fG = 0;
   for (int nq = 1; nq <= max_nq; ++nq) {
-    const void* ff = fine_kernel(p.d.precision, kLayoutSmem, nq, p.mult);
+    const void* ff = fine_kernel(p.d.precision, kLayoutSmem, nq, p.mult, p.d.family);
     size_t flimit = 0;
     const int frc = allow_dynamic_smem(ff, c->dev.dev, &flimit);
     if (frc) return frc;
@@ -912,7 +926,7 @@ int mmp_create(mmp_ctx** out, const mmp_problem_desc* descs, int n_problems, voi
     if (e == cudaSuccess) e = cudaMemsetAsync(p.ctl, 0, sizeof(double) * 16, c->stream);
     if (e == cudaSuccess)
       e = launch_init_u0(p.d.precision, p.u0, p.d.P, p.Q, p.d.m0, p.d.s0, p.key0, p.key1,
-                         p.d.problem_tag, c->stream);
+                         p.d.problem_tag, p.d.family == MMP_FAMILY_ROTATOR, c->stream);
     c->other_launches += 1;
     if (e != cudaSuccess) {
       delete c;
@@ -1192,6 +1206,7 @@ int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta, int n_theta) {
   for (int k = 0; k < n_theta; ++k)
     if (!std::isfinite(theta[k])) return MMP_ERR_INVALID_ARG;
   Prob& p = ctx->probs[prob];
+  if (p.d.family != MMP_FAMILY_POLY) return MMP_ERR_UNSUPPORTED;  // the coefficients are the polynomial drift's
   const double B = n_theta == 7 ? theta[5] : p.d.B;
   const double BE = n_theta == 7 ? theta[6] : p.d.BE;
   const bool mult = B != 0.0 || BE != 0.0;
@@ -1199,7 +1214,7 @@ int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta, int n_theta) {
     // the fine kernel changes form: a batch shares one form, and a single
     // problem keeps its launch shape only if the other form fits it too
     if (ctx->batch) return MMP_ERR_UNSUPPORTED;
-    const void* fn = fine_kernel(p.d.precision, p.layout, p.nq, mult);
+    const void* fn = fine_kernel(p.d.precision, p.layout, p.nq, mult, p.d.family);
     if (fn == nullptr) return MMP_ERR_UNSUPPORTED;
     const size_t smem = fine_smem_bytes(p.d.precision, p.layout, p.nq);
     if (p.layout == kLayoutSmem) {
@@ -1516,7 +1531,7 @@ extern "C" int mmp_fine_static(const mmp_problem_desc* desc, int n, const void* 
   a.stats = stats; a.stats_fixed = 1;
   a.partials = base; a.flags = flags; a.tags = tags; a.status = status;
   a.tight_polls = p.G <= dev.sms ? kTightPolls : 0;
-  MMP_CUDA(launch_fine(p.d.precision, p.layout, p.nq, p.mult, p.G, a, s));
+  MMP_CUDA(launch_fine(p.d.precision, p.layout, p.nq, p.mult, p.G, a, s, p.d.family));
   if (stats_dev != nullptr) {
     k_status_to_stats<<<1, 1, 0, s>>>(status, stats_dev);
     MMP_CUDA(cudaGetLastError());
@@ -1609,7 +1624,8 @@ extern "C" int mmp_autotune(const mmp_problem_desc* desc, const int* candidates,
   const int nf = probe_steps > 0 ? std::min(probe_steps, p.nf) : std::min(p.nf, 64);
   cudaStream_t s = (cudaStream_t)stream;
   MMP_CUDA(cudaMemsetAsync(L.status, 0, sizeof(unsigned) * 4, s));
-  MMP_CUDA(launch_init_u0(p.d.precision, L.u0, p.d.P, p.Q, p.d.m0, p.d.s0, p.key0, p.key1, p.d.problem_tag, s));
+  MMP_CUDA(launch_init_u0(p.d.precision, L.u0, p.d.P, p.Q, p.d.m0, p.d.s0, p.key0, p.key1, p.d.problem_tag,
+                          p.d.family == MMP_FAMILY_ROTATOR, s));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   MMP_CUDA(cudaEventCreate(&e0));
   MMP_CUDA(cudaEventCreate(&e1));
@@ -1619,7 +1635,7 @@ extern "C" int mmp_autotune(const mmp_problem_desc* desc, const int* candidates,
   for (size_t ci = 0; ci < cand.size() && err == MMP_OK; ++ci) {
     double rate = 0.0;
     const int nq = cand[ci];
-    const void* fn = nq >= 1 && nq <= max_nq ? fine_kernel(p.d.precision, kLayoutSmem, nq, p.mult) : nullptr;
+    const void* fn = nq >= 1 && nq <= max_nq ? fine_kernel(p.d.precision, kLayoutSmem, nq, p.mult, p.d.family) : nullptr;
     size_t limit = 0;
     const size_t smem = fine_smem_bytes(p.d.precision, kLayoutSmem, nq);
     if (fn != nullptr && (err = allow_dynamic_smem(fn, dev.dev, &limit)) == MMP_OK && smem <= limit) {
@@ -1655,7 +1671,7 @@ extern "C" int mmp_autotune(const mmp_problem_desc* desc, const int* candidates,
         for (int rep = 0; rep < 2 && err == MMP_OK; ++rep) {  // warm-up, then timed
           ce = cudaMemsetAsync(L.tags, 0, sync, s);
           if (ce == cudaSuccess && rep == 1) ce = cudaEventRecord(e0, s);
-          if (ce == cudaSuccess) ce = launch_fine(p.d.precision, kLayoutSmem, nq, p.mult, t.slots_max * t.G, a, s);
+          if (ce == cudaSuccess) ce = launch_fine(p.d.precision, kLayoutSmem, nq, p.mult, t.slots_max * t.G, a, s, p.d.family);
           if (ce == cudaSuccess && rep == 1) ce = cudaEventRecord(e1, s);
           if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
           if (ce != cudaSuccess) err = cuda_fail(ce, "autotune launch", __LINE__);
@@ -1845,4 +1861,33 @@ extern "C" int mmp_set_state(mmp_ctx* ctx, const void* src) {
     if (rc) return rc;
   }
   return MMP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Self-test of the failure detection (mmp_probe_wait): one CTA of a G-CTA
+// group waits for peers that never publish; its bounded wait must run out.
+// ---------------------------------------------------------------------------
+int mmp_probe_wait(int channel, int G, double limit_ms, void* ws, size_t ws_bytes, void* stream,
+                   unsigned* status_out) {
+  if (channel != 0 && channel != 1) return MMP_ERR_INVALID_ARG;
+  if (G < 1 || G > 1024 || !(limit_ms >= 1.0) || !(limit_ms <= 10000.0)) return MMP_ERR_INVALID_ARG;
+  if (ws == nullptr || ((uintptr_t)ws % kAlign) != 0) return MMP_ERR_WORKSPACE;
+  // partials [G][kSlots][kNV] doubles, tags [kSlots][G], flags [G], status
+  const size_t part = sizeof(double) * (size_t)G * kSeatDoubles;
+  const size_t tagb = sizeof(unsigned long long) * (size_t)kSlots * G;
+  const size_t need = part + tagb + sizeof(unsigned) * ((size_t)G + 1);
+  if (ws_bytes < need) return MMP_ERR_WORKSPACE;
+  char* base = (char*)ws;
+  double* partials = (double*)base;
+  unsigned long long* tags = (unsigned long long*)(base + part);
+  unsigned* flags = (unsigned*)(base + part + tagb);
+  unsigned* status = flags + G;
+  cudaStream_t s = (cudaStream_t)stream;
+  MMP_CUDA(cudaMemsetAsync(tags, 0, need - part, s));
+  MMP_CUDA(launch_wait_probe(partials, flags, tags, status, G, (unsigned long long)(limit_ms * 1e6), channel, s));
+  unsigned st = 0;
+  MMP_CUDA(cudaMemcpyAsync(&st, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  MMP_CUDA(cudaStreamSynchronize(s));
+  if (status_out != nullptr) *status_out = st;
+  return (st & kStatusTimeout) ? MMP_ERR_TIMEOUT : MMP_OK;
 }

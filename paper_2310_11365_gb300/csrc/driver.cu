@@ -69,6 +69,7 @@ __device__ void macro_store(const DriverArgs& a, double* r, const Macro& m) {
 //     v' = 2 (-3 c3 v (m^2 + v) + c1 v) + B^2 v + (B m + BE M + B0)^2
 //   Taylor (Eq. moment_model_class_1): m' = a(m) + a_XX(m) v / 2,
 //     v' = (2 a_X(m) + B^2) v + b(m)^2
+//   Taylor1: the Taylor model without the v term of the mean
 //   sigma-point (Eq. Gaussian_model_McK_V_SDE with a k-point rule on
 //     N(m, v)): m' = E[a], v' = 2 E[(X - m) a] + E[b^2]; k = 2: m -+ sqrt(v),
 //     weights 1/2; k = 3: m, m -+ sqrt(3 v), weights 2/3, 1/6, 1/6.
@@ -80,28 +81,86 @@ __device__ double diffusion_at(const DriverArgs& a, double x, double M) {
   return a.B * x + a.BE * M + a.B0;
 }
 
+// Plane rotator (Sec. 5, Eq. SDE_plane_rotator; one region): drift
+// K (S cos x - C sin x) - g sin x with S, C the means of sin X, cos X under
+// each model's own law, additive noise B0:
+//   closure: X ~ N(m, v): S = sin m e^{-v/2}, C = cos m e^{-v/2};
+//     m' = K (S C - C S) - g S, and by Stein's lemma
+//     v' = 2 v (-K (S^2 + C^2) - g C) + B0^2;
+//   Taylor (Eq. moment_model_class_1 at the point mass m: S = sin m,
+//     C = cos m): m' = a(m) + a_XX(m) v / 2, v' = 2 a_X(m) v + B0^2, with
+//     a_X(m) = -K - g cos m (Eq. plane_rotator_third_order with the sign of
+//     its variance term as Eq. moment_model_class_1 gives it); Taylor1
+//     without the v term of the mean;
+//   sigma-point: the k-point rule for every expectation, S and C included.
+__device__ double rotator_drift_at(const DriverArgs& a, double x, double S, double C) {
+  return a.K * (S * cos(x) - C * sin(x)) - a.g * sin(x);
+}
+
+__device__ void sigma_points(int model, double m, double v, double* xs, double* ws, int& k) {
+  if (model == MMP_COARSE_SIGMA2) {
+    const double d = sqrt(v > 0.0 ? v : 0.0);
+    xs[0] = m - d; xs[1] = m + d;
+    ws[0] = 0.5; ws[1] = 0.5;
+    k = 2;
+  } else {
+    const double d = sqrt(3.0 * (v > 0.0 ? v : 0.0));
+    xs[0] = m; xs[1] = m - d; xs[2] = m + d;
+    ws[0] = 2.0 / 3.0; ws[1] = 1.0 / 6.0; ws[2] = 1.0 / 6.0;
+    k = 3;
+  }
+}
+
+__device__ void rotator_rhs(const DriverArgs& a, double m, double v, double& dm, double& dv) {
+  const double b2 = a.B0 * a.B0;
+  if (a.coarse_model == MMP_COARSE_TAYLOR || a.coarse_model == MMP_COARSE_TAYLOR1) {
+    const double S = sin(m), C = cos(m);
+    const double av = rotator_drift_at(a, m, S, C);
+    const double ax = a.K * (-S * sin(m) - C * cos(m)) - a.g * cos(m);
+    const double axx = a.K * (-S * cos(m) + C * sin(m)) + a.g * sin(m);
+    dm = a.coarse_model == MMP_COARSE_TAYLOR ? av + 0.5 * axx * v : av;
+    dv = 2.0 * ax * v + b2;
+  } else if (a.coarse_model == MMP_COARSE_SIGMA2 || a.coarse_model == MMP_COARSE_SIGMA3) {
+    double xs[3], ws[3];
+    int k;
+    sigma_points(a.coarse_model, m, v, xs, ws, k);
+    double S = 0.0, C = 0.0;
+    for (int s = 0; s < k; ++s) {
+      S += ws[s] * sin(xs[s]);
+      C += ws[s] * cos(xs[s]);
+    }
+    double ea = 0.0, exa = 0.0;
+    for (int s = 0; s < k; ++s) {
+      const double av = rotator_drift_at(a, xs[s], S, C);
+      ea += ws[s] * av;
+      exa += ws[s] * (xs[s] - m) * av;
+    }
+    dm = ea;
+    dv = 2.0 * exa + b2;
+  } else {
+    const double e = exp(-0.5 * v);
+    const double S = sin(m) * e, C = cos(m) * e;
+    dm = a.K * (S * C - C * S) - a.g * S;
+    dv = 2.0 * v * (-a.K * (S * S + C * C) - a.g * C) + b2;
+  }
+}
+
 __device__ void coarse_rhs(const DriverArgs& a, double m, double v, double M, double& dm, double& dv) {
+  if (a.family == MMP_FAMILY_ROTATOR) {
+    rotator_rhs(a, m, v, dm, dv);
+    return;
+  }
   const double c3 = -a.nc3;
-  if (a.coarse_model == MMP_COARSE_TAYLOR) {
+  if (a.coarse_model == MMP_COARSE_TAYLOR || a.coarse_model == MMP_COARSE_TAYLOR1) {
     const double ax = -3.0 * c3 * m * m + a.c1;
     const double axx = -6.0 * c3 * m;
     const double b = diffusion_at(a, m, M);
-    dm = drift_at(a, m, M) + 0.5 * axx * v;
+    dm = drift_at(a, m, M) + (a.coarse_model == MMP_COARSE_TAYLOR ? 0.5 * axx * v : 0.0);
     dv = (2.0 * ax + a.B * a.B) * v + b * b;
   } else if (a.coarse_model == MMP_COARSE_SIGMA2 || a.coarse_model == MMP_COARSE_SIGMA3) {
     double xs[3], ws[3];
     int k;
-    if (a.coarse_model == MMP_COARSE_SIGMA2) {
-      const double d = sqrt(v > 0.0 ? v : 0.0);
-      xs[0] = m - d; xs[1] = m + d;
-      ws[0] = 0.5; ws[1] = 0.5;
-      k = 2;
-    } else {
-      const double d = sqrt(3.0 * (v > 0.0 ? v : 0.0));
-      xs[0] = m; xs[1] = m - d; xs[2] = m + d;
-      ws[0] = 2.0 / 3.0; ws[1] = 1.0 / 6.0; ws[2] = 1.0 / 6.0;
-      k = 3;
-    }
+    sigma_points(a.coarse_model, m, v, xs, ws, k);
     double ea = 0.0, exa = 0.0, eb2 = 0.0;
     for (int s = 0; s < k; ++s) {
       const double av = drift_at(a, xs[s], M);

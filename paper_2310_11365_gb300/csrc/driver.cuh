@@ -7,6 +7,8 @@ namespace mmp {
 
 struct DriverArgs {
   double nc3, c1, kappa, c0, B, BE, B0;  // model (nc3 = -c3)
+  int family;                            // MMP_FAMILY_POLY / MMP_FAMILY_ROTATOR
+  double K, g;                           // plane rotator: coupling, pinning
   int N, I, variant, precision;
   int coarse_model;                      // MMP_COARSE_*
   double dT, hc;                         // slice length, coarse substep

@@ -11,6 +11,8 @@ namespace mmp {
 struct FineArgs {
   // drift a(x, m) = nc3 x^3 + c1 x + kappa m + c0 (nc3 = -c3), diffusion b = B x + BE m + B0
   double nc3, c1, kappa, c0, B, BE, B0;
+  // plane rotator (family kFamRotator): a(x) = K (S cos x - C sin x) - g sin x, b = B0
+  double K = 0.0, gpin = 0.0;
   double h, sqrt_h;            // fine step and its square root
   int nf;                      // steps per slice (0: matching + restriction only)
   long long P;                 // particles
@@ -49,12 +51,13 @@ struct FineArgs {
 constexpr int kLayoutRegs = 0;
 constexpr int kLayoutSmem = 1;
 
-// Handle of one kernel instantiation (nq ignored for the shared layout).
-const void* fine_kernel(int precision, int layout, int nq, bool mult);
+// Handle of one kernel instantiation (nq ignored for the shared layout;
+// the plane rotator has the shared layout only, nullptr otherwise).
+const void* fine_kernel(int precision, int layout, int nq, bool mult, int family = 0);
 // Dynamic shared memory of a launch.
 size_t fine_smem_bytes(int precision, int layout, int nq);
 // Cooperative launch of the instantiation (grid = slots * G CTAs).
 cudaError_t launch_fine(int precision, int layout, int nq, bool mult, int grid, const FineArgs& args,
-                        cudaStream_t stream);
+                        cudaStream_t stream, int family = 0);
 
 }  // namespace mmp

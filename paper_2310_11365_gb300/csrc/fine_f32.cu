@@ -9,7 +9,8 @@ namespace mmp {
     return mult ? (const void*)k_fine<float, NQ, true>            \
                 : (const void*)k_fine<float, NQ, false>;
 
-const void* fine_kernel_f32(int nq, bool mult) {
+const void* fine_kernel_f32(int nq, bool mult, int family) {
+  if (family == kFamRotator) return nq == 0 ? (const void*)k_fine<float, 0, false, kFamRotator> : nullptr;
   if (nq == 0)
     return mult ? (const void*)k_fine<float, 0, true> : (const void*)k_fine<float, 0, false>;
   switch (nq) {

@@ -1,6 +1,7 @@
 // fine_kernel.cuh -- the fused fine-propagator kernel, templated on the
 // particle precision R (float or double), the quads of particles held per
-// thread NQ, and whether the diffusion depends on the state (MULT).
+// thread NQ, whether the diffusion depends on the state (MULT), and the
+// drift family FAM (the polynomial drift, or the plane rotator of Sec. 5).
 //
 // One slice of the Parareal sweep is one "task".  A task's P particles are
 // split over a group of G co-resident CTAs (the launch is cooperative, so
@@ -72,6 +73,9 @@ struct GroupShared {
   float afff[kMaxRegions][3]; // the task's matching records (a, b, c) per region, float particles
   double affd[kMaxRegions][3];// the same for double particles
   int amode[kMaxRegions];     // their modes
+  float cr[2];                // plane rotator: K, g as floats
+  double rotd[2];             // plane rotator: ensemble means of sin X, cos X before a step
+  float rotf[2];              // the same rounded to float
   int abort;
 };
 
@@ -266,6 +270,8 @@ __device__ __forceinline__ float addR(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ double addR(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float mulR(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mulR(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float subR(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double subR(double a, double b) { return __dsub_rn(a, b); }
 
 // The part of one Euler-Maruyama step that does not depend on the mean, for
 // the two particles that share a Box-Muller pair (normals nr (c | s)):
@@ -499,12 +505,20 @@ struct FineOccupancy {
 // Either way one CTA barrier per step: every warp forms the CTA sum from
 // the per-warp partials and the group sum from the published slots itself,
 // in the same order, so all warps hold the same values.
-template <typename R, int NQ, bool MULT, int STEP_UNROLL>
+//
+// * plane rotator (FAM == kFamRotator, Sec. 5 Eq. SDE_plane_rotator): the
+//   drift K (S cos x - C sin x) - g sin x needs the ensemble means S, C of
+//   sin X and cos X of the step's own state, so step j + 1 waits for the two
+//   group sums of step j (record channel, FP64); after the update each
+//   particle is shifted modulo 2 pi into [-pi, pi], and its sine and cosine
+//   enter the next step's sums.
+template <typename R, int NQ, bool MULT, int STEP_UNROLL, int FAM = kFamPoly>
 __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const int g, Group& grp,
                                           GroupShared& sh, QuadStore<R, NQ>& xs) {
   using SS = StepSum<R>;
   using ST = typename SS::T;
-  constexpr bool kLag = !MULT;
+  constexpr bool kRot = FAM == kFamRotator;
+  constexpr bool kLag = !MULT && !kRot;
   constexpr int kUnroll = NQ > 0 ? NQ : 2;             // prologue and epilogue
   constexpr int kStepUnroll = NQ > 0 ? NQ : STEP_UNROLL;
   const int G = a.G;
@@ -548,6 +562,8 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
     sh.cf[13] = (float)(a.h * a.c1);
     sh.cf[14] = (float)a.thr2;
     sh.cf[15] = (float)a.thr3;
+    sh.cr[0] = (float)a.K;
+    sh.cr[1] = (float)a.gpin;
   }
   if (tid < kMaxRegions) {
     // this slice's matching record of region tid (identity past n_regions)
@@ -580,6 +596,8 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   const R hc1 = fl ? (R)sh.cf[13] : (R)(a.h * a.c1);
   const R thr2 = fl ? (R)sh.cf[14] : (R)a.thr2;
   const R thr3 = fl ? (R)sh.cf[15] : (R)a.thr3;
+  const R Kr = fl ? (R)sh.cr[0] : (R)a.K;      // plane rotator only
+  const R gr = fl ? (R)sh.cr[1] : (R)a.gpin;
   const int nreg = a.n_regions;
   auto region = [&](R x) { return region_of<R>(x, nreg, thr, thr2, thr3); };
   auto aff_param = [&](int r, int k) -> R { return fl ? (R)sh.afff[r][k] : (R)sh.affd[r][k]; };
@@ -591,6 +609,7 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   // ---------------- prologue: load, match, sum --------------------------
   int flips = 0;
   R s_in = (R)0;
+  R s_sin = (R)0, s_cos = (R)0;  // plane rotator: sums of sin x, cos x of the inputs
   // The matching records of this task's regions sit in registers (NR of
   // them, loops over regions unrolled); with at most two regions the region
   // of x is one comparison.
@@ -668,6 +687,18 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
           if (plast < 2) v[1] = (R)0;
         }
         s_in = addR(s_in, addR(addR(v[0], v[1]), addR(v[2], v[3])));
+        if constexpr (kRot) {
+          const int valid = q == qlast ? plast : 4;
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            if (w < valid) {
+              R sn, cn;
+              sincosR(v[w], &sn, &cn);
+              s_sin = addR(s_sin, sn);
+              s_cos = addR(s_cos, cn);
+            }
+          }
+        }
       }
       xs.put(i, v);
     }
@@ -683,6 +714,36 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   // CTA barrier it publishes the CTA's sum of the step just finished, and
   // before the next barrier it reads the group sum that the other warps need
   // after it (through sh.gsum).
+  double m_in = 0.0;
+  R d = (R)0;                  // shift form: the pending shift d_{j-1}
+  R base = (R)0, boff = (R)0;  // general form: kappa m_j + c0, (BE m_j + B0) sqrt(h)
+  R mj = (R)0;                 // general form: m_j (recorded for the adjoint)
+  // Plane rotator: the group sums of (sin x, cos x, x) of the inputs; warp 0
+  // leaves the means of sin and cos in sh.rotd / sh.rotf for every thread.
+  auto rot_exchange = [&](int nv, double v0, double v1, double v2) -> bool {
+    double v[3] = {v0, v1, v2};
+    if (nv == 3) warp_reduce_to_shared<3>(sh, v, 0u, 0u);
+    else warp_reduce_to_shared<2>(sh, v, 0u, 0u);
+    __syncthreads();
+    const unsigned e = grp.epoch++;
+    if (warp == 0) {
+      const bool ok = nv == 3 ? group_finish<3>(sh, grp, e, 0u, 0u) : group_finish<2>(sh, grp, e, 0u, 0u);
+      if (lane == 0) {
+        if (!ok) sh.abort = 1;
+        const double S = sh.tot[0] / (double)a.P, C = sh.tot[1] / (double)a.P;
+        sh.rotd[0] = S;
+        sh.rotd[1] = C;
+        sh.rotf[0] = (float)S;
+        sh.rotf[1] = (float)C;
+      }
+    }
+    __syncthreads();
+    return !sh.abort;
+  };
+  if constexpr (kRot) {
+    if (!rot_exchange(3, (double)s_sin, (double)s_cos, (double)s_in)) return false;
+    m_in = sh.tot[2] / (double)a.P;
+  } else {
   step_sum_warp<R>(sh, 1, s_in);
   __syncthreads();
   if (warp == 0) {
@@ -690,11 +751,8 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
     if (lane == 0) SS::publish(grp, E, cta);
   }
   grp.epoch = E + 1u;
-  double m_in = 0.0;
-  R d = (R)0;                  // shift form: the pending shift d_{j-1}
-  R base = (R)0, boff = (R)0;  // general form: kappa m_j + c0, (BE m_j + B0) sqrt(h)
-  R mj = (R)0;                 // general form: m_j (recorded for the adjoint)
-  if (!kLag || nf == 0) {
+  }
+  if (!kRot && (!kLag || nf == 0)) {
     if (warp == 0) {
       ST sum;
       const bool ok = SS::fetch(grp, E, sum);
@@ -713,6 +771,43 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   }
 
   // ---------------- Euler-Maruyama steps --------------------------------
+  if constexpr (kRot) {
+    for (int j = 0; j < nf; ++j) {
+      // x <- wrap(x + h (K (S cos x - C sin x) - g sin x) + B0 sqrt(h) xi)
+      const R sb = fl ? (R)sh.rotf[0] : (R)sh.rotd[0];
+      const R cb = fl ? (R)sh.rotf[1] : (R)sh.rotd[1];
+      const bool more = j + 1 < nf;  // the last step's sums are not needed
+      R ss = (R)0, cs = (R)0;
+#pragma unroll kStepUnroll
+      for (int i = 0; i < loop_n; ++i) {
+        if (i < nq) {
+          const int q = qb + tid + i * kTPB;
+          R v[4];
+          xs.get(i, v);
+          const uint4 o = philox4x32_10(rng_counter((uint32_t)q, (uint32_t)j, (uint32_t)n, 0u, a.ptag), a.key0,
+                                        a.key1);
+          R z[4];
+          normals4<R>(o, z);
+          const int valid = q == qlast ? plast : 4;
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            R sn, cn;
+            sincosR(v[w], &sn, &cn);
+            const R drift = subR(mulR(Kr, subR(mulR(sb, cn), mulR(cb, sn))), mulR(gr, sn));
+            const R xn = wrap_angle(addR(addR(v[w], mulR(drift, h)), mulR(b0sq, z[w])));
+            v[w] = xn;
+            if (more && w < valid) {
+              sincosR(xn, &sn, &cn);
+              ss = addR(ss, sn);
+              cs = addR(cs, cn);
+            }
+          }
+          xs.put(i, v);
+        }
+      }
+      if (more && !rot_exchange(2, (double)ss, (double)cs, 0.0)) return false;
+    }
+  } else
   for (int j = 0; j < nf; ++j) {
     const long long gs = a.step_offset + j;
     const bool ckpt = a.rec_ckpt != nullptr && gs % a.ckpt_every == 0;
@@ -1006,7 +1101,7 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
   return true;
 }
 
-template <typename R, int NQ, bool MULT>
+template <typename R, int NQ, bool MULT, int FAM = kFamPoly>
 __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, NQ>::value)) k_fine(const FineArgs a) {
   __shared__ GroupShared sh;
   const int G = a.G;
@@ -1028,7 +1123,7 @@ __global__ void __launch_bounds__(kTPB, (FineOccupancy<R, NQ>::value)) k_fine(co
   QuadStore<R, NQ> xs;
   xs.bind();
   for (int task = slot; task < a.n_tasks; task += n_slots) {
-    if (!fine_task<R, NQ, MULT, kStepUnrollSmem>(a, a.slice_begin + task, g, grp, sh, xs)) return;
+    if (!fine_task<R, NQ, MULT, kStepUnrollSmem, FAM>(a, a.slice_begin + task, g, grp, sh, xs)) return;
   }
 }
 

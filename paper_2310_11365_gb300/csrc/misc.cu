@@ -7,16 +7,19 @@ namespace mmp {
 
 // X0 = m0 + s0 z with z the tag-1 normals; evaluated in FP64 and rounded to
 // the particle type, so MMP_MIXED starts from the rounded FP64 ensemble.
+// The plane rotator (wrap) shifts it into [-pi, pi] in FP64 first.
 template <typename R>
 __global__ void k_init_u0(R* u0, long long P, int Q, double m0, double s0, uint32_t k0, uint32_t k1,
-                          uint32_t ptag) {
+                          uint32_t ptag, int wrap) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
     double z[4];
     normals4<double>(philox4x32_10(rng_counter((uint32_t)q, 0u, 0u, 1u, ptag), k0, k1), z);
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
       const long long p = 4LL * q + w;
-      u0[p] = p < P ? (R)(m0 + s0 * z[w]) : (R)0;
+      double x = __dadd_rn(m0, __dmul_rn(s0, z[w]));
+      if (wrap) x = wrap_angle(x);
+      u0[p] = p < P ? (R)x : (R)0;
     }
   }
 }
@@ -48,12 +51,12 @@ static int grid_for(long long items, int block) {
 }
 
 cudaError_t launch_init_u0(int precision, void* u0, long long P, int Q, double m0, double s0,
-                           uint32_t k0, uint32_t k1, uint32_t ptag, cudaStream_t s) {
+                           uint32_t k0, uint32_t k1, uint32_t ptag, int wrap, cudaStream_t s) {
   const int grid = grid_for(Q, 256);
   if (precision == MMP_MIXED)
-    k_init_u0<float><<<grid, 256, 0, s>>>((float*)u0, P, Q, m0, s0, k0, k1, ptag);
+    k_init_u0<float><<<grid, 256, 0, s>>>((float*)u0, P, Q, m0, s0, k0, k1, ptag, wrap);
   else
-    k_init_u0<double><<<grid, 256, 0, s>>>((double*)u0, P, Q, m0, s0, k0, k1, ptag);
+    k_init_u0<double><<<grid, 256, 0, s>>>((double*)u0, P, Q, m0, s0, k0, k1, ptag, wrap);
   return cudaGetLastError();
 }
 

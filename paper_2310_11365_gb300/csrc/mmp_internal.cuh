@@ -28,6 +28,8 @@ constexpr int kMomM = 6, kMomV = 7;        // global mean, variance in a moment 
 constexpr int kStatM = 10, kStatV = 11;    // global mean, variance in a restriction record
 constexpr int kStatFlips = 12, kStatInMean = 13;
 constexpr int kMaxNQ = 8;          // largest quads-per-thread template
+constexpr int kFamPoly = MMP_FAMILY_POLY;
+constexpr int kFamRotator = MMP_FAMILY_ROTATOR;
 
 // Polls of a bounded group wait before it backs off with nanosleep, for
 // launches with at most one CTA per SM: a word about to land is then picked
@@ -176,6 +178,22 @@ __device__ __forceinline__ float apply_affine(float x, float delta, float sm1, f
 __device__ __forceinline__ double apply_affine(double x, double delta, double sm1, double m) {
   return __dadd_rn(x, __fma_rn(sm1, __dsub_rn(x, m), delta));
 }
+
+// ---------------------------------------------------------------------------
+// The plane rotator's shift of x modulo 2 pi into [-pi, pi]:
+// x - 2 pi floor((x + pi) / (2 pi)), each operation rounded once (FP64: the
+// division, as written; FP32: a product with 1 / (2 pi) rounded to float).
+// ---------------------------------------------------------------------------
+constexpr double kPi = 3.141592653589793238462643383280;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+__device__ __forceinline__ double wrap_angle(double x) {
+  return __dsub_rn(x, __dmul_rn(kTwoPi, floor(__ddiv_rn(__dadd_rn(x, kPi), kTwoPi))));
+}
+__device__ __forceinline__ float wrap_angle(float x) {
+  return __fsub_rn(x, __fmul_rn((float)kTwoPi, floorf(__fmul_rn(__fadd_rn(x, (float)kPi), (float)(1.0 / kTwoPi)))));
+}
+__device__ __forceinline__ void sincosR(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincosR(double x, double* s, double* c) { sincos(x, s, c); }
 
 // ---------------------------------------------------------------------------
 // Memory-model helpers for the cross-CTA group barrier.

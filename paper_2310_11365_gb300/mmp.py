@@ -49,7 +49,7 @@ EXPORTED = [
     "mmp_normals", "mmp_get_plan", "mmp_set_timing", "mmp_timing", "mmp_fine_static",
     "mmp_set_params", "mmp_adjoint_workspace_size", "mmp_adjoint_forward", "mmp_adjoint_backward", "mmp_adjoint",
     "mmp_batch_info", "mmp_autotune_workspace_size", "mmp_autotune", "mmp_set_tuning", "mmp_set_batch_nq",
-    "mmp_state_size", "mmp_get_state", "mmp_set_state",
+    "mmp_state_size", "mmp_get_state", "mmp_set_state", "mmp_probe_wait",
 ]
 
 
@@ -76,6 +76,7 @@ class ProblemDesc(C.Structure):
         ("variant", C.c_int), ("precision", C.c_int), ("seed", C.c_ulonglong),
         ("problem_tag", C.c_uint), ("tol", C.c_double), ("max_iter", C.c_int), ("coarse_model", C.c_int),
         ("threshold2", C.c_double), ("threshold3", C.c_double),
+        ("family", C.c_int), ("K", C.c_double), ("g", C.c_double),
     ]
 
 
@@ -127,6 +128,7 @@ def load():
         "mmp_state_size": ([vp, C.POINTER(C.c_size_t)], i),
         "mmp_get_state": ([vp, vp], i),
         "mmp_set_state": ([vp, vp], i),
+        "mmp_probe_wait": ([i, i, C.c_double, vp, C.c_size_t, vp, C.POINTER(C.c_uint)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -142,15 +144,14 @@ def _check(rc: int, where: str):
 
 
 def desc(p: workloads.Problem) -> ProblemDesc:
-    """The C descriptor of a problem record; refuses drift families the kernels do not run."""
-    if p.family != workloads.POLY or p.q2 != 0.0:
-        # the library's kernels propagate the polynomial drift family without
-        # the second-moment coupling only
+    """The C descriptor of a problem record; refuses the terms the kernels do not run."""
+    if p.q2 != 0.0:
+        # the library's kernels do not carry the second-moment coupling
         raise MMPError(-3, "desc")
     prec = MMP_MIXED if p.precision == "mixed" else MMP_FP64
     return ProblemDesc(p.c3, p.c1, p.kappa, p.c0, p.B, p.BE, p.B0, p.m0, p.s0, p.T, p.N, p.dt, p.P,
                        p.coarse_h, p.n_regions, p.threshold, p.variant, prec, p.seed, p.problem_tag,
-                       p.tol, p.max_iter, p.coarse_model, p.threshold2, p.threshold3)
+                       p.tol, p.max_iter, p.coarse_model, p.threshold2, p.threshold3, p.family, p.K, p.g)
 
 
 def _descs(problems) -> C.Array:
@@ -337,6 +338,14 @@ def mmp_set_state(ctx, blob: bytes) -> None:
     """Restores a checkpoint taken by mmp_get_state into a context over the same problems."""
     buf = C.create_string_buffer(blob, len(blob))
     _check(load().mmp_set_state(ctx, buf), "mmp_set_state")
+
+
+def mmp_probe_wait(channel: int, G: int, limit_ms: float, ws_ptr: int, ws_bytes: int, stream=None):
+    """Self-test of the bounded group wait: (return code, status word); the
+    code is MMP_ERR_TIMEOUT (-6) when the wait ran out as it must for G >= 2."""
+    st = C.c_uint()
+    rc = load().mmp_probe_wait(channel, G, float(limit_ms), ws_ptr, ws_bytes, _stream_handle(stream), C.byref(st))
+    return rc, st.value
 
 
 def mmp_fine_static(p: workloads.Problem, n: int, u_in_ptr: int, u_out_ptr: int, stats_ptr: int | None,

@@ -107,12 +107,46 @@ def test_workspace_checked_before_any_device_work(mmplib):
     assert lib.mmp_get_moments(None, 0, v) == -1
 
 
-def test_plane_rotator_is_refused_by_the_library(mmplib):
-    """The plane rotator (a drift family only the oracle propagates) never
-    reaches the library as a polynomial problem: the binding refuses it."""
+def test_plane_rotator_descriptors_checked_on_the_host(mmplib):
+    """The plane rotator (family MMP_FAMILY_ROTATOR) has additive noise and
+    one region: a state-dependent diffusion is refused as invalid, more
+    regions as unsupported, an unknown family or coarse model as invalid, all
+    before any device work.  The second-moment coupling of App. C is refused
+    by the binding (the kernels do not carry it)."""
+    lib = mmplib.load()
+    n = C.c_size_t()
+
+    def rc(p, **fields):
+        d = mmplib.desc(p)
+        for k, v in fields.items():
+            setattr(d, k, v)
+        return lib.mmp_workspace_size(C.byref(d), 1, C.byref(n))
+
+    r = W.plane_rotator(P=1000)
+    assert rc(r, B=0.5) == -1
+    assert rc(r, BE=0.5) == -1
+    assert rc(r, n_regions=2, threshold=0.0) == -3
+    assert rc(r, family=2) == -1
+    assert rc(r, coarse_model=5) == -1
+    assert rc(r, K=float("nan")) == -1
     with pytest.raises(mmplib.MMPError) as e:
-        mmplib.mmp_workspace_size([W.plane_rotator(P=1000)])
+        mmplib.desc(W.polynomial_drift())
     assert e.value.code == -3
+
+
+def test_probe_wait_arguments_checked_on_the_host(mmplib):
+    """The failure-detection self-test refuses an unknown channel, a group
+    size or wait limit out of range, and a NULL, misaligned or short
+    scratch, before any device work."""
+    lib = mmplib.load()
+    assert lib.mmp_probe_wait(2, 2, 20.0, 4096, 1 << 16, None, None) == -1
+    assert lib.mmp_probe_wait(0, 0, 20.0, 4096, 1 << 16, None, None) == -1
+    assert lib.mmp_probe_wait(0, 1025, 20.0, 4096, 1 << 20, None, None) == -1
+    assert lib.mmp_probe_wait(0, 2, 0.5, 4096, 1 << 16, None, None) == -1
+    assert lib.mmp_probe_wait(0, 2, 2e4, 4096, 1 << 16, None, None) == -1
+    assert lib.mmp_probe_wait(0, 2, 20.0, None, 1 << 16, None, None) == -2
+    assert lib.mmp_probe_wait(0, 2, 20.0, 4096 + 16, 1 << 16, None, None) == -2
+    assert lib.mmp_probe_wait(0, 2, 20.0, 4096, 2 * 548 + 3, None, None) == -2
 
 
 def test_normals_arguments_checked_on_the_host(mmplib):

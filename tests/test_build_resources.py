@@ -24,8 +24,9 @@ def _select(usage, pattern):
 
 
 @pytest.mark.parametrize("pattern,what", [
-    (r"_ZN3mmp6k_fineIfLi0ELb[01]EEEvNS_8FineArgsE", "mixed fine kernels (shared-memory layout, both noise forms)"),
-    (r"_ZN3mmp6k_fineIdLi0ELb[01]EEEvNS_8FineArgsE", "FP64 fine kernels (shared-memory layout, both noise forms)"),
+    (r"_ZN3mmp6k_fineIfLi0ELb[01]ELi0EEEvNS_8FineArgsE", "mixed fine kernels (shared-memory layout, both noise forms)"),
+    (r"_ZN3mmp6k_fineIdLi0ELb[01]ELi0EEEvNS_8FineArgsE", "FP64 fine kernels (shared-memory layout, both noise forms)"),
+    (r"_ZN3mmp6k_fineI[fd]Li0ELb0ELi1EEEvNS_8FineArgsE", "plane-rotator fine kernels (mixed and FP64)"),
     (r"_ZN3mmp12k_fine_batchIfLb[01]EEEvNS_9BatchArgsE", "mixed batched fine kernels"),
     (r"_ZN3mmp9k_adjointI[fd]Lb[01]EEEvNS_11AdjointArgsE", "adjoint reverse kernels"),
 ])
