@@ -96,3 +96,39 @@ def test_non_finite_values_are_reported(mmplib, orc, prec):
     assert ok.run() >= 1
     assert ok.status()["dev_err"] == 0
     ok.close()
+
+
+@pytest.mark.parametrize("channel", [0, 1])
+def test_bounded_wait_runs_out_and_the_device_stays_usable(mmplib, orc, channel):
+    """Failure detection of the group exchange: one CTA of a two-CTA group
+    waits for a peer that never publishes (channel 0: the epoch-flag records;
+    channel 1: the tagged step words of float particles).  The wait gives up
+    after its 20 ms limit, sets the timeout bit and returns MMP_ERR_TIMEOUT;
+    a group of one waits for nobody; the library then solves a healthy
+    problem."""
+    import time
+
+    import torch
+
+    from paper_2310_11365_gb300.mmp import Solver
+
+    ws = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
+    t0 = time.perf_counter()
+    rc, st = mmplib.mmp_probe_wait(channel, 2, 20.0, ws.data_ptr(), ws.numel())
+    waited = time.perf_counter() - t0
+    assert rc == -6 and st & 1, (rc, st)
+    assert 0.015 < waited < 5.0, waited
+    assert mmplib.mmp_probe_wait(channel, 1, 20.0, ws.data_ptr(), ws.numel()) == (0, 0)
+    # argument checks before any launch
+    assert mmplib.mmp_probe_wait(2, 2, 20.0, ws.data_ptr(), ws.numel())[0] == -1
+    assert mmplib.mmp_probe_wait(channel, 2, 0.5, ws.data_ptr(), ws.numel())[0] == -1
+    assert mmplib.mmp_probe_wait(channel, 2, 20.0, ws.data_ptr() + 16, ws.numel())[0] == -2
+    assert mmplib.mmp_probe_wait(channel, 64, 20.0, ws.data_ptr(), 1024)[0] == -2
+    p = _healthy()
+    s = Solver(p)
+    k = s.run()
+    ref = orc.parareal(p)
+    assert k == ref["sweeps"] and s.status()["dev_err"] == 0
+    M, V = ref["hist"][-1][p.N]
+    assert abs(s.moments()[p.N, 6] - M) <= 1e-10 * max(abs(M), np.sqrt(V))
+    s.close()
