@@ -376,6 +376,60 @@ int mmp_philox(const unsigned int* ctr, const unsigned int* key, unsigned int* o
 int mmp_normals(const mmp_problem_desc* desc, int tag, unsigned int j, unsigned int n,
                 long long count, void* out, void* stream);
 
+/* Counters of the device-side iteration of problem `prob` (the paper has
+ * no counterpart; for diagnosing convergence): out[0] regions accepted by
+ * the iterator (Defs. 3.1, 3.2), summed over slices and sweeps since the
+ * lift; out[1] regions rejected; out[2] 1 if the last sweep used learned
+ * fractions (Def. 3.4); out[3], out[4] the two-region fit (alpha, beta) of
+ * that sweep; out[5] the change max_n max(|dM|, |dV|) of that sweep.  out:
+ * host, 6 doubles.  Synchronising. */
+int mmp_sweep_info(mmp_ctx* ctx, int prob, double* out);
+
+/* Throughput of fused multiply-adds on this device in FP64 (precision
+ * MMP_FP64) or FP32 (MMP_MIXED), in TFLOP/s (2 flops per FMA): one launch of
+ * 4 CTAs per SM whose threads run 8 independent FMA chains, timed with CUDA
+ * events after a warm-up launch.  The plain FP64 form is measured against
+ * it (the paper has no counterpart).  ws: device, 256-byte aligned, 8 bytes
+ * at least (a sink the kernel never writes in practice).  Synchronising. */
+int mmp_probe_fma(int precision, void* ws, size_t ws_bytes, void* stream, double* tflops);
+
+/* One problem's slices on several GPUs.  Within a Parareal iteration the
+ * fine propagations of the slices are independent (Sec. 3.1: the parallel
+ * step of Parareal), so the slices can be split into contiguous blocks, one
+ * per GPU (rank), each rank holding a context over the whole problem.  A
+ * sweep k (Eq. mM_parareal_other_k_NEW) then runs in two phases:
+ *
+ * mmp_sweep_fine: the fine propagations F_n(u^{k-1}_n), matching fused, of
+ *   the slices n in [max(k - 1, n_lo), n_hi) (slices before k - 1 are exact,
+ *   Property 3.3).  Slice n reads the fine output of slice n - 1 of sweep
+ *   k - 1, so a rank whose block starts at n_lo >= k needs that row from the
+ *   previous rank first (mmp_set_output).  Asynchronous.  Not for batched
+ *   contexts (MMP_ERR_UNSUPPORTED); MMP_ERR_STATE before mmp_lift, after the
+ *   problem stopped, or when a fine phase already waits for its driver.
+ * mmp_sweep_coarse: the driver of sweep k (the sequential coarse sweep, the
+ *   iterator, the matching records, the convergence test) over all N slices,
+ *   from the restriction records of all of them, which must therefore be in
+ *   place (mmp_set_records).  On every rank the same inputs give the same
+ *   results bit for bit.  *done (optional) = 1 when the problem stopped.
+ *   Synchronising; returns a device-side error like mmp_iterate.
+ * mmp_get_records / mmp_set_records: restriction records of the fine
+ *   outputs of slices [n_lo, n_hi) (MMP_STAT_STRIDE doubles each, host
+ *   memory), to gather them on every rank between the phases.  Synchronising.
+ * mmp_get_output / mmp_set_output: the P values of the fine output of slice
+ *   n written by the latest fine phase (dst / src in host memory if to_host /
+ *   from_host, else device memory; host copies synchronise).  After sweep k
+ *   the rank that propagated slice n_hi - 1 sends it to the rank whose block
+ *   starts at n_hi, which sets it before its fine phase of sweep k + 1.
+ *   MMP_ERR_STATE before the first fine phase.
+ * mmp_iterate is refused (MMP_ERR_STATE) while a fine phase waits for its
+ * driver, and so is mmp_get_state. */
+int mmp_sweep_fine(mmp_ctx* ctx, int prob, int n_lo, int n_hi);
+int mmp_sweep_coarse(mmp_ctx* ctx, int prob, int* done);
+int mmp_get_records(mmp_ctx* ctx, int prob, int n_lo, int n_hi, double* out);
+int mmp_set_records(mmp_ctx* ctx, int prob, int n_lo, int n_hi, const double* in);
+int mmp_get_output(mmp_ctx* ctx, int prob, int n, void* dst, int to_host);
+int mmp_set_output(mmp_ctx* ctx, int prob, int n, const void* src, int from_host);
+
 /* Self-test of the failure detection of the fine kernel's group exchange
  * (the paper has no counterpart; a property of the library).  Launches one
  * CTA of a group of G CTAs on `stream`; it runs the kernel's own group

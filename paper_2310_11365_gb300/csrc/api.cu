@@ -20,6 +20,7 @@
 static_assert(mmp::kNGrad == MMP_N_THETA, "adjoint gradient length");
 
 namespace mmp {
+cudaError_t launch_fma_probe(int precision, void* sink, long long iters, int grid, cudaStream_t stream);
 cudaError_t launch_wait_probe(double* partials, unsigned* flags, unsigned long long* tags, unsigned* status, int G,
                               unsigned long long limit_ns, int channel, cudaStream_t stream);
 const void* fine_kernel_f32(int nq, bool mult, int family);
@@ -110,6 +111,7 @@ struct Prob {
   bool lifted = false, done = false, converged = false;
   double last_change = 0.0;
   std::vector<int> out_buf;  // which B buffer holds the latest F_n output of slice n
+  int fine_pending = 0;      // sweep whose fine phase ran alone (mmp_sweep_fine), awaiting its driver
   // adjoint state: the forward run recorded into adj_ws
   bool adj_ready = false;
   void* adj_ws = nullptr;
@@ -976,6 +978,7 @@ int mmp_lift(mmp_ctx* ctx) {
     p.done = false;
     p.converged = false;
     p.last_change = 0.0;
+    p.fine_pending = 0;
     std::fill(p.out_buf.begin(), p.out_buf.end(), -1);
   }
   if (ctx->batch)
@@ -986,7 +989,7 @@ int mmp_lift(mmp_ctx* ctx) {
 int mmp_iterate(mmp_ctx* ctx, int n_iter, int* all_converged) {
   if (ctx == nullptr || n_iter < 0) return MMP_ERR_INVALID_ARG;
   for (Prob& p : ctx->probs)
-    if (!p.lifted) return MMP_ERR_STATE;
+    if (!p.lifted || p.fine_pending != 0) return MMP_ERR_STATE;
   if (ctx->batch) {
     // sweeps are built and run on the device, kGraphSweeps per graph launch;
     // the host reads the problems' summaries once per launch
@@ -1106,6 +1109,115 @@ int mmp_iterate(mmp_ctx* ctx, int n_iter, int* all_converged) {
     for (Prob& p : ctx->probs) all = all && p.done;
     *all_converged = all ? 1 : 0;
   }
+  return MMP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// A sweep in two phases, for running one problem's slices on several GPUs
+// (each rank propagates a contiguous block of slices; the restriction
+// records are gathered on every rank, the driver runs redundantly, and the
+// fine output at the end of a block is handed to the next rank).
+// ---------------------------------------------------------------------------
+int mmp_sweep_fine(mmp_ctx* ctx, int prob, int n_lo, int n_hi) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  if (ctx->batch) return MMP_ERR_UNSUPPORTED;
+  Prob& p = ctx->probs[prob];
+  if (n_lo < 0 || n_hi > p.d.N || n_lo >= n_hi) return MMP_ERR_INVALID_ARG;
+  if (!p.lifted || p.fine_pending != 0 || p.done) return MMP_ERR_STATE;
+  const int k = p.sweeps + 1;
+  const int first = std::max(k - 1, n_lo);  // slices before k - 1 are exact (Property 3.3)
+  if (first < n_hi) {
+    const char* src = k == 1 ? nullptr : p.B[(k - 1) & 1];
+    rc = run_fine(ctx, p, first, n_hi - first, p.nf, p.u0, src, p.B[k & 1], 0, p.aff, 0, p.stats, 0);
+    if (rc) return rc;
+  }
+  p.fine_pending = k;
+  return MMP_OK;
+}
+
+int mmp_sweep_coarse(mmp_ctx* ctx, int prob, int* done) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  Prob& p = ctx->probs[prob];
+  if (p.fine_pending != p.sweeps + 1 || p.fine_pending == 0) return MMP_ERR_STATE;
+  const int k = p.fine_pending;
+  rc = run_driver(ctx, p, k);
+  if (rc) return rc;
+  double ctl[16];
+  MMP_CUDA(cudaMemcpyAsync(ctl, p.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, ctx->stream));
+  MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  rc = collect_timing(ctx);
+  if (rc) return rc;
+  for (int n = k - 1; n < p.d.N; ++n) p.out_buf[n] = k & 1;
+  p.sweeps = k;
+  p.fine_pending = 0;
+  p.last_change = ctl[0];
+  p.converged = ctl[1] != 0.0 || k == p.d.N;
+  p.done = ctl[3] != 0.0;
+  if (done != nullptr) *done = p.done ? 1 : 0;
+  return status_to_error((unsigned)ctl[15]);
+}
+
+int mmp_get_records(mmp_ctx* ctx, int prob, int n_lo, int n_hi, double* out) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  Prob& p = ctx->probs[prob];
+  if (out == nullptr || n_lo < 0 || n_hi > p.d.N || n_lo > n_hi) return MMP_ERR_INVALID_ARG;
+  if (!p.lifted) return MMP_ERR_STATE;
+  if (n_hi == n_lo) return MMP_OK;
+  MMP_CUDA(cudaMemcpyAsync(out, p.stats + (size_t)n_lo * kStat, sizeof(double) * kStat * (n_hi - n_lo),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+  MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return MMP_OK;
+}
+
+int mmp_set_records(mmp_ctx* ctx, int prob, int n_lo, int n_hi, const double* in) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  Prob& p = ctx->probs[prob];
+  if (in == nullptr || n_lo < 0 || n_hi > p.d.N || n_lo > n_hi) return MMP_ERR_INVALID_ARG;
+  if (!p.lifted) return MMP_ERR_STATE;
+  if (n_hi == n_lo) return MMP_OK;
+  MMP_CUDA(cudaMemcpyAsync(p.stats + (size_t)n_lo * kStat, in, sizeof(double) * kStat * (n_hi - n_lo),
+                           cudaMemcpyHostToDevice, ctx->stream));
+  MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return MMP_OK;
+}
+
+// Row n of the buffer the latest fine phase wrote (sweep fine_pending, or the
+// last complete sweep), or nullptr before the first fine phase.
+static char* output_row(Prob& p, int n) {
+  const int k = p.fine_pending != 0 ? p.fine_pending : p.sweeps;
+  if (k < 1) return nullptr;
+  return p.B[k & 1] + (size_t)n * p.pitch * p.esz;
+}
+
+int mmp_get_output(mmp_ctx* ctx, int prob, int n, void* dst, int to_host) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  Prob& p = ctx->probs[prob];
+  if (dst == nullptr || n < 0 || n >= p.d.N) return MMP_ERR_INVALID_ARG;
+  if (ctx->batch) return MMP_ERR_UNSUPPORTED;
+  char* row = output_row(p, n);
+  if (!p.lifted || row == nullptr) return MMP_ERR_STATE;
+  MMP_CUDA(cudaMemcpyAsync(dst, row, (size_t)p.d.P * p.esz, to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+  if (to_host) MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return MMP_OK;
+}
+
+int mmp_set_output(mmp_ctx* ctx, int prob, int n, const void* src, int from_host) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  Prob& p = ctx->probs[prob];
+  if (src == nullptr || n < 0 || n >= p.d.N) return MMP_ERR_INVALID_ARG;
+  if (ctx->batch) return MMP_ERR_UNSUPPORTED;
+  char* row = output_row(p, n);
+  if (!p.lifted || row == nullptr) return MMP_ERR_STATE;
+  MMP_CUDA(cudaMemcpyAsync(row, src, (size_t)p.d.P * p.esz, from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+  if (from_host) MMP_CUDA(cudaStreamSynchronize(ctx->stream));
   return MMP_OK;
 }
 
@@ -1798,6 +1910,9 @@ extern "C" int mmp_state_size(mmp_ctx* ctx, size_t* bytes) {
 }
 
 extern "C" int mmp_get_state(mmp_ctx* ctx, void* dst) {
+  if (ctx != nullptr)
+    for (const Prob& p : ctx->probs)
+      if (p.fine_pending != 0) return MMP_ERR_STATE;  // a sweep half done is no resumable state
   if (ctx == nullptr || dst == nullptr) return MMP_ERR_INVALID_ARG;
   char* o = (char*)dst;
   StateHeader hd{kStateMagic, mmp_version(), (int)ctx->probs.size(), state_digest(ctx), ctx->ws_used};
@@ -1890,4 +2005,58 @@ int mmp_probe_wait(int channel, int G, double limit_ms, void* ws, size_t ws_byte
   MMP_CUDA(cudaStreamSynchronize(s));
   if (status_out != nullptr) *status_out = st;
   return (st & kStatusTimeout) ? MMP_ERR_TIMEOUT : MMP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FMA throughput of the device in a precision (mmp_probe_fma): the peak the
+// plain FP64 form is measured against.
+// ---------------------------------------------------------------------------
+int mmp_probe_fma(int precision, void* ws, size_t ws_bytes, void* stream, double* tflops) {
+  if (precision != MMP_FP64 && precision != MMP_MIXED) return MMP_ERR_INVALID_ARG;
+  if (tflops == nullptr) return MMP_ERR_INVALID_ARG;
+  if (ws == nullptr || ((uintptr_t)ws % kAlign) != 0 || ws_bytes < 8) return MMP_ERR_WORKSPACE;
+  Device dev;
+  int rc = query_device(dev);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int grid = dev.sms * 4;
+  const long long threads = (long long)grid * kTPB;
+  // about 10^10 (FP64) or 3 x 10^11 (FP32) fused multiply-adds per timed launch
+  const long long iters = std::max(1LL, (precision == MMP_FP64 ? 10000000000LL : 300000000000LL) / (threads * 8));
+  MMP_CUDA(launch_fma_probe(precision, ws, iters / 10 + 1, grid, s));  // warm-up
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  MMP_CUDA(cudaEventCreate(&e0));
+  MMP_CUDA(cudaEventCreate(&e1));
+  MMP_CUDA(cudaEventRecord(e0, s));
+  cudaError_t le = launch_fma_probe(precision, ws, iters, grid, s);
+  cudaError_t re = cudaEventRecord(e1, s);
+  cudaError_t se = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  cudaError_t te = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  MMP_CUDA(le);
+  MMP_CUDA(re);
+  MMP_CUDA(se);
+  MMP_CUDA(te);
+  *tflops = 2.0 * 8.0 * (double)threads * (double)iters / ((double)ms * 1e-3) / 1e12;
+  return MMP_OK;
+}
+
+// Counters of the device-side iteration (mmp_sweep_info).
+int mmp_sweep_info(mmp_ctx* ctx, int prob, double* out) {
+  int rc = check_prob(ctx, prob);
+  if (rc) return rc;
+  if (out == nullptr) return MMP_ERR_INVALID_ARG;
+  Prob& p = ctx->probs[prob];
+  double ctl[16];
+  MMP_CUDA(cudaMemcpyAsync(ctl, p.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, ctx->stream));
+  MMP_CUDA(cudaStreamSynchronize(ctx->stream));
+  out[0] = ctl[4];  // regions accepted, summed over slices and sweeps
+  out[1] = ctl[5];  // regions rejected
+  out[2] = ctl[8];  // the last sweep used learned fractions
+  out[3] = ctl[6];  // two-region fit: alpha
+  out[4] = ctl[7];  //                 beta
+  out[5] = ctl[0];  // change of the last sweep
+  return MMP_OK;
 }

@@ -43,3 +43,33 @@ cudaError_t launch_wait_probe(double* partials, unsigned* flags, unsigned long l
 }
 
 }  // namespace mmp
+
+namespace mmp {
+
+// FMA throughput probe: every thread runs 8 independent chains
+// x <- fma(x, a, b) for `iters` iterations; the sum is stored only if it
+// takes a value it never takes, which keeps every chain alive.
+template <typename R>
+__global__ void __launch_bounds__(kTPB) k_fma_probe(R* sink, long long iters, R a, R b) {
+  R x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = (R)(threadIdx.x + k) * (R)1e-3;
+  for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  R s = (R)0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  if (s == (R)-1.25e-30) sink[0] = s;
+}
+
+cudaError_t launch_fma_probe(int precision, void* sink, long long iters, int grid, cudaStream_t stream) {
+  if (precision == MMP_FP64)
+    k_fma_probe<double><<<grid, kTPB, 0, stream>>>((double*)sink, iters, 0.999999, 1e-7);
+  else
+    k_fma_probe<float><<<grid, kTPB, 0, stream>>>((float*)sink, iters, 0.999999f, 1e-7f);
+  return cudaGetLastError();
+}
+
+}  // namespace mmp

@@ -50,6 +50,8 @@ EXPORTED = [
     "mmp_set_params", "mmp_adjoint_workspace_size", "mmp_adjoint_forward", "mmp_adjoint_backward", "mmp_adjoint",
     "mmp_batch_info", "mmp_autotune_workspace_size", "mmp_autotune", "mmp_set_tuning", "mmp_set_batch_nq",
     "mmp_state_size", "mmp_get_state", "mmp_set_state", "mmp_probe_wait",
+    "mmp_sweep_fine", "mmp_sweep_coarse", "mmp_get_records", "mmp_set_records", "mmp_get_output", "mmp_set_output",
+    "mmp_sweep_info", "mmp_probe_fma",
 ]
 
 
@@ -129,6 +131,14 @@ def load():
         "mmp_get_state": ([vp, vp], i),
         "mmp_set_state": ([vp, vp], i),
         "mmp_probe_wait": ([i, i, C.c_double, vp, C.c_size_t, vp, C.POINTER(C.c_uint)], i),
+        "mmp_sweep_fine": ([vp, i, i, i], i),
+        "mmp_sweep_coarse": ([vp, i, C.POINTER(i)], i),
+        "mmp_get_records": ([vp, i, i, i, d], i),
+        "mmp_set_records": ([vp, i, i, i, d], i),
+        "mmp_get_output": ([vp, i, i, vp, i], i),
+        "mmp_set_output": ([vp, i, i, vp, i], i),
+        "mmp_sweep_info": ([vp, i, d], i),
+        "mmp_probe_fma": ([i, vp, C.c_size_t, vp, d], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -338,6 +348,63 @@ def mmp_set_state(ctx, blob: bytes) -> None:
     """Restores a checkpoint taken by mmp_get_state into a context over the same problems."""
     buf = C.create_string_buffer(blob, len(blob))
     _check(load().mmp_set_state(ctx, buf), "mmp_set_state")
+
+
+def mmp_sweep_fine(ctx, prob: int, n_lo: int, n_hi: int) -> None:
+    """Fine phase of the next sweep over slices [n_lo, n_hi) (asynchronous)."""
+    _check(load().mmp_sweep_fine(ctx, prob, n_lo, n_hi), "mmp_sweep_fine")
+
+
+def mmp_sweep_coarse(ctx, prob: int) -> bool:
+    """Driver phase of the pending sweep over all slices; True when the problem stopped."""
+    done = C.c_int()
+    _check(load().mmp_sweep_coarse(ctx, prob, C.byref(done)), "mmp_sweep_coarse")
+    return bool(done.value)
+
+
+def mmp_get_records(ctx, prob: int, n_lo: int, n_hi: int) -> np.ndarray:
+    """Restriction records of slices [n_lo, n_hi), [n_hi - n_lo, STAT_STRIDE]."""
+    out = np.zeros((max(n_hi - n_lo, 0), STAT_STRIDE))
+    _check(load().mmp_get_records(ctx, prob, n_lo, n_hi, out.ctypes.data_as(C.POINTER(C.c_double))),
+           "mmp_get_records")
+    return out
+
+
+def mmp_set_records(ctx, prob: int, n_lo: int, n_hi: int, rows) -> None:
+    """Write restriction records of slices [n_lo, n_hi)."""
+    arr = np.ascontiguousarray(rows, dtype=np.float64)
+    _check(load().mmp_set_records(ctx, prob, n_lo, n_hi, arr.ctypes.data_as(C.POINTER(C.c_double))),
+           "mmp_set_records")
+
+
+def mmp_get_output(ctx, prob: int, n: int, dst_ptr: int, to_host: bool) -> None:
+    """Copy the latest fine output of slice n to dst."""
+    _check(load().mmp_get_output(ctx, prob, n, dst_ptr, 1 if to_host else 0), "mmp_get_output")
+
+
+def mmp_set_output(ctx, prob: int, n: int, src_ptr: int, from_host: bool) -> None:
+    """Replace the latest fine output of slice n by src."""
+    _check(load().mmp_set_output(ctx, prob, n, src_ptr, 1 if from_host else 0), "mmp_set_output")
+
+
+def mmp_sweep_info(ctx, prob: int) -> dict:
+    """Counters of the device-side iteration (acceptance, fit use, last change)."""
+    out = np.zeros(6)
+    _check(load().mmp_sweep_info(ctx, prob, out.ctypes.data_as(C.POINTER(C.c_double))), "mmp_sweep_info")
+    return {"accepted": int(out[0]), "rejected": int(out[1]), "fit_used": bool(out[2]),
+            "fit_alpha": float(out[3]), "fit_beta": float(out[4]), "change": float(out[5])}
+
+
+def mmp_probe_fma(precision: str, stream=None) -> float:
+    """FMA throughput of the device in TFLOP/s, FP64 ("fp64") or FP32 ("mixed")."""
+    import torch
+
+    sink = torch.empty(64, dtype=torch.uint8, device="cuda")
+    tf = C.c_double()
+    prec = MMP_MIXED if precision == "mixed" else MMP_FP64
+    _check(load().mmp_probe_fma(prec, sink.data_ptr(), sink.numel(), _stream_handle(stream), C.byref(tf)),
+           "mmp_probe_fma")
+    return tf.value
 
 
 def mmp_probe_wait(channel: int, G: int, limit_ms: float, ws_ptr: int, ws_bytes: int, stream=None):

@@ -129,7 +129,7 @@ def test_edge_cases(mmplib, orc):
         s, k, mom, st = _gpu_run(p)
         ref = orc.parareal(p)
         assert k == ref["sweeps"]
-        _assert_moments_close(mom, ref, rtol=1e-9)
+        _assert_moments_close(mom, ref)  # 1e-10, as every other FP64 parity test
         assert st["dev_err"] == 0
         s.close()
 
