@@ -96,6 +96,30 @@ def _profile_bytes_per_slice():
         return None
 
 
+# The FP64 form's ncu summary: executed FP64 operations (FMA, multiply, add,
+# each counted once) per particle-step of k_fine<double>.
+PROFILE_FP64 = os.path.join(ROOT, "profiles", "k_fine_config2_N8_fp64.md")
+PROFILE_FP64_SOURCES = ("fine_kernel.cuh", "mmp_internal.cuh", "fine_f64.cu")
+
+
+def _profile_value(path, sources, key):
+    """A number recorded in a committed ncu summary, while the sources it
+    was captured on are unchanged (else None)."""
+    try:
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                line = line.strip().lstrip("- ")
+                for k in ("code-sha256-16:", key):
+                    if line.startswith(k):
+                        fields[k] = line[len(k):].split()[0]
+        if code_digest(sources) != fields.get("code-sha256-16:"):
+            return None
+        return float(fields[key])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -217,6 +241,30 @@ def _oracle_worker(args):
     return slices * p.P * nf, time.perf_counter() - t0
 
 
+def _oracle_time_to_tol(_=None) -> dict:
+    """The oracle (single-threaded FP64 C, as it stands) from lifting to
+    tolerance: config 1 at full size, config 2 at P = 1e4 (FP64), and one
+    sweep of config 3 at P = 1e4 (its whole run, up to N = 128 sweeps of all
+    slices, would take hours on one core; the sweep's time times a sweep
+    count is the extrapolation)."""
+    import oracle
+    from paper_2310_11365_gb300 import workloads as W
+
+    oracle.build()
+    out = {}
+    for name, p in (("config1", W.config1()), ("config2_P1e4", W.config2(P=10_000, precision="fp64"))):
+        t0 = time.perf_counter()
+        r = oracle.parareal(p)
+        out[name] = {"time_to_tol_s": time.perf_counter() - t0, "sweeps": r["sweeps"],
+                     "converged": r["converged"], "P": p.P, "N": p.N}
+    p3 = W.config3(P=10_000, precision="fp64", max_iter=1, tol=0.0)
+    t0 = time.perf_counter()
+    oracle.parareal(p3)
+    out["config3_P1e4_one_sweep"] = {"s": time.perf_counter() - t0, "P": p3.P, "N": p3.N,
+                                     "note": "every sweep of the oracle propagates all N slices"}
+    return out
+
+
 def cpu_baseline(seconds: float = 12.0) -> dict:
     """The FP64 oracle as it stands (single-threaded C) on this host's cores:
     one process per core (spawned, so no CUDA state is inherited), each
@@ -294,6 +342,72 @@ def batched_run(n_problems: int, sweeps: int, rank: int, to_tol: bool = False) -
     return out
 
 
+def sweep_by_sweep(p, diagnose: bool = False) -> dict:
+    """One solve of problem p, sweep by sweep, against its own serial fine
+    run (the exact answer the iteration reaches at k = N, Property 3.3):
+    the device time of the serial run, of the lift and of every sweep (CUDA
+    events on the stream), the change the stopping rule sees and the
+    largest |dM|, |dV| over slice ends against the serial run after each
+    sweep.  time_to_tol: up to the sweep where the stopping rule
+    (max_n max(|dM|, |dV|) < tol between iterates, or k = N) stops;
+    time_to_accuracy: up to the first sweep whose moments are within tol of
+    the serial run's (the comparison at equal moment accuracy).  With
+    diagnose, per sweep also the regions accepted and rejected and whether
+    learned fractions were used."""
+    import numpy as np
+    import torch
+
+    from paper_2310_11365_gb300 import mmp
+
+    # solved without the stopping rule (tol 0), which is applied to the
+    # recorded changes instead, so the run goes on to equal accuracy
+    s = mmp.Solver(p.scaled(tol=0.0))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    ser = s.serial()
+    ev[1].record()
+    torch.cuda.synchronize()
+    serial_s = ev[0].elapsed_time(ev[1]) / 1e3
+    ev[0].record()
+    s.lift()
+    ev[1].record()
+    torch.cuda.synchronize()
+    t = ev[0].elapsed_time(ev[1]) / 1e3
+    lift_s = t
+    rows = []
+    t_tol = k_tol = t_acc = k_acc = None
+    prev = {"accepted": 0, "rejected": 0}
+    for k in range(1, p.N + 1):
+        ev[0].record()
+        s.iterate(1)
+        ev[1].record()
+        torch.cuda.synchronize()
+        t += ev[0].elapsed_time(ev[1]) / 1e3
+        mom = s.moments()
+        st = s.status()
+        dm = float(np.max(np.abs(mom[:, 6] - ser[:, 10])))
+        dv = float(np.max(np.abs(mom[:, 7] - ser[:, 11])))
+        row = {"k": k, "t_s": t, "change": st["last_change"], "max_abs_dM": dm, "max_abs_dV": dv}
+        if diagnose:
+            info = mmp.mmp_sweep_info(s.ctx, 0)
+            row.update({"accepted": info["accepted"] - prev["accepted"],
+                        "rejected": info["rejected"] - prev["rejected"], "fit_used": info["fit_used"]})
+            prev = info
+        rows.append(row)
+        if k_acc is None and dm <= p.tol and dv <= p.tol:
+            k_acc, t_acc = k, t
+        if k_tol is None and (st["last_change"] < p.tol or k == p.N):
+            k_tol, t_tol = k, t
+        if k_tol is not None and k_acc is not None:
+            break
+    if k_acc is None:  # k = N reproduces the serial run; rounding of the mixture aside
+        k_acc, t_acc = rows[-1]["k"], rows[-1]["t_s"]
+    s.close()
+    return {"serial_fine_s": serial_s, "lift_s": lift_s, "sweeps_to_tol": k_tol, "time_to_tol_s": t_tol,
+            "sweeps_to_accuracy": k_acc, "time_to_accuracy_s": t_acc, "tol": p.tol,
+            "at_stop": rows[k_tol - 1] if k_tol else None, "per_sweep": rows if diagnose else None}
+
+
 def coarse_models_run() -> dict:
     """Config 2 (mixed) to tolerance with each coarse moment model: the sweeps
     and device time the choice of coarse propagator costs (the fine sweeps are
@@ -347,6 +461,45 @@ def config3_run() -> dict:
            "particle_steps": tm["fine_particle_steps"], "value": tm["fine_particle_steps"] / (ms / 1e3),
            "unit": UNIT, "plan": s.plan(0), "autotune": {kk: v["nq"] for kk, v in tuned.items()}}
     s.close()
+    # why the run takes the sweeps it takes: per sweep the stopping rule's
+    # change, the distance to the serial run, accepted / rejected regions and
+    # the use of learned fractions
+    out["diagnosis"] = sweep_by_sweep(p, diagnose=True)
+    return out
+
+
+def rotator_run() -> dict:
+    """The plane rotator of Sec. 5 at the example's settings (T = 10,
+    dt = 1e-3, N = 10, P = 1e5, X0 ~ N(pi/4, 3 pi/4)), mixed and FP64, to
+    tolerance: sweeps, device time, fine particle-steps/s, and the same
+    against the serial run (sweep_by_sweep)."""
+    import torch
+
+    from paper_2310_11365_gb300 import mmp
+    from paper_2310_11365_gb300 import workloads as W
+
+    out = {"workload": "plane rotator: dX = (K (E sin X cos X - E cos X sin X) - g sin X) dt + sqrt(2 k_B T) dW "
+                       "mod 2 pi in [-pi, pi], K=1, g=1, k_B T=1/4, X0~N(pi/4, 3 pi/4), T=10, N=10, dt=1e-3, "
+                       "P=1e5, Gaussian-closure coarse, tol 1e-6"}
+    for prec in ("mixed", "fp64"):
+        p = W.plane_rotator(precision=prec)
+        s = mmp.Solver(p)
+        mmp.mmp_set_timing(s.ctx, True)
+        s.run()  # warm-up
+        mmp.mmp_timing(s.ctx, reset=True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        k = s.run()
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        tm = mmp.mmp_timing(s.ctx, reset=True)
+        out[prec] = {"sweeps": k, "time_to_tol_s": ms / 1e3, "particle_steps": tm["fine_particle_steps"],
+                     "value": tm["fine_particle_steps"] / (ms / 1e3),
+                     "fine_kernel_rate": tm["fine_particle_steps"] / (tm["fine_ms"] / 1e3),
+                     "plan": s.plan(0), "unit": UNIT}
+        s.close()
+        out[prec]["against_serial"] = sweep_by_sweep(p)
     return out
 
 
@@ -474,8 +627,9 @@ def main():
     ap.add_argument("--P", type=int, default=None, help="override the particle count (profiling runs)")
     ap.add_argument("--batch", type=int, default=512,
                     help="problems of the batched config-5 workload (0: skip)")
-    ap.add_argument("--batch-tol", action="store_true",
-                    help="also time the batched workload from lifting to tolerance")
+    ap.add_argument("--no-batch-tol", action="store_true",
+                    help="skip timing the batched workload from lifting to tolerance")
+    ap.add_argument("--no-rotator", action="store_true", help="skip the plane-rotator solves")
     ap.add_argument("--batch-sweeps", type=int, default=2, help="fine sweeps timed for the batched workload")
     ap.add_argument("--no-cfg3", action="store_true", help="skip the config-3 (learning variant) solve")
     ap.add_argument("--no-cfg4", action="store_true", help="skip the config-4 adjoint timing")
@@ -491,6 +645,12 @@ def main():
     import numpy as np
     import torch
 
+    oracle_ttt = None
+    if rank == 0 and not args.no_cpu and args.adjoint_only is None:
+        import multiprocessing as mp
+
+        oracle_pool = mp.get_context("spawn").Pool(1)
+        oracle_ttt = oracle_pool.apply_async(_oracle_time_to_tol, (0,))
     torch.cuda.set_device(local)
     if args.adjoint_only is not None:
         print(json.dumps({"config4_adjoint": config4_run(args.adjoint_only)}))
@@ -586,37 +746,60 @@ def main():
     accuracy = {"tol": p.tol, "mixed": {"max_abs_dM": float(np.max(np.abs(mom[:, 6] - ser[:, 10]))),
                                         "max_abs_dV": float(np.max(np.abs(mom[:, 7] - ser[:, 11])))}}
 
-    # plain FP64 GPU form: time to the same tolerance (one solve)
+    # plain FP64 GPU form against the mixed form: each solved sweep by sweep
+    # against its own serial fine run, to the stopping rule and to equal
+    # moment accuracy (max |dM|, |dV| <= tol against that run)
     fp64 = None
     if not args.no_fp64:
         p64 = W.config2(precision="fp64", problem_tag=rank, **overrides)
+        fp64 = {"fp64": sweep_by_sweep(p64), "mixed": sweep_by_sweep(p)}
         s64 = mmp.Solver(p64)
         mmp.mmp_set_timing(s64.ctx, True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        ev0.record(stream)
         k64 = s64.run()
+        ev1.record(stream)
         torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
+        ms64 = ev0.elapsed_time(ev1)
         tm64 = mmp.mmp_timing(s64.ctx, reset=True)
         m64 = s64.moments()
-        fp64 = {"time_to_tol_s": t64, "sweeps": k64, "particle_steps_per_s": tm64["fine_particle_steps"] / t64,
-                "max_abs_diff_M_vs_mixed": float(np.max(np.abs(m64[:, 6] - mom[:, 6]))),
-                "max_abs_diff_V_vs_mixed": float(np.max(np.abs(m64[:, 7] - mom[:, 7])))}
-        ser64 = s64.serial()
-        accuracy["fp64"] = {"max_abs_dM": float(np.max(np.abs(m64[:, 6] - ser64[:, 10]))),
-                            "max_abs_dV": float(np.max(np.abs(m64[:, 7] - ser64[:, 11])))}
         s64.close()
+        fp64["max_abs_diff_M_vs_mixed"] = float(np.max(np.abs(m64[:, 6] - mom[:, 6])))
+        fp64["max_abs_diff_V_vs_mixed"] = float(np.max(np.abs(m64[:, 7] - mom[:, 7])))
+        rate64 = tm64["fine_particle_steps"] / (tm64["fine_ms"] / 1e3)
+        # the FP64 form against the device's measured FP64 FMA throughput:
+        # how many FP64 fused multiply-adds per particle-step that throughput
+        # would allow at the measured rate, and the fraction of the FP64 pipe
+        # the kernel's executed FP64 operations (ncu count) take
+        peak64 = mmp.mmp_probe_fma("fp64")
+        peak32 = mmp.mmp_probe_fma("mixed")
+        ops64 = _profile_value(PROFILE_FP64, PROFILE_FP64_SOURCES, "fp64-ops-per-particle-step:")
+        fp64["fp64_form"] = {"sweeps": k64, "time_to_tol_s": ms64 / 1e3,
+                             "particle_steps_per_s": tm64["fine_particle_steps"] / (ms64 / 1e3),
+                             "fine_kernel_rate": rate64,
+                             "fma_per_particle_step_at_fp64_peak": peak64 * 1e12 / 2.0 / rate64,
+                             "fp64_ops_per_particle_step": ops64,
+                             "fp64_pipe_frac": None if ops64 is None else ops64 * rate64 / (peak64 * 1e12 / 2.0)}
+        fp64["measured_fma_peaks_tflops"] = {"fp64": peak64, "fp32": peak32,
+                                             "how": "mmp_probe_fma: 4 CTAs per SM x 256 threads x 8 independent "
+                                                    "FMA chains, CUDA events, after a warm-up launch"}
 
     batch = None
     if args.batch > 0:
-        batch = batched_run(args.batch, args.batch_sweeps, rank, args.batch_tol)
+        batch = batched_run(args.batch, args.batch_sweeps, rank, not args.no_batch_tol)
     coarse = None if overrides else coarse_models_run()
+    rot = None if args.no_rotator or overrides else rotator_run()
+    cfg1 = None if overrides else sweep_by_sweep(W.config1(problem_tag=rank))
     cfg3 = None if args.no_cfg3 or overrides else config3_run()
     cfg4 = None if args.no_cfg4 or overrides else config4_run()
 
     cpu = None
     if rank == 0 and not args.no_cpu:
+        ttt = oracle_ttt.get(timeout=1800)
+        oracle_pool.close()
         cpu = cpu_baseline()
+        ttt["config3_P1e4_extrapolated_to_gpu_sweeps"] = (
+            None if cfg3 is None else ttt["config3_P1e4_one_sweep"]["s"] * cfg3["sweeps"])
+        cpu["time_to_tol"] = ttt
 
     if rank == 0:
         line = {
@@ -644,6 +827,8 @@ def main():
             "e2e": e2e,
             "fp64_plain": fp64,
             "accuracy_vs_own_serial": accuracy,
+            "plane_rotator": rot,
+            "config1_fp64": cfg1,
             "batched_config5": batch,
             "coarse_models_config2": coarse,
             "config3": cfg3,
