@@ -12,6 +12,8 @@
 #include <vector>
 
 #include "adjoint.cuh"
+#include <nvtx3/nvToolsExt.h>
+
 #include "batch.cuh"
 #include "driver.cuh"
 #include "fine.cuh"
@@ -51,6 +53,15 @@ cudaError_t launch_fine(int precision, int layout, int nq, bool mult, int grid, 
 using namespace mmp;
 
 namespace {
+
+// An NVTX range over a library call (a tool such as Nsight Systems shows the
+// phases of a run on its timeline; without a tool attached it costs a call).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 // written by any thread that sees a CUDA call fail
 std::atomic<int> g_last_cuda_error{0};
@@ -892,6 +903,7 @@ int mmp_workspace_size(const mmp_problem_desc* descs, int n_problems, size_t* by
 
 int mmp_create(mmp_ctx** out, const mmp_problem_desc* descs, int n_problems, void* workspace,
                size_t workspace_bytes, void* stream) {
+  Range nvtx_range("mmp_create");
   if (out == nullptr) return MMP_ERR_INVALID_ARG;
   *out = nullptr;
   if (workspace == nullptr || ((uintptr_t)workspace % kAlign) != 0) return MMP_ERR_WORKSPACE;
@@ -967,6 +979,7 @@ int mmp_set_initial(mmp_ctx* ctx, int prob, const void* u0, int from_host) {
 }
 
 int mmp_lift(mmp_ctx* ctx) {
+  Range nvtx_range("mmp_lift");
   if (ctx == nullptr) return MMP_ERR_INVALID_ARG;
   for (Prob& p : ctx->probs) {
     int rc = run_fine(ctx, p, 0, 1, 0, p.u0, nullptr, nullptr, 0, nullptr, 0, p.stats_u0, 1);
@@ -987,6 +1000,7 @@ int mmp_lift(mmp_ctx* ctx) {
 }
 
 int mmp_iterate(mmp_ctx* ctx, int n_iter, int* all_converged) {
+  Range nvtx_range("mmp_iterate");
   if (ctx == nullptr || n_iter < 0) return MMP_ERR_INVALID_ARG;
   for (Prob& p : ctx->probs)
     if (!p.lifted || p.fine_pending != 0) return MMP_ERR_STATE;
@@ -1119,6 +1133,7 @@ int mmp_iterate(mmp_ctx* ctx, int n_iter, int* all_converged) {
 // fine output at the end of a block is handed to the next rank).
 // ---------------------------------------------------------------------------
 int mmp_sweep_fine(mmp_ctx* ctx, int prob, int n_lo, int n_hi) {
+  Range nvtx_range("mmp_sweep_fine");
   int rc = check_prob(ctx, prob);
   if (rc) return rc;
   if (ctx->batch) return MMP_ERR_UNSUPPORTED;
@@ -1137,6 +1152,7 @@ int mmp_sweep_fine(mmp_ctx* ctx, int prob, int n_lo, int n_hi) {
 }
 
 int mmp_sweep_coarse(mmp_ctx* ctx, int prob, int* done) {
+  Range nvtx_range("mmp_sweep_coarse");
   int rc = check_prob(ctx, prob);
   if (rc) return rc;
   Prob& p = ctx->probs[prob];
@@ -1222,6 +1238,7 @@ int mmp_set_output(mmp_ctx* ctx, int prob, int n, const void* src, int from_host
 }
 
 int mmp_run(mmp_ctx* ctx, int* sweeps_out) {
+  Range nvtx_range("mmp_run");
   int rc = mmp_lift(ctx);
   if (rc) return rc;
   int all = 0;
@@ -1287,6 +1304,7 @@ int mmp_get_particles(mmp_ctx* ctx, int prob, int n, void* dst, int to_host) {
 }
 
 int mmp_fine_serial(mmp_ctx* ctx, int prob, int n_end, double* stats_out, void* parts_dev) {
+  Range nvtx_range("mmp_fine_serial");
   int rc = check_prob(ctx, prob);
   if (rc) return rc;
   Prob& p = ctx->probs[prob];
@@ -1364,6 +1382,7 @@ int mmp_adjoint_workspace_size(mmp_ctx* ctx, int prob, int ckpt_every, size_t* b
 }
 
 int mmp_adjoint_forward(mmp_ctx* ctx, int prob, int ckpt_every, void* ws, size_t ws_bytes, double* moments_out) {
+  Range nvtx_range("mmp_adjoint_forward");
   int rc = check_prob(ctx, prob);
   if (rc) return rc;
   if (ckpt_every < 1) return MMP_ERR_INVALID_ARG;
@@ -1416,6 +1435,7 @@ int mmp_adjoint_forward(mmp_ctx* ctx, int prob, int ckpt_every, void* ws, size_t
 
 int mmp_adjoint_backward(mmp_ctx* ctx, int prob, const double* gm, const double* gv, void* ws, size_t ws_bytes,
                          double* grad_out) {
+  Range nvtx_range("mmp_adjoint_backward");
   int rc = check_prob(ctx, prob);
   if (rc) return rc;
   if (gm == nullptr || gv == nullptr || grad_out == nullptr) return MMP_ERR_INVALID_ARG;
@@ -1517,6 +1537,7 @@ int mmp_get_plan(mmp_ctx* ctx, int prob, int* quads_per_thread, int* ctas_per_sl
 }
 
 int mmp_fine(mmp_ctx* ctx, int prob, int n, const void* u_in, void* u_out, double* stats_out) {
+  Range nvtx_range("mmp_fine");
   int rc = check_prob(ctx, prob);
   if (rc) return rc;
   Prob& p = ctx->probs[prob];
@@ -1713,6 +1734,7 @@ extern "C" int mmp_autotune_workspace_size(const mmp_problem_desc* desc, size_t*
 
 extern "C" int mmp_autotune(const mmp_problem_desc* desc, const int* candidates, int n_candidates, int probe_steps,
                             void* workspace, size_t bytes, void* stream, int* best_nq, double* rates) {
+  Range nvtx_range("mmp_autotune");
   if (desc == nullptr || best_nq == nullptr) return MMP_ERR_INVALID_ARG;
   if (candidates != nullptr && n_candidates < 1) return MMP_ERR_INVALID_ARG;
   if (workspace == nullptr || ((uintptr_t)workspace % kAlign) != 0) return MMP_ERR_WORKSPACE;
@@ -1910,6 +1932,7 @@ extern "C" int mmp_state_size(mmp_ctx* ctx, size_t* bytes) {
 }
 
 extern "C" int mmp_get_state(mmp_ctx* ctx, void* dst) {
+  Range nvtx_range("mmp_get_state");
   if (ctx != nullptr)
     for (const Prob& p : ctx->probs)
       if (p.fine_pending != 0) return MMP_ERR_STATE;  // a sweep half done is no resumable state
@@ -1931,6 +1954,7 @@ extern "C" int mmp_get_state(mmp_ctx* ctx, void* dst) {
 }
 
 extern "C" int mmp_set_state(mmp_ctx* ctx, const void* src) {
+  Range nvtx_range("mmp_set_state");
   if (ctx == nullptr || src == nullptr) return MMP_ERR_INVALID_ARG;
   const char* i = (const char*)src;
   StateHeader hd;
