@@ -248,7 +248,9 @@ int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta, int n_theta);
  * mmp_adjoint_workspace_size: bytes of caller-owned device workspace for a
  * checkpoint every `ckpt_every` fine steps: one particle row per checkpoint,
  * 3 recorded values per step, ckpt_every + 1 state rows and ckpt_every
- * draw rows for the segment being reversed.
+ * draw rows for the segment being reversed (the draw rows are used with B
+ * or BE nonzero; with additive noise the reverse sweep regenerates the
+ * draws; the size does not depend on the form).
  *
  * mmp_adjoint_forward: runs the serial fine propagation from u0 with the
  * current coefficients, recording checkpoints and per-step mean-field values

@@ -21,7 +21,10 @@
 // and the two mean-dependent terms of the step).  Per segment, in reverse:
 // each thread recomputes its own particles over the c steps from the
 // checkpoint (no reduction is needed: the means are recorded), storing
-// states and draws, then sweeps backward with one group exchange per step,
+// states (and, with state- or mean-dependent diffusion, draws; with
+// additive noise the backward step regenerates its draws from Philox, which
+// costs less than reading them back), then sweeps backward with one group
+// exchange per step,
 // in the shift form that lets that exchange run one step behind the sweep
 // (below).  The replay evaluates the step exactly as the forward kernel did,
 // so it reproduces the forward states.
@@ -31,6 +34,7 @@
 #include "fine_kernel.cuh"
 
 namespace mmp {
+
 
 // MULT false: additive diffusion (B = BE = 0), the forward's shift form;
 // the per-step exchange is the group sum of mu (one value).
@@ -120,6 +124,18 @@ __global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
 #pragma unroll
     for (int w = 0; w < 4; ++w) l[w] += ca + cb * (x[w] - Mr);
     zero_tail(q, l);
+  };
+  // the draws of global step j for quad q as the additive form's step uses
+  // them, radius times cosine or sine (lanes past P zeroed)
+  auto polar_draws = [&](long long j, int q, R z[4]) {
+    R nr[2], c[2], sn[2];
+    normals4_polar<R>(philox4x32_10(rng_counter((uint32_t)q, (uint32_t)(j % a.nf), (uint32_t)(j / a.nf), 0u,
+                                                a.ptag), a.key0, a.key1), nr, c, sn);
+    z[0] = mulR(nr[0], c[0]);
+    z[1] = mulR(nr[0], sn[0]);
+    z[2] = mulR(nr[1], c[1]);
+    z[3] = mulR(nr[1], sn[1]);
+    zero_tail(q, z);
   };
   // the draws of global step j for quad q (lanes past P zeroed)
   auto draws = [&](long long j, int q, R z[4]) {
@@ -212,11 +228,9 @@ __global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
             x[w] = fmaR(amp, z[w], fmaR(h, drift, xv));
           }
         } else {
+          // the draws are not stored: the reverse sweep regenerates them
           R nr[2], c[2], sn[2];
           normals4_polar<R>(o, nr, c, sn);
-          R z[4] = {mulR(nr[0], c[0]), mulR(nr[0], sn[0]), mulR(nr[1], c[1]), mulR(nr[1], sn[1])};
-          zero_tail(q, z);
-          Quad<R>::store(segz + (size_t)jj * a.pitch + 4 * (size_t)q, z);
           const R d = uni[3 * j + 1];    // h (kappa m_j + c0) as the forward used it
           const R amp = uni[3 * j + 2];  // B0 sqrt(h) as the forward used it
           em_partial_pair(x[0], x[1], nr[0], c[0], sn[0], hn3, hc1, amp);
@@ -280,9 +294,13 @@ __global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
       for (int i = 0; i < nq; ++i) {
         const int q = qb + tid + i * kTPB;
         R l[4], x[4], z[4];
+        if constexpr (MULT) {
+          Quad<R>::load(segz + (size_t)jj * a.pitch + 4 * (size_t)q, z);
+        } else {
+          polar_draws(j, q, z);  // regenerated: half the bytes of a stored row
+        }
         lam.get(i, l);
         Quad<R>::load(segx + (size_t)jj * a.pitch + 4 * (size_t)q, x);
-        Quad<R>::load(segz + (size_t)jj * a.pitch + 4 * (size_t)q, z);
 #pragma unroll
         for (int w = 0; w < 4; ++w) l[w] = addR(l[w], s_next);  // lambda_{j+1}
         zero_tail(q, l);

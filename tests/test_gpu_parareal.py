@@ -111,14 +111,15 @@ def test_property_3_3_gpu_bitwise(mmplib, make, prec):
 def test_mixed_config2_small_against_oracle(mmplib, orc):
     """Mixed precision on the config-2 model vs the FP64 oracle on the same
     draws after a fixed number of sweeps: moments within the stated bounds
-    (means 2e-6 of max(|m|, sd), variances 1e-5 relative)."""
+    (means 1.2e-6 of max(|m|, sd), variances 3e-6 relative; about twice the
+    errors measured on a GB300, 5.3e-7 and 1.15e-6)."""
     p = W.config2(P=20_000, N=8, T=1.0, precision="mixed", max_iter=3, tol=0.0)
     s, k, mom, st = _gpu_run(p)
     ref = orc.parareal(p.scaled(precision="fp64"))
     for n in range(p.N + 1):
         M, V = ref["hist"][-1][n]
-        assert abs(mom[n, 6] - M) < 2e-6 * max(abs(M), np.sqrt(V)), n
-        assert abs(mom[n, 7] - V) < 1e-5 * V, n
+        assert abs(mom[n, 6] - M) < 1.2e-6 * max(abs(M), np.sqrt(V)), n
+        assert abs(mom[n, 7] - V) < 3e-6 * V, n
     s.close()
 
 
