@@ -34,9 +34,11 @@ const void* fine_kernel(int precision, int layout, int nq, bool mult, int family
   return precision == MMP_MIXED ? fine_kernel_f32(t, mult, family) : fine_kernel_f64(t, mult, family);
 }
 
-size_t fine_smem_bytes(int precision, int layout, int nq) {
+size_t fine_smem_bytes(int precision, int layout, int nq, int family) {
   if (layout != kLayoutSmem) return 0;
-  return (size_t)nq * kTPB * 4 * (precision == MMP_MIXED ? sizeof(float) : sizeof(double));
+  // the plane rotator keeps sin x and cos x beside x
+  const size_t per = family == MMP_FAMILY_ROTATOR ? 3 : 1;
+  return per * (size_t)nq * kTPB * 4 * (precision == MMP_MIXED ? sizeof(float) : sizeof(double));
 }
 
 cudaError_t launch_fine(int precision, int layout, int nq, bool mult, int grid, const FineArgs& args,
@@ -46,7 +48,7 @@ cudaError_t launch_fine(int precision, int layout, int nq, bool mult, int grid, 
   FineArgs copy = args;
   void* params[] = {&copy};
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTPB), params,
-                                     fine_smem_bytes(precision, layout, nq), stream);
+                                     fine_smem_bytes(precision, layout, nq, family), stream);
 }
 }  // namespace mmp
 
@@ -233,10 +235,10 @@ int plan(Prob& p, const Device& dev, int batch_nq = 0) {
     size_t limit = 0;
     const int rc = allow_dynamic_smem(fn, dev.dev, &limit);
     if (rc) return rc;
-    if (fine_smem_bytes(p.d.precision, kLayoutSmem, p.nq) > limit) return MMP_ERR_UNSUPPORTED;
+    if (fine_smem_bytes(p.d.precision, kLayoutSmem, p.nq, p.d.family) > limit) return MMP_ERR_UNSUPPORTED;
     int occ = 0;
     MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB,
-                                                           fine_smem_bytes(p.d.precision, kLayoutSmem, p.nq)));
+                                                           fine_smem_bytes(p.d.precision, kLayoutSmem, p.nq, p.d.family)));
     if ((long long)occ * dev.sms < p.G) return MMP_ERR_UNSUPPORTED;
     return MMP_OK;
   }
@@ -252,7 +254,7 @@ int plan(Prob& p, const Device& dev, int batch_nq = 0) {
     const void* fn = fine_kernel(p.d.precision, layout, tuned, p.mult, p.d.family);
     size_t limit = 0;
     int occ = 0;
-    const size_t smem = fine_smem_bytes(p.d.precision, layout, tuned);
+    const size_t smem = fine_smem_bytes(p.d.precision, layout, tuned, p.d.family);
     const int rc = allow_dynamic_smem(fn, dev.dev, &limit);
     if (rc) return rc;
     if (smem <= limit) MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, smem));
@@ -266,7 +268,7 @@ int plan(Prob& p, const Device& dev, int batch_nq = 0) {
     int occ = 0;
     const void* fn = fine_kernel(p.d.precision, layout, nq, p.mult, p.d.family);
     if (fn == nullptr) return MMP_ERR_UNSUPPORTED;
-    const size_t smem = fine_smem_bytes(p.d.precision, layout, nq);
+    const size_t smem = fine_smem_bytes(p.d.precision, layout, nq, p.d.family);
     if (layout == kLayoutSmem) {
       size_t limit = 0;
       const int rc = allow_dynamic_smem(fn, dev.dev, &limit);
@@ -824,7 +826,7 @@ int adjoint_layout(mmp_ctx* c, Prob& p, int ckpt_every, char* base, AdjLayout& L
     size_t flimit = 0;
     const int frc = allow_dynamic_smem(ff, c->dev.dev, &flimit);
     if (frc) return frc;
-    const size_t smem = fine_smem_bytes(p.d.precision, kLayoutSmem, nq);
+    const size_t smem = fine_smem_bytes(p.d.precision, kLayoutSmem, nq, p.d.family);
     if (smem > flimit) break;
     int occ = 0;
     MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ff, kTPB, smem));
@@ -1348,7 +1350,7 @@ int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta, int n_theta) {
     if (ctx->batch) return MMP_ERR_UNSUPPORTED;
     const void* fn = fine_kernel(p.d.precision, p.layout, p.nq, mult, p.d.family);
     if (fn == nullptr) return MMP_ERR_UNSUPPORTED;
-    const size_t smem = fine_smem_bytes(p.d.precision, p.layout, p.nq);
+    const size_t smem = fine_smem_bytes(p.d.precision, p.layout, p.nq, p.d.family);
     if (p.layout == kLayoutSmem) {
       size_t limit = 0;
       rc = allow_dynamic_smem(fn, ctx->dev.dev, &limit);
@@ -1773,7 +1775,7 @@ extern "C" int mmp_autotune(const mmp_problem_desc* desc, const int* candidates,
     const int nq = cand[ci];
     const void* fn = nq >= 1 && nq <= max_nq ? fine_kernel(p.d.precision, kLayoutSmem, nq, p.mult, p.d.family) : nullptr;
     size_t limit = 0;
-    const size_t smem = fine_smem_bytes(p.d.precision, kLayoutSmem, nq);
+    const size_t smem = fine_smem_bytes(p.d.precision, kLayoutSmem, nq, p.d.family);
     if (fn != nullptr && (err = allow_dynamic_smem(fn, dev.dev, &limit)) == MMP_OK && smem <= limit) {
       int occ = 0;
       cudaError_t ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, smem);

@@ -54,8 +54,9 @@ constexpr int kLayoutSmem = 1;
 // Handle of one kernel instantiation (nq ignored for the shared layout;
 // the plane rotator has the shared layout only, nullptr otherwise).
 const void* fine_kernel(int precision, int layout, int nq, bool mult, int family = 0);
-// Dynamic shared memory of a launch.
-size_t fine_smem_bytes(int precision, int layout, int nq);
+// Dynamic shared memory of a launch (three values per particle for the
+// plane rotator: x, sin x, cos x).
+size_t fine_smem_bytes(int precision, int layout, int nq, int family = 0);
 // Cooperative launch of the instantiation (grid = slots * G CTAs).
 cudaError_t launch_fine(int precision, int layout, int nq, bool mult, int grid, const FineArgs& args,
                         cudaStream_t stream, int family = 0);

@@ -688,16 +688,19 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
         }
         s_in = addR(s_in, addR(addR(v[0], v[1]), addR(v[2], v[3])));
         if constexpr (kRot) {
+          // sin x and cos x are kept beside x (slots nq_max + i, 2 nq_max + i)
           const int valid = q == qlast ? plast : 4;
+          R sv[4], cv[4];
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
+            sincosR(v[w], &sv[w], &cv[w]);
             if (w < valid) {
-              R sn, cn;
-              sincosR(v[w], &sn, &cn);
-              s_sin = addR(s_sin, sn);
-              s_cos = addR(s_cos, cn);
+              s_sin = addR(s_sin, sv[w]);
+              s_cos = addR(s_cos, cv[w]);
             }
           }
+          xs.put(nq_max + i, sv);
+          xs.put(2 * nq_max + i, cv);
         }
       }
       xs.put(i, v);
@@ -772,40 +775,121 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
 
   // ---------------- Euler-Maruyama steps --------------------------------
   if constexpr (kRot) {
+    // Each step in two phases around the group sums of sin x_j and cos x_j:
+    //   A: y = x - h g sin x + B0 sqrt(h) xi        (no ensemble sum needed)
+    //   B: x' = wrap(y + h K (S cos x - C sin x)), then sin x', cos x' and
+    //      their sums for the next step.
+    // Warp 0 publishes a step's sums at the end of its phase B and collects
+    // the group's after the next phase A, so the exchange travels while
+    // phase A computes.  The sums of step 0 come from the prologue.
+    const R hK = mulR(h, Kr);
+    const R hg = mulR(h, gr);
+    double cta_s = 0.0, cta_c = 0.0;  // warp 0: this CTA's sums of the pending epoch
+    unsigned e_pub = 0;
+    bool pending = false;
     for (int j = 0; j < nf; ++j) {
-      // x <- wrap(x + h (K (S cos x - C sin x) - g sin x) + B0 sqrt(h) xi)
+#pragma unroll kStepUnroll
+      for (int i = 0; i < loop_n; ++i) {
+        if (i < nq) {
+          const int q = qb + tid + i * kTPB;
+          R v[4], sv[4];
+          xs.get(i, v);
+          xs.get(nq_max + i, sv);
+          const uint4 o = philox4x32_10(rng_counter((uint32_t)q, (uint32_t)j, (uint32_t)n, 0u, a.ptag), a.key0,
+                                        a.key1);
+          R z[4];
+          normals4<R>(o, z);
+#pragma unroll
+          for (int w = 0; w < 4; ++w) v[w] = addR(subR(v[w], mulR(hg, sv[w])), mulR(b0sq, z[w]));
+          xs.put(i, v);
+        }
+      }
+      if (pending) {
+        if (warp == 0) {
+          double gs0 = 0.0, gs1 = 0.0;
+          bool ok = true;
+          if (grp.G > 1) {
+            ok = group_wait(grp, e_pub);
+            for (int c = lane; c < grp.G; c += 32) {
+              const double* sl = group_slot(grp, c, e_pub);
+              gs0 += __ldcg(sl);
+              gs1 += __ldcg(sl + 1);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+              gs0 += __shfl_xor_sync(0xffffffffu, gs0, off);
+              gs1 += __shfl_xor_sync(0xffffffffu, gs1, off);
+            }
+          } else {
+            gs0 = cta_s;
+            gs1 = cta_c;
+          }
+          if (lane == 0) {
+            if (!ok) sh.abort = 1;
+            const double S = gs0 / (double)a.P, C = gs1 / (double)a.P;
+            sh.rotd[0] = S;
+            sh.rotd[1] = C;
+            sh.rotf[0] = (float)S;
+            sh.rotf[1] = (float)C;
+          }
+        }
+        __syncthreads();
+        if (sh.abort) return false;
+        pending = false;
+      }
       const R sb = fl ? (R)sh.rotf[0] : (R)sh.rotd[0];
       const R cb = fl ? (R)sh.rotf[1] : (R)sh.rotd[1];
-      const bool more = j + 1 < nf;  // the last step's sums are not needed
+      const bool more = j + 1 < nf;  // the last step's sines, cosines and sums are not needed
       R ss = (R)0, cs = (R)0;
 #pragma unroll kStepUnroll
       for (int i = 0; i < loop_n; ++i) {
         if (i < nq) {
           const int q = qb + tid + i * kTPB;
-          R v[4];
+          R v[4], sv[4], cv[4];
           xs.get(i, v);
-          const uint4 o = philox4x32_10(rng_counter((uint32_t)q, (uint32_t)j, (uint32_t)n, 0u, a.ptag), a.key0,
-                                        a.key1);
-          R z[4];
-          normals4<R>(o, z);
+          xs.get(nq_max + i, sv);
+          xs.get(2 * nq_max + i, cv);
           const int valid = q == qlast ? plast : 4;
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
-            R sn, cn;
-            sincosR(v[w], &sn, &cn);
-            const R drift = subR(mulR(Kr, subR(mulR(sb, cn), mulR(cb, sn))), mulR(gr, sn));
-            const R xn = wrap_angle(addR(addR(v[w], mulR(drift, h)), mulR(b0sq, z[w])));
-            v[w] = xn;
-            if (more && w < valid) {
-              sincosR(xn, &sn, &cn);
-              ss = addR(ss, sn);
-              cs = addR(cs, cn);
+            v[w] = wrap_angle(addR(v[w], mulR(hK, subR(mulR(sb, cv[w]), mulR(cb, sv[w])))));
+            if (more) {
+              sincosR(v[w], &sv[w], &cv[w]);
+              if (w < valid) {
+                ss = addR(ss, sv[w]);
+                cs = addR(cs, cv[w]);
+              }
             }
           }
           xs.put(i, v);
+          if (more) {
+            xs.put(nq_max + i, sv);
+            xs.put(2 * nq_max + i, cv);
+          }
         }
       }
-      if (more && !rot_exchange(2, (double)ss, (double)cs, 0.0)) return false;
+      if (more) {
+        double v2[2] = {(double)ss, (double)cs};
+        warp_reduce_to_shared<2>(sh, v2, 0u, 0u);
+        __syncthreads();
+        e_pub = grp.epoch++;
+        if (warp == 0) {
+          double w0 = lane < kWarps ? sh.red[lane][0] : 0.0;
+          double w1 = lane < kWarps ? sh.red[lane][1] : 0.0;
+#pragma unroll
+          for (int off = kWarps / 2; off > 0; off >>= 1) {
+            w0 += __shfl_xor_sync(0xffffffffu, w0, off);
+            w1 += __shfl_xor_sync(0xffffffffu, w1, off);
+          }
+          cta_s = __shfl_sync(0xffffffffu, w0, 0);
+          cta_c = __shfl_sync(0xffffffffu, w1, 0);
+          if (grp.G > 1 && lane == 0) {
+            const double pub[2] = {cta_s, cta_c};
+            group_publish(grp, e_pub, pub, 2);
+          }
+        }
+        pending = true;
+      }
     }
   } else
   for (int j = 0; j < nf; ++j) {
