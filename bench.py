@@ -635,6 +635,9 @@ def main():
     ap.add_argument("--no-cfg4", action="store_true", help="skip the config-4 adjoint timing")
     ap.add_argument("--no-tune", action="store_true",
                     help="plan config 2 with the cost model instead of measured shapes (profiling runs)")
+    ap.add_argument("--main-precision", default="mixed", choices=["mixed", "fp64"],
+                    help="precision of the timed config-2 solves (profiling runs of the FP64 form)")
+    ap.add_argument("--rotator-only", action="store_true", help="only the plane-rotator leg (profiling runs)")
     ap.add_argument("--adjoint-only", type=int, default=None, metavar="N",
                     help="only the config-4 adjoint leg, with N slices of the config's length (profiling runs)")
     args = ap.parse_args()
@@ -646,7 +649,7 @@ def main():
     import torch
 
     oracle_ttt = None
-    if rank == 0 and not args.no_cpu and args.adjoint_only is None:
+    if rank == 0 and not args.no_cpu and args.adjoint_only is None and not args.rotator_only:
         import multiprocessing as mp
 
         oracle_pool = mp.get_context("spawn").Pool(1)
@@ -654,6 +657,9 @@ def main():
     torch.cuda.set_device(local)
     if args.adjoint_only is not None:
         print(json.dumps({"config4_adjoint": config4_run(args.adjoint_only)}))
+        return 0
+    if args.rotator_only:
+        print(json.dumps({"plane_rotator": rotator_run()}))
         return 0
     if world > 1:
         import torch.distributed as dist
@@ -668,7 +674,7 @@ def main():
     overrides = {k: v for k, v in (("N", args.N), ("P", args.P)) if v is not None}
     if "N" in overrides:
         overrides["T"] = 8.0 * overrides["N"] / 64  # keep the slice length (n_f = 125)
-    p = W.config2(problem_tag=rank, **overrides)
+    p = W.config2(problem_tag=rank, precision=args.main_precision, **overrides)
     # measured launch shapes (mmp_autotune) for the mixed and FP64 config-2
     # problems, registered before any context is planned
     from paper_2310_11365_gb300 import tune
