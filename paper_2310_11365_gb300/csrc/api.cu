@@ -294,7 +294,14 @@ int plan(Prob& p, const Device& dev, int batch_nq = 0) {
     const int slots = std::min(N, S / G);
     const int waves = (N + slots - 1) / slots;
     const int per_sm = (slots * G + dev.sms - 1) / dev.sms;
-    const double step = per_sm * (double)kTPB * nq / quad_rate + (G > 1 ? 2500.0 : 400.0);
+    // the rotator's step is latency-bound (a group exchange per step): an SM
+    // with fewer than the two CTAs the kernel is built for runs them at their
+    // own rate, not the SM's, so its throughput scales with the CTAs it holds
+    // (also where its shared memory fits only one) (measured on
+    // the Sec. 5 example: one CTA per SM ran 7 % (mixed) and 22 % (FP64)
+    // slower than the best shape with two)
+    const double fill = p.d.family == MMP_FAMILY_ROTATOR ? std::min(1.0, per_sm / 2.0) : 1.0;  // built for 2 per SM
+    const double step = per_sm * (double)kTPB * nq / (quad_rate * fill) + (G > 1 ? 2500.0 : 400.0);
     const double cost = waves * step;
     // forced (MMP_FINE_NQ or a tuning entry): the largest reachable count
     // not above the forced one, else the cheapest by the cost model
