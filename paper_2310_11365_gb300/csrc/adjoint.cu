@@ -40,10 +40,14 @@ namespace mmp {
 // the per-step exchange is the group sum of mu (one value).
 // MULT true: general diffusion; the shift of lambda_j also needs Z_j, so
 // the exchange carries three sums (below) as FP64 records.
-template <typename R, bool MULT>
-__global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
-  __shared__ GroupShared sh;
-  __shared__ double mred[2][kWarps][3];  // general form: per-warp partials, by exchange parity
+// TPB threads per CTA, one CTA per SM: the whole GPU holds one slice's
+// particles, a few quads per thread, and the warps of the one CTA hide
+// the latency of the loads of the replayed states.
+template <typename R, bool MULT, int TPB>
+__global__ void __launch_bounds__(TPB, 1) k_adjoint(const AdjointArgs a) {
+  constexpr int NW = TPB / 32;
+  __shared__ GroupSharedT<NW> sh;
+  __shared__ double mred[2][NW][3];      // general form: per-warp partials, by exchange parity
   __shared__ double mtot[2][3];          // general form: group sums, by exchange parity
   const int G = a.G;
   const int g = blockIdx.x;
@@ -53,7 +57,7 @@ __global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
   const int qb = (int)(((long long)a.Q * g) / G);
   const int qe = (int)(((long long)a.Q * (g + 1)) / G);
   const int span = qe - qb - tid;
-  const int nq = span <= 0 ? 0 : min(a.nq, (span + kTPB - 1) / kTPB);
+  const int nq = span <= 0 ? 0 : min(a.nq, (span + TPB - 1) / TPB);
   const int qlast = a.Q - 1;
   const int plast = (int)(a.P - 4LL * qlast);
 
@@ -69,7 +73,7 @@ __global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
   grp.tight_polls = G <= a.sms ? kTightPolls : 0;
   if (tid == 0) sh.abort = 0;
 
-  QuadStore<R, 0> lam;  // mu of this thread's quads, in shared memory
+  QuadStore<R, 0, TPB> lam;  // mu of this thread's quads, in shared memory
   lam.bind();
   for (int i = 0; i < nq; ++i) {
     const R zero[4] = {0, 0, 0, 0};
@@ -163,9 +167,9 @@ __global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
   auto mult_publish = [&](unsigned e) {
     double v[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v[k] = lane < kWarps ? mred[par][lane][k] : 0.0;
+    for (int k = 0; k < 3; ++k) v[k] = lane < NW ? mred[par][lane][k] : 0.0;
 #pragma unroll
-    for (int off = kWarps / 2; off > 0; off >>= 1) {
+    for (int off = NW / 2; off > 0; off >>= 1) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
     }
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
     // ---- replay the segment from its checkpoint (thread-private) --------
     const R* ck = (const R*)a.ckpt + (size_t)seg * a.pitch;
     for (int i = 0; i < nq; ++i) {
-      const int q = qb + tid + i * kTPB;
+      const int q = qb + tid + i * TPB;
       R x[4];
       Quad<R>::load(ck + 4 * (size_t)q, x);
       for (int jj = 0; jj < L; ++jj) {
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
       // lambda_J: the last slice end's injection alone (s_J = 0); its sums are epoch 0
       R part = (R)0, pz = (R)0, zs = (R)0;
       for (int i = 0; i < nq; ++i) {
-        const int q = qb + tid + i * kTPB;
+        const int q = qb + tid + i * TPB;
         R x[4], l[4] = {0, 0, 0, 0};
         Quad<R>::load(segx + (size_t)L * a.pitch + 4 * (size_t)q, x);
         inject(a.J, q, x, l);
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
       const R mj = uni[3 * j];                  // m_j as the forward used it
       R part = (R)0, p3 = (R)0, p1 = (R)0, pb = (R)0, pB = (R)0, pz = (R)0, zs = (R)0;
       for (int i = 0; i < nq; ++i) {
-        const int q = qb + tid + i * kTPB;
+        const int q = qb + tid + i * TPB;
         R l[4], x[4], z[4];
         if constexpr (MULT) {
           Quad<R>::load(segz + (size_t)jj * a.pitch + 4 * (size_t)q, z);
@@ -422,18 +426,19 @@ __global__ void __launch_bounds__(kTPB, 2) k_adjoint(const AdjointArgs a) {
 }
 
 const void* adjoint_kernel(int precision, bool mult) {
-  if (precision == MMP_MIXED) return mult ? (const void*)k_adjoint<float, true> : (const void*)k_adjoint<float, false>;
-  return mult ? (const void*)k_adjoint<double, true> : (const void*)k_adjoint<double, false>;
+  if (precision == MMP_MIXED)
+    return mult ? (const void*)k_adjoint<float, true, kAdjTPB> : (const void*)k_adjoint<float, false, kAdjTPB>;
+  return mult ? (const void*)k_adjoint<double, true, kAdjTPB> : (const void*)k_adjoint<double, false, kAdjTPB>;
 }
 
 size_t adjoint_smem_bytes(int precision, int nq) {
-  return (size_t)nq * kTPB * 4 * (precision == MMP_MIXED ? sizeof(float) : sizeof(double));
+  return (size_t)nq * kAdjTPB * 4 * (precision == MMP_MIXED ? sizeof(float) : sizeof(double));
 }
 
 cudaError_t launch_adjoint(int precision, bool mult, const AdjointArgs& args, cudaStream_t stream) {
   AdjointArgs copy = args;
   void* params[] = {&copy};
-  return cudaLaunchCooperativeKernel(adjoint_kernel(precision, mult), dim3(args.G), dim3(kTPB), params,
+  return cudaLaunchCooperativeKernel(adjoint_kernel(precision, mult), dim3(args.G), dim3(kAdjTPB), params,
                                      adjoint_smem_bytes(precision, args.nq), stream);
 }
 

@@ -7,7 +7,8 @@
 
 namespace mmp {
 
-constexpr int kNGrad = 7;  // d/d(c3, c1, kappa, c0, B0, B, BE): MMP_N_THETA
+constexpr int kNGrad = 7;    // d/d(c3, c1, kappa, c0, B0, B, BE): MMP_N_THETA
+constexpr int kAdjTPB = 512;  // threads per CTA of the reverse kernel
 
 struct AdjointArgs {
   double nc3, c1, kappa, h, sqrt_h;  // model (nc3 = -c3), step

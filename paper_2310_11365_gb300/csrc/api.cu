@@ -787,7 +787,9 @@ int status_to_error(unsigned s) {
 // Layout of the adjoint workspace: checkpoint rows, recorded uniforms, the
 // segment buffers, cotangents, gradient and the reverse kernel's group
 // scratch; also the reverse kernel's launch shape (all particles in one
-// co-resident group, the fewest quads per thread that fit).
+// co-resident group of at most one CTA per SM, the fewest quads per thread
+// that fit, the particles spread over as many SMs as there are CTAs' worth
+// of threads).
 struct AdjLayout {
   size_t bytes = 0;
   int n_seg = 0, G = 1, nq = 1;
@@ -814,11 +816,11 @@ int adjoint_layout(mmp_ctx* c, Prob& p, int ckpt_every, char* base, AdjLayout& L
     int occ = 0;
     const size_t smem = adjoint_smem_bytes(p.d.precision, nq);
     if (smem > limit) break;
-    MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTPB, smem));
-    const long long G = ((long long)p.Q + (long long)nq * kTPB - 1) / ((long long)nq * kTPB);
+    MMP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kAdjTPB, smem));
+    const long long G = ((long long)p.Q + (long long)nq * kAdjTPB - 1) / ((long long)nq * kAdjTPB);
     if (occ >= 1 && G <= (long long)c->dev.sms) {  // about one CTA per SM (see the forward below)
       L.nq = nq;
-      L.G = (int)G;
+      L.G = (int)std::min<long long>(c->dev.sms, std::max<long long>(G, ((long long)p.Q + kAdjTPB - 1) / kAdjTPB));
       break;
     }
   }

@@ -62,10 +62,11 @@ struct Quad<double> {
 };
 
 // Per-CTA shared state of the group reductions.
-struct GroupShared {
-  double red[kWarps][kNV];    // per-warp partials of the restriction reductions
-  float2 redf[2][kWarps];     // per-warp double-float partials of the per-step sum (by step parity)
-  double redd[2][kWarps];     // the same for double particles
+template <int NW>
+struct GroupSharedT {
+  double red[NW][kNV];        // per-warp partials of the restriction reductions
+  float2 redf[2][NW];         // per-warp double-float partials of the per-step sum (by step parity)
+  double redd[2][NW];         // the same for double particles
   float2 gsumf[2];            // group sum of a step, handed from warp 0 to the CTA (by parity)
   double gsumd[2];
   double tot[kNV];            // group totals, broadcast
@@ -78,12 +79,21 @@ struct GroupShared {
   float rotf[2];              // the same rounded to float
   int abort;
 };
+// The fine kernels' CTAs have kWarps warps.
+using GroupShared = GroupSharedT<kWarps>;
 
 // A compile-time region count (the prologue and the epilogue are compiled
 // for at most 2 and for at most 4 regions; a task takes the first when it can).
 template <int N>
 struct RegionsUpTo {
   static constexpr int value = N;
+};
+
+// A compile-time switch (the step body is compiled with and without the
+// checkpoint store, so that no branch splits the unrolled quads).
+template <bool B>
+struct Switch {
+  static constexpr bool value = B;
 };
 
 // Region index of x: D_0 = {x < t1}, D_i = {t_i <= x < t_{i+1}}, D_{I-1} = {x >= t_{I-1}}.
@@ -170,8 +180,8 @@ __device__ __forceinline__ bool group_wait(const Group& grp, unsigned e) {
 // min_mask / max_mask select values combined by min / max (all others are
 // summed).  Every thread of the CTA advances grp.epoch past e itself.
 // Returns false if the wait gave up.
-template <int NV>
-__device__ __forceinline__ bool group_finish(GroupShared& sh, const Group& grp, unsigned e, unsigned min_mask,
+template <int NV, int NW>
+__device__ __forceinline__ bool group_finish(GroupSharedT<NW>& sh, const Group& grp, unsigned e, unsigned min_mask,
                                              unsigned max_mask) {
   const int lane = threadIdx.x & 31;
   auto comb = [&](int k, double x, double o) {
@@ -182,9 +192,9 @@ __device__ __forceinline__ bool group_finish(GroupShared& sh, const Group& grp, 
   };
   double v[NV];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = lane < kWarps ? sh.red[lane][k] : ident(k);
+  for (int k = 0; k < NV; ++k) v[k] = lane < NW ? sh.red[lane][k] : ident(k);
 #pragma unroll
-  for (int off = kWarps / 2; off > 0; off >>= 1) {
+  for (int off = NW / 2; off > 0; off >>= 1) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = comb(k, v[k], __shfl_xor_sync(0xffffffffu, v[k], off));
   }
@@ -303,8 +313,10 @@ struct StepSum<float> {
   static __device__ __forceinline__ T bcast0(T v) {
     return make_float2(__shfl_sync(0xffffffffu, v.x, 0), __shfl_sync(0xffffffffu, v.y, 0));
   }
-  static __device__ __forceinline__ T* warp_slots(GroupShared& sh, int parity) { return sh.redf[parity]; }
-  static __device__ __forceinline__ T& gsum(GroupShared& sh, int parity) { return sh.gsumf[parity]; }
+  template <class SH>
+  static __device__ __forceinline__ T* warp_slots(SH& sh, int parity) { return sh.redf[parity]; }
+  template <class SH>
+  static __device__ __forceinline__ T& gsum(SH& sh, int parity) { return sh.gsumf[parity]; }
   static __device__ __forceinline__ uint32_t tag_of(unsigned e) { return 0x8000u | ((e + 1u) & 0x7FFFu); }
   // one thread: the CTA's value of epoch e as a tagged word
   static __device__ __forceinline__ void publish(const Group& grp, unsigned e, T v) {
@@ -379,8 +391,10 @@ struct StepSum<double> {
   static __device__ __forceinline__ T add(T a, T b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ T shfl_xor(T v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
   static __device__ __forceinline__ T bcast0(T v) { return __shfl_sync(0xffffffffu, v, 0); }
-  static __device__ __forceinline__ T* warp_slots(GroupShared& sh, int parity) { return sh.redd[parity]; }
-  static __device__ __forceinline__ T& gsum(GroupShared& sh, int parity) { return sh.gsumd[parity]; }
+  template <class SH>
+  static __device__ __forceinline__ T* warp_slots(SH& sh, int parity) { return sh.redd[parity]; }
+  template <class SH>
+  static __device__ __forceinline__ T& gsum(SH& sh, int parity) { return sh.gsumd[parity]; }
   // one thread: the CTA's value of epoch e in its record slot, then its flag
   static __device__ __forceinline__ void publish(const Group& grp, unsigned e, T v) {
     __stcg(group_slot(grp, grp.g, e), v);
@@ -401,8 +415,8 @@ struct StepSum<double> {
 
 // Per-warp stage: butterfly of the per-thread sums, lane 0 stores the warp's
 // partial into the slot array of the step's parity.
-template <typename R>
-__device__ __forceinline__ void step_sum_warp(GroupShared& sh, int parity, R s) {
+template <typename R, int NW>
+__device__ __forceinline__ void step_sum_warp(GroupSharedT<NW>& sh, int parity, R s) {
   using S = StepSum<R>;
   typename S::T v = S::of(s);
 #pragma unroll
@@ -412,19 +426,19 @@ __device__ __forceinline__ void step_sum_warp(GroupShared& sh, int parity, R s) 
 
 // Every warp, after the CTA barrier that follows step_sum_warp: the CTA's
 // sum (warps in index order; the same value in every warp and lane).
-template <typename R>
-__device__ __forceinline__ typename StepSum<R>::T step_sum_cta(GroupShared& sh, int parity) {
+template <typename R, int NW>
+__device__ __forceinline__ typename StepSum<R>::T step_sum_cta(GroupSharedT<NW>& sh, int parity) {
   using S = StepSum<R>;
   const int lane = threadIdx.x & 31;
-  typename S::T v = lane < kWarps ? S::warp_slots(sh, parity)[lane] : S::zero();
+  typename S::T v = lane < NW ? S::warp_slots(sh, parity)[lane] : S::zero();
 #pragma unroll
-  for (int off = kWarps / 2; off > 0; off >>= 1) v = S::add(v, S::shfl_xor(v, off));
+  for (int off = NW / 2; off > 0; off >>= 1) v = S::add(v, S::shfl_xor(v, off));
   return S::bcast0(v);
 }
 
 // General per-warp stage of nv double values.
-template <int NV>
-__device__ __forceinline__ void warp_reduce_to_shared(GroupShared& sh, double v[NV], unsigned min_mask,
+template <int NV, int NW>
+__device__ __forceinline__ void warp_reduce_to_shared(GroupSharedT<NW>& sh, double v[NV], unsigned min_mask,
                                                       unsigned max_mask) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -442,12 +456,13 @@ __device__ __forceinline__ void warp_reduce_to_shared(GroupShared& sh, double v[
 
 // Where a thread keeps its quads of particles between steps.
 // NQ > 0: in registers, NQ quads (loops over quads fully unrolled).
-// NQ == 0: in dynamic shared memory, a.nq quads at stride kTPB quads, so a
-// warp touches 512 contiguous bytes per quad (conflict-free 16-byte
-// accesses) and registers stay few, which lets more CTAs share an SM.
+// NQ == 0: in dynamic shared memory, a.nq quads at stride TPB quads (the
+// CTA's threads), so a warp touches 512 contiguous bytes per quad
+// (conflict-free 16-byte accesses) and registers stay few, which lets more
+// CTAs share an SM.
 extern __shared__ __align__(16) unsigned char mmp_fine_smem[];
 
-template <typename R, int NQ>
+template <typename R, int NQ, int TPB = kTPB>
 struct QuadStore {
   R x[NQ][4];
   __device__ __forceinline__ void bind() {}
@@ -460,12 +475,12 @@ struct QuadStore {
     for (int w = 0; w < 4; ++w) x[i][w] = v[w];
   }
 };
-template <typename R>
-struct QuadStore<R, 0> {
+template <typename R, int TPB>
+struct QuadStore<R, 0, TPB> {
   R* base;
   __device__ __forceinline__ void bind() { base = reinterpret_cast<R*>(mmp_fine_smem) + 4 * threadIdx.x; }
-  __device__ __forceinline__ void get(int i, R v[4]) const { Quad<R>::load(base + 4 * (size_t)i * kTPB, v); }
-  __device__ __forceinline__ void put(int i, const R v[4]) { Quad<R>::store(base + 4 * (size_t)i * kTPB, v); }
+  __device__ __forceinline__ void get(int i, R v[4]) const { Quad<R>::load(base + 4 * (size_t)i * TPB, v); }
+  __device__ __forceinline__ void put(int i, const R v[4]) { Quad<R>::store(base + 4 * (size_t)i * TPB, v); }
 };
 
 // Resident CTAs per SM the register budget is sized for.  Register layout:
@@ -905,39 +920,46 @@ __device__ __forceinline__ bool fine_task(const FineArgs& a, const int n, const 
         u[2] = boff;
       }
     }
-    R s = (R)0;
+    // the step over this thread's quads, with (CK) or without the
+    // checkpoint row of the step's states
+    auto step_quads = [&](auto ck_c) -> R {
+      constexpr bool CK = decltype(ck_c)::value;
+      R sq = (R)0;
 #pragma unroll kStepUnroll
-    for (int i = 0; i < loop_n; ++i) {
-      if (i < nq) {
-        const uint32_t q = (uint32_t)(qb + tid + i * kTPB);
-        R v[4];
-        xs.get(i, v);
-        const uint4 o = philox4x32_10(rng_counter(q, (uint32_t)j, (uint32_t)n, 0u, a.ptag), a.key0, a.key1);
-        if constexpr (kLag) {
-          R nr[2], c[2], sn[2];
-          normals4_polar<R>(o, nr, c, sn);
+      for (int i = 0; i < loop_n; ++i) {
+        if (i < nq) {
+          const uint32_t q = (uint32_t)(qb + tid + i * kTPB);
+          R v[4];
+          xs.get(i, v);
+          const uint4 o = philox4x32_10(rng_counter(q, (uint32_t)j, (uint32_t)n, 0u, a.ptag), a.key0, a.key1);
+          if constexpr (kLag) {
+            R nr[2], c[2], sn[2];
+            normals4_polar<R>(o, nr, c, sn);
 #pragma unroll
-          for (int w = 0; w < 4; ++w) v[w] = addR(v[w], d);  // x_j = y_{j-1} + d_{j-1}
-          if (ckpt) Quad<R>::store(ck_row + 4 * (size_t)q, v);
-          em_partial_pair(v[0], v[1], nr[0], c[0], sn[0], hn3, hc1, b0sq);
-          em_partial_pair(v[2], v[3], nr[1], c[1], sn[1], hn3, hc1, b0sq);
-        } else {
-          if (ckpt) Quad<R>::store(ck_row + 4 * (size_t)q, v);
-          R z[4];
-          normals4<R>(o, z);
+            for (int w = 0; w < 4; ++w) v[w] = addR(v[w], d);  // x_j = y_{j-1} + d_{j-1}
+            if constexpr (CK) Quad<R>::store(ck_row + 4 * (size_t)q, v);
+            em_partial_pair(v[0], v[1], nr[0], c[0], sn[0], hn3, hc1, b0sq);
+            em_partial_pair(v[2], v[3], nr[1], c[1], sn[1], hn3, hc1, b0sq);
+          } else {
+            if constexpr (CK) Quad<R>::store(ck_row + 4 * (size_t)q, v);
+            R z[4];
+            normals4<R>(o, z);
 #pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            const R xv = v[w];
-            const R drift = fmaR(fmaR(nc3, mulR(xv, xv), c1), xv, base);
-            const R amp = fmaR(bsq, xv, boff);
-            v[w] = fmaR(amp, z[w], fmaR(h, drift, xv));
+            for (int w = 0; w < 4; ++w) {
+              const R xv = v[w];
+              const R drift = fmaR(fmaR(nc3, mulR(xv, xv), c1), xv, base);
+              const R amp = fmaR(bsq, xv, boff);
+              v[w] = fmaR(amp, z[w], fmaR(h, drift, xv));
+            }
           }
+          // lanes past P evolve like particles; their values leave the sum below
+          sq = addR(sq, addR(addR(v[0], v[1]), addR(v[2], v[3])));
+          xs.put(i, v);
         }
-        // lanes past P evolve like particles; their values leave the sum below
-        s = addR(s, addR(addR(v[0], v[1]), addR(v[2], v[3])));
-        xs.put(i, v);
       }
-    }
+      return sq;
+    };
+    R s = ckpt ? step_quads(Switch<true>{}) : step_quads(Switch<false>{});
     if (tail_i >= 0) {
       // the lanes past P of the ragged last quad (this thread's, if any)
       // leave the sum: they evolve like particles but are none

@@ -1,7 +1,8 @@
 """Resource budget of the hot kernels as ptxas reported it when the library
-was compiled (no GPU needed): the launches run 256-thread CTAs two to an SM,
-so a kernel that needs more than 128 registers a thread, or spills to local
-memory, loses occupancy or bandwidth before it ever runs."""
+was compiled (no GPU needed): the fine kernels run 256-thread CTAs two to an
+SM and the adjoint's reverse kernel 512-thread CTAs one to an SM, so a kernel
+that needs more than 128 registers a thread, or spills to local memory, loses
+occupancy or bandwidth before it ever runs."""
 import re
 
 import pytest
@@ -28,7 +29,7 @@ def _select(usage, pattern):
     (r"_ZN3mmp6k_fineIdLi0ELb[01]ELi0EEEvNS_8FineArgsE", "FP64 fine kernels (shared-memory layout, both noise forms)"),
     (r"_ZN3mmp6k_fineI[fd]Li0ELb0ELi1EEEvNS_8FineArgsE", "plane-rotator fine kernels (mixed and FP64)"),
     (r"_ZN3mmp12k_fine_batchIfLb[01]EEEvNS_9BatchArgsE", "mixed batched fine kernels"),
-    (r"_ZN3mmp9k_adjointI[fd]Lb[01]EEEvNS_11AdjointArgsE", "adjoint reverse kernels"),
+    (r"_ZN3mmp9k_adjointI[fd]Lb[01]ELi512EEEvNS_11AdjointArgsE", "adjoint reverse kernels (512 threads)"),
 ])
 def test_hot_kernels_fit_two_ctas_per_sm_without_spills(usage, pattern, what):
     for name, rec in _select(usage, pattern).items():
