@@ -798,6 +798,18 @@ def main():
     cfg3 = None if args.no_cfg3 or overrides else config3_run()
     cfg4 = None if args.no_cfg4 or overrides else config4_run()
 
+    # the same step's arithmetic without the cross-CTA exchange (the fine
+    # kernel's step loop measured against it), after the timed region
+    fine_rate = steps_done / fine_s
+    ceil_regs = mmp.mmp_probe_step(0)
+    ceil_smem = mmp.mmp_probe_step(1)
+    step_ceiling = {"registers_no_sync": ceil_regs, "shared_memory_cta_barrier": ceil_smem,
+                    "unit": "particle-steps/s", "fine_kernel_rate": fine_rate,
+                    "fine_kernel_frac_of_shared_memory_form": fine_rate / ceil_smem,
+                    "arithmetic_frac_of_lane_peak": ALG_OPS_PER_PARTICLE_STEP * ceil_regs / 1e12 / peak,
+                    "how": "mmp_probe_step: the additive-noise mixed step (same device functions), 2 CTAs x 256 "
+                           "threads per SM, particles on chip, no cross-CTA exchange; CUDA events"}
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         ttt = oracle_ttt.get(timeout=1800)
@@ -829,7 +841,8 @@ def main():
                          "kernel": "k_fine<float>", "ops_per_particle_step": ALG_OPS_PER_PARTICLE_STEP,
                          "fine_launches": tm["fine_launches"],
                          "fine_ms_per_launch": tm["fine_ms"] / max(1, tm["fine_launches"]),
-                         "peak_note": "152 SMs x 128 FP32/INT32 lanes x max SM clock (MEASURED_PEAKS sm_max_mhz)"},
+                         "peak_note": "152 SMs x 128 FP32/INT32 lanes x max SM clock (MEASURED_PEAKS sm_max_mhz)",
+                         "step_ceiling": step_ceiling},
             "e2e": e2e,
             "fp64_plain": fp64,
             "accuracy_vs_own_serial": accuracy,

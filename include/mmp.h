@@ -395,6 +395,22 @@ int mmp_sweep_info(mmp_ctx* ctx, int prob, double* out);
  * at least (a sink the kernel never writes in practice).  Synchronising. */
 int mmp_probe_fma(int precision, void* ws, size_t ws_bytes, void* stream, double* tflops);
 
+/* Throughput, in particle-steps/s, of the fine step's arithmetic without the
+ * cross-CTA exchange of the mean: the mixed-precision additive-noise
+ * Euler-Maruyama step (Eq. Euler_Maruyama with the draws of Philox-4x32-10
+ * and Box-Muller, the per-step sum of the particles) evaluated by the same
+ * device functions as the fine kernel, two 256-thread CTAs per SM, on
+ * particles that stay on chip for every step.  form 0: 4 quads (16
+ * particles) per thread in registers, no synchronisation; form 1: 26 quads
+ * per thread in shared memory, the fine kernel's layout, with a warp
+ * butterfly and a CTA barrier every step.  One launch of about 2.5e10
+ * particle-steps timed with CUDA events after a warm-up launch; the fused
+ * fine kernel's step loop is measured against it (the paper has no
+ * counterpart).  ws: device, 256-byte aligned, 8 bytes at least (a sink the
+ * kernel never writes in practice).  MMP_ERR_INVALID_ARG for another form
+ * or a null result pointer.  Synchronising. */
+int mmp_probe_step(int form, void* ws, size_t ws_bytes, void* stream, double* particle_steps_per_s);
+
 /* One problem's slices on several GPUs.  Within a Parareal iteration the
  * fine propagations of the slices are independent (Sec. 3.1: the parallel
  * step of Parareal), so the slices can be split into contiguous blocks, one

@@ -23,6 +23,9 @@ static_assert(mmp::kNGrad == MMP_N_THETA, "adjoint gradient length");
 
 namespace mmp {
 cudaError_t launch_fma_probe(int precision, void* sink, long long iters, int grid, cudaStream_t stream);
+int step_probe_quads(int form);
+cudaError_t prepare_step_probe(int form);
+cudaError_t launch_step_probe(int form, float* sink, int steps, int grid, cudaStream_t stream);
 cudaError_t launch_wait_probe(double* partials, unsigned* flags, unsigned long long* tags, unsigned* status, int G,
                               unsigned long long limit_ns, int channel, cudaStream_t stream);
 const void* fine_kernel_f32(int nq, bool mult, int family);
@@ -2077,6 +2080,43 @@ int mmp_probe_fma(int precision, void* ws, size_t ws_bytes, void* stream, double
   MMP_CUDA(se);
   MMP_CUDA(te);
   *tflops = 2.0 * 8.0 * (double)threads * (double)iters / ((double)ms * 1e-3) / 1e12;
+  return MMP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The fine step's arithmetic without the cross-CTA exchange (mmp_probe_step):
+// the ceiling the fused fine kernel's step loop is compared against.
+// ---------------------------------------------------------------------------
+int mmp_probe_step(int form, void* ws, size_t ws_bytes, void* stream, double* particle_steps_per_s) {
+  if (form != 0 && form != 1) return MMP_ERR_INVALID_ARG;
+  if (particle_steps_per_s == nullptr) return MMP_ERR_INVALID_ARG;
+  if (ws == nullptr || ((uintptr_t)ws % kAlign) != 0 || ws_bytes < 8) return MMP_ERR_WORKSPACE;
+  Range nvtx_range("mmp_probe_step");
+  Device dev;
+  int rc = query_device(dev);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  MMP_CUDA(prepare_step_probe(form));
+  const int grid = dev.sms * 2;  // two CTAs per SM, as the fine kernel runs
+  const double particles = (double)grid * kTPB * 4.0 * step_probe_quads(form);
+  const int steps = (int)std::max(1.0, 2.5e10 / particles);  // about 2.5e10 particle-steps per launch
+  MMP_CUDA(launch_step_probe(form, (float*)ws, steps / 10 + 1, grid, s));  // warm-up
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  MMP_CUDA(cudaEventCreate(&e0));
+  MMP_CUDA(cudaEventCreate(&e1));
+  MMP_CUDA(cudaEventRecord(e0, s));
+  cudaError_t le = launch_step_probe(form, (float*)ws, steps, grid, s);
+  cudaError_t re = cudaEventRecord(e1, s);
+  cudaError_t se = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  cudaError_t te = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  MMP_CUDA(le);
+  MMP_CUDA(re);
+  MMP_CUDA(se);
+  MMP_CUDA(te);
+  *particle_steps_per_s = particles * (double)steps / ((double)ms * 1e-3);
   return MMP_OK;
 }
 

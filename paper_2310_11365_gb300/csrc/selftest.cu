@@ -73,3 +73,96 @@ cudaError_t launch_fma_probe(int precision, void* sink, long long iters, int gri
 }
 
 }  // namespace mmp
+
+namespace mmp {
+
+// Ceiling of the fine step's arithmetic without the cross-CTA exchange
+// (mmp_probe_step): the additive-noise step of float particles exactly as
+// the fine kernel evaluates it (Philox-4x32-10, the polar Box-Muller form,
+// the mean-free partial step, the pending shift and the per-thread sum),
+// on particles that stay on chip for every step.
+//   form 0: kProbeQuads quads per thread in registers, no synchronisation;
+//   form 1: nq quads per thread in dynamic shared memory (the fine kernel's
+//           layout) with a warp butterfly and a CTA barrier every step.
+// The sums are stored only if they take a value they never take, which
+// keeps every chain alive.
+constexpr int kProbeQuads = 4;
+
+struct StepProbeCoef {
+  uint32_t k0, k1;
+  float hn3, hc1, amp, d;
+};
+
+template <bool SMEM>
+__global__ void __launch_bounds__(kTPB, 2) k_step_probe(float* sink, int steps, int nq, StepProbeCoef cf) {
+  __shared__ float red[kWarps];
+  constexpr int NQ = SMEM ? 0 : kProbeQuads;
+  QuadStore<float, NQ> xs;
+  xs.bind();
+  const int loop_n = SMEM ? nq : kProbeQuads;
+#pragma unroll kProbeQuads
+  for (int i = 0; i < loop_n; ++i) {
+    float v[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) v[w] = 0.01f * (float)(w + 1 + (threadIdx.x & 7));
+    xs.put(i, v);
+  }
+  const uint32_t q0 = blockIdx.x * kTPB * loop_n + threadIdx.x;
+  float acc = 0.0f;
+  float d = cf.d;
+  for (int j = 0; j < steps; ++j) {
+    float s = 0.0f;
+#pragma unroll kStepUnrollSmem
+    for (int i = 0; i < loop_n; ++i) {
+      float v[4];
+      xs.get(i, v);
+      const uint4 o = philox4x32_10(rng_counter(q0 + i * kTPB, (uint32_t)j, 0u, 0u, 7u), cf.k0, cf.k1);
+      float nr[2], c[2], sn[2];
+      normals4_polar<float>(o, nr, c, sn);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) v[w] = addR(v[w], d);
+      em_partial_pair(v[0], v[1], nr[0], c[0], sn[0], cf.hn3, cf.hc1, cf.amp);
+      em_partial_pair(v[2], v[3], nr[1], c[1], sn[1], cf.hn3, cf.hc1, cf.amp);
+      s = addR(s, addR(addR(v[0], v[1]), addR(v[2], v[3])));
+      xs.put(i, v);
+    }
+    if (SMEM) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+      __syncthreads();
+      float t = 0.0f;
+#pragma unroll
+      for (int k = 0; k < kWarps; ++k) t += red[k];
+      d = cf.d + 1e-12f * t;
+      __syncthreads();
+    }
+    acc += s;
+  }
+  if (acc == -1.25e-30f) sink[0] = acc;
+}
+
+int step_probe_quads(int form) { return form == 0 ? kProbeQuads : 26; }
+
+size_t step_probe_smem(int form) {
+  return form == 0 ? 0 : (size_t)kTPB * step_probe_quads(form) * 4 * sizeof(float);
+}
+
+cudaError_t prepare_step_probe(int form) {
+  if (form == 0) return cudaSuccess;
+  return cudaFuncSetAttribute(k_step_probe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)step_probe_smem(form));
+}
+
+cudaError_t launch_step_probe(int form, float* sink, int steps, int grid, cudaStream_t stream) {
+  const float h = 1e-3f;
+  // the config-2 model: c3 = 1, c1 = -1, sigma = 0.5, dt = 1e-3
+  const StepProbeCoef cf{0x1234567u, 0x89abcdefu, -h, -h, 0.5f * sqrtf(h), 0.05f * h};
+  if (form == 0)
+    k_step_probe<false><<<grid, kTPB, 0, stream>>>(sink, steps, kProbeQuads, cf);
+  else
+    k_step_probe<true><<<grid, kTPB, step_probe_smem(form), stream>>>(sink, steps, step_probe_quads(form), cf);
+  return cudaGetLastError();
+}
+
+}  // namespace mmp

@@ -51,7 +51,7 @@ EXPORTED = [
     "mmp_batch_info", "mmp_autotune_workspace_size", "mmp_autotune", "mmp_set_tuning", "mmp_set_batch_nq",
     "mmp_state_size", "mmp_get_state", "mmp_set_state", "mmp_probe_wait",
     "mmp_sweep_fine", "mmp_sweep_coarse", "mmp_get_records", "mmp_set_records", "mmp_get_output", "mmp_set_output",
-    "mmp_sweep_info", "mmp_probe_fma",
+    "mmp_sweep_info", "mmp_probe_fma", "mmp_probe_step",
 ]
 
 
@@ -139,6 +139,7 @@ def load():
         "mmp_set_output": ([vp, i, i, vp, i], i),
         "mmp_sweep_info": ([vp, i, d], i),
         "mmp_probe_fma": ([i, vp, C.c_size_t, vp, d], i),
+        "mmp_probe_step": ([i, vp, C.c_size_t, vp, d], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -405,6 +406,19 @@ def mmp_probe_fma(precision: str, stream=None) -> float:
     _check(load().mmp_probe_fma(prec, sink.data_ptr(), sink.numel(), _stream_handle(stream), C.byref(tf)),
            "mmp_probe_fma")
     return tf.value
+
+
+def mmp_probe_step(form: int, stream=None) -> float:
+    """Particle-steps/s of the fine step's arithmetic without the cross-CTA
+    exchange: form 0 with the particles in registers, form 1 in shared
+    memory with a CTA barrier every step (the fine kernel's layout)."""
+    import torch
+
+    sink = torch.empty(64, dtype=torch.uint8, device="cuda")
+    r = C.c_double()
+    _check(load().mmp_probe_step(int(form), sink.data_ptr(), sink.numel(), _stream_handle(stream), C.byref(r)),
+           "mmp_probe_step")
+    return r.value
 
 
 def mmp_probe_wait(channel: int, G: int, limit_ms: float, ws_ptr: int, ws_bytes: int, stream=None):

@@ -149,6 +149,19 @@ def test_probe_wait_arguments_checked_on_the_host(mmplib):
     assert lib.mmp_probe_wait(0, 2, 20.0, 4096, 2 * 548 + 3, None, None) == -2
 
 
+def test_probe_step_arguments_checked_on_the_host(mmplib):
+    import ctypes as C
+
+    lib = mmplib.load()
+    r = C.c_double()
+    assert lib.mmp_probe_step(2, 4096, 64, None, C.byref(r)) == -1
+    assert lib.mmp_probe_step(-1, 4096, 64, None, C.byref(r)) == -1
+    assert lib.mmp_probe_step(0, 4096, 64, None, None) == -1
+    assert lib.mmp_probe_step(1, None, 64, None, C.byref(r)) == -2
+    assert lib.mmp_probe_step(1, 4096 + 16, 64, None, C.byref(r)) == -2
+    assert lib.mmp_probe_step(0, 4096, 4, None, C.byref(r)) == -2
+
+
 def test_normals_arguments_checked_on_the_host(mmplib):
     """mmp_normals refuses a misaligned output, an oversized count, a tag
     past 8 bits and a slice past 24 bits before any launch."""
