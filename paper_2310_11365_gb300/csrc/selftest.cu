@@ -89,7 +89,7 @@ namespace mmp {
 constexpr int kProbeQuads = 4;
 
 struct StepProbeCoef {
-  uint32_t k0, k1;
+  uint32_t k0, k1, n, tag;  // Philox key, slice index and problem tag (runtime values, as in the fine kernel)
   float hn3, hc1, amp, d;
 };
 
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kTPB, 2) k_step_probe(float* sink, int steps, 
     for (int i = 0; i < loop_n; ++i) {
       float v[4];
       xs.get(i, v);
-      const uint4 o = philox4x32_10(rng_counter(q0 + i * kTPB, (uint32_t)j, 0u, 0u, 7u), cf.k0, cf.k1);
+      const uint4 o = philox4x32_10(rng_counter(q0 + i * kTPB, (uint32_t)j, cf.n, 0u, cf.tag), cf.k0, cf.k1);
       float nr[2], c[2], sn[2];
       normals4_polar<float>(o, nr, c, sn);
 #pragma unroll
@@ -157,7 +157,7 @@ cudaError_t prepare_step_probe(int form) {
 cudaError_t launch_step_probe(int form, float* sink, int steps, int grid, cudaStream_t stream) {
   const float h = 1e-3f;
   // the config-2 model: c3 = 1, c1 = -1, sigma = 0.5, dt = 1e-3
-  const StepProbeCoef cf{0x1234567u, 0x89abcdefu, -h, -h, 0.5f * sqrtf(h), 0.05f * h};
+  const StepProbeCoef cf{0x1234567u, 0x89abcdefu, 3u, 7u, -h, -h, 0.5f * sqrtf(h), 0.05f * h};
   if (form == 0)
     k_step_probe<false><<<grid, kTPB, 0, stream>>>(sink, steps, kProbeQuads, cf);
   else
