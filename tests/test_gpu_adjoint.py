@@ -51,6 +51,25 @@ def test_adjoint_fp64_matches_oracle(mmplib, orc, ckpt_every, general):
     assert np.max(np.abs(g - g_ref) / scale) < 1e-10, (g, g_ref)
 
 
+@pytest.mark.parametrize("general", [False, True])
+def test_adjoint_fp64_whole_gpu_shape_matches_oracle(mmplib, orc, general):
+    """The reverse kernel's launch shape at a million particles (one
+    512-thread CTA on every SM, three or four quads per thread, a ragged last
+    quad) with a checkpoint interval that crosses slice ends: FP64 GPU
+    adjoint = oracle adjoint to 1e-10 relative."""
+    p = W.double_well(0.25, 0.5, 0.1, 0.7, m0=0.2, s0=0.5, T=0.2, N=2, dt=0.01, P=1_000_003, seed=29,
+                      precision="fp64")
+    if general:
+        p = _general(p)
+    rng = np.random.default_rng(2)
+    gm, gv = rng.normal(size=p.N), rng.normal(size=p.N)
+    g_ref, mom_ref = orc.adjoint(p, gm, gv)
+    g, mom = _gpu_adjoint(p, gm, gv, 7)
+    assert np.allclose(mom, mom_ref, rtol=1e-11, atol=1e-13)
+    scale = np.maximum(np.abs(g_ref), 1e-12)
+    assert np.max(np.abs(g - g_ref) / scale) < 1e-10, (g, g_ref)
+
+
 def test_adjoint_fp64_config4_loss_gradient(mmplib, orc):
     """Config-4 loss L = sum (M - m*)^2 + (V - v*)^2 on the double-well model
     (targets from a run at (kappa, sigma) = (0.15, 0.65)), reduced to
