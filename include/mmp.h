@@ -247,10 +247,12 @@ int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta, int n_theta);
  *
  * mmp_adjoint_workspace_size: bytes of caller-owned device workspace for a
  * checkpoint every `ckpt_every` fine steps: one particle row per checkpoint,
- * 3 recorded values per step, ckpt_every + 1 state rows and ckpt_every
- * draw rows for the segment being reversed (the draw rows are used with B
- * or BE nonzero; with additive noise the reverse sweep regenerates the
- * draws; the size does not depend on the form).
+ * 3 recorded values per step, two buffers of ckpt_every + 1 state rows and
+ * ckpt_every draw rows (with additive noise the reverse sweep replays the
+ * next segment into the second state buffer while it reverses one, and
+ * regenerates the draws; with B or BE nonzero it replays each segment,
+ * draws included, before reversing it; the size does not depend on the
+ * form).
  *
  * mmp_adjoint_forward: runs the serial fine propagation from u0 with the
  * current coefficients, recording checkpoints and per-step mean-field values
@@ -263,7 +265,7 @@ int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta, int n_theta);
  * (the derivatives in B and BE are those at the current values, zero
  * included).  Needs the workspace of the last forward run of this problem
  * (else MMP_ERR_STATE).  Each segment of ckpt_every steps is recomputed
- * from its checkpoint with the same draws, then reversed with one group
+ * from its checkpoint with the same draws and reversed with one group
  * exchange of the adjoint per step (one sum for additive noise; with B or
  * BE nonzero also the sums that form Z_j = sum_p lambda_{j+1,p} xi_{j,p}).
  * Synchronising. */

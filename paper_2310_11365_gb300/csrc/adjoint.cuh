@@ -25,7 +25,7 @@ struct AdjointArgs {
   const void* ckpt;                  // rows at steps 0, c, 2c, ... (n_seg rows)
   const void* uni;                   // [J][3] recorded per step: (m_j, h (kappa m_j + c0), B0 sqrt h) for
                                      // additive noise, (m_j, kappa m_j + c0, (BE m_j + B0) sqrt h) otherwise
-  void* segx;                        // (c + 1) rows: states of the segment being reversed
+  void* segx;                        // 2 x (c + 1) rows: replayed states, two segment buffers
   void* segz;                        // c rows: its normal draws
   const double* mom;                 // [(N+1)][kStat] restriction records of the serial run
   const double* gm;                  // [N] cotangents of the slice-end means (n = 1..N)
