@@ -248,11 +248,10 @@ int mmp_set_params(mmp_ctx* ctx, int prob, const double* theta, int n_theta);
  * mmp_adjoint_workspace_size: bytes of caller-owned device workspace for a
  * checkpoint every `ckpt_every` fine steps: one particle row per checkpoint,
  * 3 recorded values per step, two buffers of ckpt_every + 1 state rows and
- * ckpt_every draw rows (with additive noise the reverse sweep replays the
- * next segment into the second state buffer while it reverses one, and
- * regenerates the draws; with B or BE nonzero it replays each segment,
- * draws included, before reversing it; the size does not depend on the
- * form).
+ * two of ckpt_every draw rows (the reverse sweep replays the next segment
+ * into the second buffers while it reverses one; the draw rows are used
+ * with B or BE nonzero, additive noise regenerating its draws; the size
+ * does not depend on the form).
  *
  * mmp_adjoint_forward: runs the serial fine propagation from u0 with the
  * current coefficients, recording checkpoints and per-step mean-field values

@@ -199,38 +199,58 @@ __global__ void __launch_bounds__(TPB, 1) k_adjoint(const AdjointArgs a) {
     }
   };
 
-  // Segment buffers of replayed states: the general form replays a segment
-  // before reversing it, into one buffer (with its draws).  The additive
-  // form keeps two: while the group reverses segment s (reading buffer
-  // s & 1), warps 1.. replay segment s - 1 into the other, one step per
-  // reverse step, in the time warp 0 waits for the peers' sums; only the
-  // last segment is replayed on its own.  The replayed values are the same
-  // either way (each quad's steps run in order through the same
-  // arithmetic); a replayed quad is carried from step to step through its
-  // row of the buffer.
-  auto buf = [&](int sg) -> R* {
-    return MULT ? segx : segx + (size_t)(sg & 1) * (size_t)(a.c + 1) * (size_t)a.pitch;
-  };
+  // Two buffers of a segment's replayed states (and, for the general form,
+  // its draws).  While the group reverses segment s (reading buffer s & 1),
+  // warps 1.. replay segment s - 1 into the other, one step per reverse
+  // step, in the time warp 0 waits for the peers' sums; only the last
+  // segment is replayed on its own.  The replayed values are those of a
+  // replay done before the reverse sweep (each quad's steps run in order
+  // through the same arithmetic); a replayed quad is carried from step to
+  // step through its row of the buffer.
+  auto buf = [&](int sg) -> R* { return segx + (size_t)(sg & 1) * (size_t)(a.c + 1) * (size_t)a.pitch; };
+  auto bufz = [&](int sg) -> R* { return segz + (size_t)(sg & 1) * (size_t)a.c * (size_t)a.pitch; };
   const int n_rep = TPB - 32;  // replay threads (warps 1..)
   const int rt = tid - 32;     // this thread's replay index (negative in warp 0)
-  // additive form: x at global step j -> x at step j + 1, as the forward stepped it
-  auto replay_step = [&](int q, long long j, R x[4]) {
-    R nr[2], c[2], sn[2];
-    normals4_polar<R>(philox4x32_10(rng_counter((uint32_t)q, (uint32_t)(j % a.nf), (uint32_t)(j / a.nf), 0u,
-                                                a.ptag), a.key0, a.key1), nr, c, sn);
-    const R d = uni[3 * j + 1];    // h (kappa m_j + c0) as the forward used it
-    const R amp = uni[3 * j + 2];  // B0 sqrt(h) as the forward used it
-    em_partial_pair(x[0], x[1], nr[0], c[0], sn[0], hn3, hc1, amp);
-    em_partial_pair(x[2], x[3], nr[1], c[1], sn[1], hn3, hc1, amp);
+  // x at global step j -> x at step j + 1, as the forward stepped it; the
+  // general form also stores the step's draws at zdst
+  auto replay_step = [&](int q, long long j, R x[4], R* zdst) {
+    const uint4 o = philox4x32_10(
+        rng_counter((uint32_t)q, (uint32_t)(j % a.nf), (uint32_t)(j / a.nf), 0u, a.ptag), a.key0, a.key1);
+    if constexpr (MULT) {
+      // x + h (nc3 x^3 + c1 x + kappa m_j + c0) + (B sqrt(h) x + (BE m_j + B0) sqrt(h)) xi,
+      // rounded as the forward's general form rounds it
+      R z[4];
+      normals4<R>(o, z);
+      zero_tail(q, z);
+      Quad<R>::store(zdst + 4 * (size_t)q, z);
+      const R base = uni[3 * j + 1];  // kappa m_j + c0 as the forward used it
+      const R boff = uni[3 * j + 2];  // (BE m_j + B0) sqrt(h) as the forward used it
 #pragma unroll
-    for (int w = 0; w < 4; ++w) x[w] = addR(x[w], d);
+      for (int w = 0; w < 4; ++w) {
+        const R xv = x[w];
+        const R drift = fmaR(fmaR(nc3, mulR(xv, xv), c1), xv, base);
+        const R amp = fmaR(bsq, xv, boff);
+        x[w] = fmaR(amp, z[w], fmaR(h, drift, xv));
+      }
+    } else {
+      // the draws are not stored: the reverse sweep regenerates them
+      R nr[2], c[2], sn[2];
+      normals4_polar<R>(o, nr, c, sn);
+      const R d = uni[3 * j + 1];    // h (kappa m_j + c0) as the forward used it
+      const R amp = uni[3 * j + 2];  // B0 sqrt(h) as the forward used it
+      em_partial_pair(x[0], x[1], nr[0], c[0], sn[0], hn3, hc1, amp);
+      em_partial_pair(x[2], x[3], nr[1], c[1], sn[1], hn3, hc1, amp);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) x[w] = addR(x[w], d);
+    }
     zero_tail(q, x);
   };
-  // additive form, warps 1..: step r of segment sr for this thread's replay
-  // quads (rows r, from the checkpoint at r = 0, and r + 1 of its buffer)
+  // warps 1..: step r of segment sr for this thread's replay quads (rows r,
+  // from the checkpoint at r = 0, and r + 1 of its state buffer; draw row r)
   auto replay_rows = [&](int sr, int r) {
     if (rt < 0) return;
     R* bx = buf(sr);
+    R* bz = bufz(sr) + (size_t)r * a.pitch;
     const R* ckr = (const R*)a.ckpt + (size_t)sr * a.pitch;
     const long long jr = (long long)sr * a.c + r;
     for (int q = qb + rt; q < qe; q += n_rep) {
@@ -241,7 +261,7 @@ __global__ void __launch_bounds__(TPB, 1) k_adjoint(const AdjointArgs a) {
       } else {
         Quad<R>::load(bx + (size_t)r * a.pitch + 4 * (size_t)q, x);
       }
-      replay_step(q, jr, x);
+      replay_step(q, jr, x, bz);
       Quad<R>::store(bx + (size_t)(r + 1) * a.pitch + 4 * (size_t)q, x);
     }
   };
@@ -250,56 +270,23 @@ __global__ void __launch_bounds__(TPB, 1) k_adjoint(const AdjointArgs a) {
     const long long j0 = (long long)seg * a.c;
     const long long j1 = min(a.J, j0 + a.c);
     const int L = (int)(j1 - j0);
-    R* const bxs = buf(seg);  // this segment's replayed states
-    const R* ck = (const R*)a.ckpt + (size_t)seg * a.pitch;
-    if constexpr (!MULT) {
-      // ---- the last segment: replayed on its own (warps 1..) -------------
-      if (seg == a.n_seg - 1) {
-        if (rt >= 0) {
-          for (int q = qb + rt; q < qe; q += n_rep) {
-            R x[4];
-            Quad<R>::load(ck + 4 * (size_t)q, x);
-            for (int jj = 0; jj < L; ++jj) {
-              Quad<R>::store(bxs + (size_t)jj * a.pitch + 4 * (size_t)q, x);
-              replay_step(q, j0 + jj, x);
-            }
-            Quad<R>::store(bxs + (size_t)L * a.pitch + 4 * (size_t)q, x);
+    R* const bxs = buf(seg);   // this segment's replayed states
+    R* const bzs = bufz(seg);  // and draws (general form)
+    // ---- the last segment: replayed on its own (warps 1..) ---------------
+    if (seg == a.n_seg - 1) {
+      const R* ck = (const R*)a.ckpt + (size_t)seg * a.pitch;
+      if (rt >= 0) {
+        for (int q = qb + rt; q < qe; q += n_rep) {
+          R x[4];
+          Quad<R>::load(ck + 4 * (size_t)q, x);
+          for (int jj = 0; jj < L; ++jj) {
+            Quad<R>::store(bxs + (size_t)jj * a.pitch + 4 * (size_t)q, x);
+            replay_step(q, j0 + jj, x, bzs + (size_t)jj * a.pitch);
           }
+          Quad<R>::store(bxs + (size_t)L * a.pitch + 4 * (size_t)q, x);
         }
-        __syncthreads();  // the rows are read by other threads than their writers
       }
-    }
-    // ---- general form: replay the segment from its checkpoint (thread-private)
-    for (int i = 0; i < (MULT ? nq : 0); ++i) {
-      const int q = qb + tid + i * TPB;
-      R x[4];
-      Quad<R>::load(ck + 4 * (size_t)q, x);
-      for (int jj = 0; jj < L; ++jj) {
-        const long long j = j0 + jj;
-        Quad<R>::store(segx + (size_t)jj * a.pitch + 4 * (size_t)q, x);
-        const uint4 o =
-            philox4x32_10(rng_counter((uint32_t)q, (uint32_t)(j % a.nf), (uint32_t)(j / a.nf), 0u, a.ptag),
-                          a.key0, a.key1);
-        if constexpr (MULT) {
-          // x + h (nc3 x^3 + c1 x + kappa m_j + c0) + (B sqrt(h) x + (BE m_j + B0) sqrt(h)) xi,
-          // rounded as the forward's general form rounds it
-          R z[4];
-          normals4<R>(o, z);
-          zero_tail(q, z);
-          Quad<R>::store(segz + (size_t)jj * a.pitch + 4 * (size_t)q, z);
-          const R base = uni[3 * j + 1];  // kappa m_j + c0 as the forward used it
-          const R boff = uni[3 * j + 2];  // (BE m_j + B0) sqrt(h) as the forward used it
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            const R xv = x[w];
-            const R drift = fmaR(fmaR(nc3, mulR(xv, xv), c1), xv, base);
-            const R amp = fmaR(bsq, xv, boff);
-            x[w] = fmaR(amp, z[w], fmaR(h, drift, xv));
-          }
-        }
-        zero_tail(q, x);
-      }
-      Quad<R>::store(segx + (size_t)L * a.pitch + 4 * (size_t)q, x);
+      __syncthreads();  // the rows are read by other threads than their writers
     }
     // ---- backward through the segment ----------------------------------
     // Shift form of the reverse recursion: lambda_j = mu_j + s_j with
@@ -321,7 +308,7 @@ __global__ void __launch_bounds__(TPB, 1) k_adjoint(const AdjointArgs a) {
         part = addR(part, addR(addR(l[0], l[1]), addR(l[2], l[3])));
         if constexpr (MULT) {
           R zp[4];
-          Quad<R>::load(segz + (size_t)(L - 1) * a.pitch + 4 * (size_t)q, zp);
+          Quad<R>::load(bzs + (size_t)(L - 1) * a.pitch + 4 * (size_t)q, zp);
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
             pz = fmaR(l[w], zp[w], pz);
@@ -354,7 +341,7 @@ __global__ void __launch_bounds__(TPB, 1) k_adjoint(const AdjointArgs a) {
         const int q = qb + tid + i * TPB;
         R l[4], x[4], z[4];
         if constexpr (MULT) {
-          Quad<R>::load(segz + (size_t)jj * a.pitch + 4 * (size_t)q, z);
+          Quad<R>::load(bzs + (size_t)jj * a.pitch + 4 * (size_t)q, z);
         } else {
           polar_draws(j, q, z);  // regenerated: half the bytes of a stored row
         }
@@ -388,7 +375,7 @@ __global__ void __launch_bounds__(TPB, 1) k_adjoint(const AdjointArgs a) {
             // regenerated: that segment is replayed only later)
             R zp[4];
             if (jj > 0) {
-              Quad<R>::load(segz + (size_t)(jj - 1) * a.pitch + 4 * (size_t)q, zp);
+              Quad<R>::load(bzs + (size_t)(jj - 1) * a.pitch + 4 * (size_t)q, zp);
             } else {
               draws(j - 1, q, zp);
             }
@@ -409,7 +396,11 @@ __global__ void __launch_bounds__(TPB, 1) k_adjoint(const AdjointArgs a) {
         // warp 0 reads the sums of mu_{j+1} (epoch ej - 1, published a step
         // ago) before the barrier and publishes those of mu_j after it
         mult_warp((double)part, (double)pz, (double)zs);
-        if (warp == 0) mult_fetch(ej - 1u);
+        if (warp == 0) {
+          mult_fetch(ej - 1u);
+        } else if (seg > 0) {
+          replay_rows(seg - 1, L - 1 - jj);
+        }
         __syncthreads();
         if (sh.abort) return;
         const double sn = (double)s_next;
@@ -461,14 +452,12 @@ __global__ void __launch_bounds__(TPB, 1) k_adjoint(const AdjointArgs a) {
       grp.epoch = ej + 1u;
       par ^= 1;
     }
-    if constexpr (!MULT) {
-      // a segment shorter than c (the last) leaves steps of the previous
-      // segment's replay, which are done here; the barrier of the last
-      // reverse step (or this one) makes the rows visible to their readers
-      if (seg > 0 && L < a.c) {
-        for (int r = L; r < a.c; ++r) replay_rows(seg - 1, r);
-        __syncthreads();
-      }
+    // a segment shorter than c (the last) leaves steps of the previous
+    // segment's replay, which are done here; the barrier of the last reverse
+    // step (or this one) makes the rows visible to their readers
+    if (seg > 0 && L < a.c) {
+      for (int r = L; r < a.c; ++r) replay_rows(seg - 1, r);
+      __syncthreads();
     }
   }
   // ---- reduce the parameter partials over the group (FP64) -------------

@@ -26,7 +26,7 @@ struct AdjointArgs {
   const void* uni;                   // [J][3] recorded per step: (m_j, h (kappa m_j + c0), B0 sqrt h) for
                                      // additive noise, (m_j, kappa m_j + c0, (BE m_j + B0) sqrt h) otherwise
   void* segx;                        // 2 x (c + 1) rows: replayed states, two segment buffers
-  void* segz;                        // c rows: its normal draws
+  void* segz;                        // 2 x c rows: the draws of the two segments (general form)
   const double* mom;                 // [(N+1)][kStat] restriction records of the serial run
   const double* gm;                  // [N] cotangents of the slice-end means (n = 1..N)
   const double* gv;                  // [N] cotangents of the slice-end variances

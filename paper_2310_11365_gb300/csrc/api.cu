@@ -858,12 +858,13 @@ int adjoint_layout(mmp_ctx* c, Prob& p, int ckpt_every, char* base, AdjLayout& L
   };
   L.ckpt = ptr(row * L.n_seg);
   L.uni = ptr(p.esz * 3 * (size_t)J);
-  // two buffers of c + 1 rows of replayed states (the additive form replays
-  // one segment while it reverses the next; the general form uses the first)
+  // two buffers of c + 1 rows of replayed states (one segment is replayed
+  // while the next is reversed)
   L.segx = ptr(row * 2 * (size_t)(ckpt_every + 1));
-  // draw rows: used by the general diffusion form only (additive noise regenerates its
-  // draws), carved for both so that the size does not change with the form (mmp_set_params)
-  L.segz = ptr(row * (size_t)ckpt_every);
+  // two buffers of c draw rows: used by the general diffusion form only (additive noise
+  // regenerates its draws), carved for both so that the size does not change with the form
+  // (mmp_set_params)
+  L.segz = ptr(row * 2 * (size_t)ckpt_every);
   L.gm = (double*)ptr(sizeof(double) * p.d.N);
   L.gv = (double*)ptr(sizeof(double) * p.d.N);
   L.grad = (double*)ptr(sizeof(double) * 8);
